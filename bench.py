@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the fused smoothing-proximal-gradient step at 512^3.
+
+One timed step = one fused iteration (Eq. 20-21 with FISTA extrapolation,
+weighted smoothed TV of Eq. 14-17, and the fused F(x_k) reduction) over the
+whole 512^3 synthetic volume, inputs resident in HBM. Every iteration reads
+about 3.8 GB, far more than the 129 MB L2, so no flush is needed between
+steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl spg|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank solves its own
+independent volume (replicas of the workload, no data-path collective);
+value = voxel-iterations of all ranks / max-over-ranks time.
+
+--impl reference times the FP64 CPU oracle on the host cores (rank 0 only)
+on a bounded z-slab of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gvoxel-iter/s of fused SPG step at 512^3 (% HBM roofline); time to rel gap 1e-3"
+UNIT = "Gvoxel-iter/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="spg", choices=["spg", "reference"])
+    ap.add_argument("--workload", default="vol512")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--tile", default="auto")
+    ap.add_argument("--zchunk", type=int, default=0)
+    ap.add_argument("--no-gap", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(name, dtype):
+    from paper_1905_13408_gb300 import synth
+    s = synth.WORKLOADS[name]
+    h = synth.DEFAULT_HYPER
+    return (f"{name}: {s['n']}^3 {'FP32' if dtype == 'f32' else 'BF16-storage (b,w)'} volume, {s['blobs']} "
+            f"Gaussian blobs in r={s['radius']:g} ball, w=exp(0.5 g) (sigma-4 smoothed field), "
+            f"b=phantom+N(0,0.3^2)/sqrt(w); lambda_l1={h['lambda_l1']}, lambda_tv={h['lambda_tv']}, "
+            f"mu={h['mu']}, eps={h['eps']}; round-1 subproblem (weights 1), FISTA")
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def step_source_hash():
+    with open(os.path.join(ROOT, "paper_1905_13408_gb300", "csrc", "spg_step.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic(workload, dtype):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current fused-step source; else None."""
+    path = os.path.join(ROOT, "profiles", f"spg_step_{workload}_{dtype}.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_sha256") != step_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def bytes_per_voxel(dtype):
+    # reads x_k, x_{k-1}, b, w, om1, omtv; writes x_{k+1}
+    return 28 if dtype == "f32" else 24
+
+
+def cpu_baseline(vol, hyper, nz_slab=64, iters=6):
+    """The FP64 oracle, as it stands, on a z-slab of the workload."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    b = np.ascontiguousarray(vol.b[:nz_slab], dtype=np.float64)
+    w = np.ascontiguousarray(vol.w[:nz_slab], dtype=np.float64)
+    p = oracle.Params(b.shape, **hyper)
+    t0 = time.perf_counter()
+    oracle.solve(b, w, p, rounds=1, iters=iters, with_hist=True)
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    nthreads = int(os.environ.get("OMP_NUM_THREADS", cores))
+    return {"value": b.size * iters / dt / 1e9, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"{iters} iterations (with the objective each iteration, plus one re-weighting) on a "
+                      f"{b.shape[2]}x{b.shape[1]}x{nz_slab} z-slab of the 512^3 workload, FP64, OpenMP",
+            "seconds": dt}
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, local = dist_setup(args)
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_1905_13408_gb300 import synth
+    oracle.build()
+    vol, hyper, _, _ = synth.workload(args.workload)
+    nz_slab = 32
+    b = np.ascontiguousarray(vol.b[:nz_slab], dtype=np.float64)
+    w = np.ascontiguousarray(vol.w[:nz_slab], dtype=np.float64)
+    p = oracle.Params(b.shape, **hyper)
+    om1, omtv, st = oracle.reweight(np.zeros_like(b), p)
+    tau = 1.0 / oracle.lipschitz(w, st[0], p)
+    beta = oracle.beta_table(args.warmup + args.steps + 1)
+    x = np.zeros_like(b)
+    xp = x.copy()
+    for k in range(args.warmup):
+        xn = oracle.step(x, xp, beta[k], tau, b, w, om1, omtv, p)
+        xp, x = x, xn
+    t0 = time.perf_counter()
+    for k in range(args.warmup, args.warmup + args.steps):
+        oracle.objective(x, b, w, om1, omtv, p)
+        xn = oracle.step(x, xp, beta[k], tau, b, w, om1, omtv, p)
+        xp, x = x, xn
+    dt = time.perf_counter() - t0
+    value = b.size * args.steps / dt / 1e9
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    nthreads = int(os.environ.get("OMP_NUM_THREADS", cores))
+    sample = (f"each step: one FP64 oracle iteration (objective + step) on a {b.shape[2]}x{b.shape[1]}x{nz_slab} "
+              f"z-slab of the 512^3 workload")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": workload_desc(args.workload, "f32"),
+                                           "sample_voxels": int(b.size)},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def time_to_gap(vol, hyper, args, stream):
+    """Round-1 subproblem from x_0 = 0: iterations and wall time (CUDA events)
+    until F(x_k) <= F* (1 + 1e-3), F* the best objective of a run with about
+    10x as many iterations (same code, FP64 reductions)."""
+    import numpy as np
+    import torch
+
+    from paper_1905_13408_gb300 import spg
+    n_ref = 1500
+    s = spg.SPG(dict(shape=vol.b.shape, **hyper), data_dtype=args.dtype, hist_capacity=n_ref + 16,
+                tile=args.tile, zchunk=args.zchunk, stream=stream.cuda_stream)
+    s.set_data(0, *dev_inputs(vol, args.dtype))
+    s.reweight()
+    s.iterate(n_ref)
+    h = s.history(0)
+    fstar = float(h[:, 4].min())
+    rel = (h[:, 4] - fstar) / abs(fstar)
+    hit = np.nonzero(rel <= 1e-3)[0]
+    k_gap = int(h[hit[0], 0]) if len(hit) else None
+    result = {"F_star": fstar, "F_star_iterations": n_ref, "iterations_to_gap": k_gap}
+    if k_gap is not None:
+        # timed re-run: reweight + k_gap fused iterations from x_0 = 0 (history checked every 10)
+        zero = torch.zeros(vol.b.shape, dtype=torch.float32, device="cuda")
+        s.set_x(0, zero)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.reweight()
+        done = 0
+        while done < k_gap:
+            c = min(10, k_gap - done)
+            s.iterate(c)
+            done += c
+        e1.record(stream)
+        torch.cuda.synchronize()
+        result["time_to_gap_ms"] = e0.elapsed_time(e1)
+        result["note"] = "round-1 subproblem (x_0 = 0, weights 1); paper's 512^3 figure: 'medium accurate' in 10 s, hardware unnamed"
+    s.close()
+    return result
+
+
+def dev_inputs(vol, dtype):
+    import torch
+    b = torch.from_numpy(vol.b).cuda()
+    w = torch.from_numpy(vol.w).cuda()
+    return b, w
+
+
+def run_spg(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1905_13408_gb300 import spg, synth
+    rank, world, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    spec = synth.WORKLOADS[args.workload]
+    n = spec["n"]
+    vol = synth.make_volume((n, n, n), spec["blobs"], spec["radius"], spec["seed"] + 100 * rank)
+    hyper = dict(synth.DEFAULT_HYPER)
+    nvox = vol.b.size
+
+    s = spg.SPG(dict(shape=vol.b.shape, **hyper), data_dtype=args.dtype, tile=args.tile, zchunk=args.zchunk,
+                stream=stream.cuda_stream, max_iters=max(100000, args.steps + args.warmup + 16))
+    s.set_data(0, *dev_inputs(vol, args.dtype))
+    s.reweight()
+    s.iterate(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = s.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.iterate(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = s.launch_count() - l0
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    obj = s.objective(0)
+    plan = s.plan_info()
+    s.close()
+
+    per_launch_s = ms / 1e3 / args.steps
+    value = world * nvox * args.steps / (ms / 1e3) / 1e9
+    peaks, peak_kind = measured_peaks()
+    bpv = bytes_per_voxel(args.dtype)
+    achieved = bpv * nvox / per_launch_s / 1e9
+    traffic = profiled_traffic(args.workload, args.dtype)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": bpv * nvox,
+            "kernel": "spg_step_kernel (fused iteration + objective)"}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(vol, hyper, args, stream)
+    gap = None
+    if not args.no_gap and rank == 0:
+        gap = time_to_gap(vol, hyper, args, stream)
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_baseline(vol, hyper)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+               "config": {"workload": workload_desc(args.workload, args.dtype), "voxels": nvox,
+                          "l2": "inputs larger than L2 (each step streams ~%.1f GB)" % (bpv * nvox / 1e9),
+                          "tile": f"{plan['tile_x']}x{plan['tile_y']}", "zchunk": plan["zchunk"],
+                          "grid": plan["grid"], "items": plan["items"], "objective_every_step": True,
+                          "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+               "roofline": roof, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
+               "cpu_baseline": cpu, "time_to_gap": gap, "final_objective": float(obj[3])}
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_e2e(vol, hyper, args, stream, iters=100, reps=3):
+    """Through the public API with host buffers: each step uploads b and w from
+    pinned host memory, re-weights, runs `iters` fused iterations, reads the
+    objective and downloads x to pinned host memory."""
+    import torch
+
+    from paper_1905_13408_gb300 import spg
+    b_h = torch.from_numpy(vol.b).pin_memory()
+    w_h = torch.from_numpy(vol.w).pin_memory()
+    x_h = torch.empty(vol.b.shape, dtype=torch.float32).pin_memory()
+    s = spg.SPG(dict(shape=vol.b.shape, **hyper), data_dtype=args.dtype, tile=args.tile, zchunk=args.zchunk,
+                stream=stream.cuda_stream)
+    zero = torch.zeros(vol.b.shape, dtype=torch.float32)
+    s.set_data(0, b_h, w_h)
+    s.reweight()
+    s.iterate(5)
+    s.get_x(0, x_h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        s.set_data(0, b_h, w_h)
+        s.reweight()
+        s.iterate(iters)
+        s.objective(0)
+        s.get_x(0, x_h)
+        torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    del zero
+    nvox = vol.b.size
+    return {"value": nvox * iters * reps / dt / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": int(b_h.numel() * 4 + w_h.numel() * 4),
+            "d2h_bytes_per_step": int(x_h.numel() * 4 + 4 * 8),
+            "step": f"upload b,w from pinned host, re-weight, {iters} fused iterations, objective, download x"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_spg(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,208 @@
+/*
+ * spg.h - C ABI of the GB300 reweighted smoothing-proximal-gradient solver.
+ *
+ * The solver minimises, for each volume and each re-weighting round r,
+ *
+ *   F_r(x) = 1/2 sum_v w_v (x_v - b_v)^2                     data term (Sec. 2.2, Eq. 28;
+ *                                                            the 1/2 of Eq. 31)
+ *          + lambda_l1 sum_v om1_v |x_v|                     weighted l1 (Eq. 11)
+ *          + lambda_tv sum_v omtv_v h_mu((Dx)_v)             weighted smoothed TV (Eq. 11, 14)
+ *
+ * over a real-space density x on an nx*ny*nz grid (Sec. 2.1, the vectorised
+ * volume of Eq. 8). D is the backward difference of Eq. 12 (zero on the first
+ * plane of each axis), h_mu is Nesterov's smoothing of the Euclidean norm
+ * (Eq. 14), whose gradient z/max(mu,|z|) is Eq. 16, and D^T is Eq. 17. The
+ * weights are re-set between rounds from the current iterate (Eq. 11, scaled
+ * by eps as Sec. 2.5 prescribes):
+ *
+ *   om1_v = eps / (|x_v| + eps),   omtv_v = eps_tv / (|(Dx)_v| + eps_tv).
+ *
+ * Each iteration is one fused pass over the volume (Eq. 20 and Eq. 21 with
+ * FISTA extrapolation; beta = 0 gives the paper's plain update):
+ *
+ *   y       = x_k + beta_k (x_k - x_{k-1})
+ *   x_{k+1} = soft(y - tau grad f(y), tau lambda_l1 om1),
+ *   grad f  = w (y - b) + lambda_tv D^T(omtv grad h_mu(D y)),
+ *
+ * with tau = 1/L, L = max w + 12 lambda_tv max(omtv) / mu (|D|^2 <= 12).
+ *
+ * Conventions (every entry point):
+ *  - Volumes are dense float32 (or bfloat16 where stated) arrays in C order
+ *    [nz][ny][nx], x fastest, no padding. Pointers may be device pointers or
+ *    host pointers (pinned or pageable): copies use unified addressing. The
+ *    library never keeps or frees a caller pointer; it copies what it needs.
+ *  - Work is enqueued on the CUDA stream given at creation (NULL = the legacy
+ *    default stream). Entry points that return host values synchronise that
+ *    stream; the others are asynchronous.
+ *  - Every call returns an spg_status; spg_last_error() gives a message. No
+ *    C++ exception crosses this interface. There is no CPU fallback: without
+ *    a usable CUDA device, spg_create fails with SPG_ECUDA.
+ *  - One context is used by one host thread at a time.
+ */
+#ifndef SPG_H
+#define SPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spg_ctx spg_ctx;
+
+typedef enum {
+    SPG_OK = 0,
+    SPG_EINVAL = -1,      /* bad argument (NULL, size, dtype, volume index, w <= 0 ...) */
+    SPG_ENOMEM = -2,      /* device allocation failed */
+    SPG_ECUDA = -3,       /* CUDA runtime / driver error */
+    SPG_ENOTREADY = -4,   /* call order violated (e.g. iterate before set_data/reweight) */
+    SPG_ENONFINITE = -5,  /* a non-finite objective value or input was detected */
+    SPG_ETIMEOUT = -6     /* a bounded device-side wait gave up (context stays usable) */
+} spg_status;
+
+typedef enum { SPG_F32 = 0, SPG_BF16 = 1 } spg_dtype;
+
+/* SPG_FISTA: Beck-Teboulle extrapolation, restarted every round.
+ * SPG_ISTA: beta = 0, the paper's Eq. 20-21 update as printed. */
+typedef enum { SPG_FISTA = 0, SPG_ISTA = 1 } spg_momentum;
+
+/* Per-volume problem description. eps/eps_tv set the weight scale of Eq. 11
+ * (Sec. 2.5 multiplies the weights by eps so that a zero voxel gets weight 1). */
+typedef struct {
+    int nx, ny, nz;
+    float lambda_l1;   /* alpha of Eq. 8-11 */
+    float lambda_tv;   /* beta of Eq. 8-11 */
+    float mu;          /* Nesterov smoothing parameter of Eq. 14 */
+    float eps;         /* epsilon of Eq. 9/11 for the l1 weights */
+    float eps_tv;      /* epsilon' of Eq. 31 for the TV weights */
+} spg_volume_params;
+
+/* Context-wide options. Zero-initialised options are valid defaults. */
+typedef struct {
+    spg_dtype data_dtype;     /* storage of b and w on the device: SPG_F32 or SPG_BF16
+                                 (arithmetic stays float32 either way) */
+    spg_momentum momentum;    /* SPG_FISTA (default) or SPG_ISTA */
+    int hist_every;           /* record F(x_k) every this many iterations; 0 = 1 */
+    int hist_capacity;        /* entries kept in the history ring; 0 = 4096 */
+    int max_iters_per_round;  /* length of the extrapolation table; 0 = 100000 */
+    int tile;                 /* 0 = built-in choice, else an spg_tile_* code */
+    int zchunk;               /* 0 = built-in choice, else planes per work item */
+    int ctas_per_sm;          /* 0 = occupancy limit, else a cap */
+} spg_options;
+
+/* Tile codes for spg_options.tile: x extent = 32 * vx, y extent = ty. */
+enum { SPG_TILE_AUTO = 0, SPG_TILE_128x8 = 1, SPG_TILE_128x4 = 2, SPG_TILE_64x8 = 3,
+       SPG_TILE_64x4 = 4, SPG_TILE_128x16 = 5, SPG_TILE_64x16 = 6 };
+
+/* Create a solver for one volume (spg_create) or for nvol independent
+ * volumes of possibly different sizes advanced together, one fused launch per
+ * iteration for all of them (spg_create_batch; the paper refines classes and
+ * the two gold-standard half-maps independently, Sec. 2 and Sec. 2.3).
+ * params: one (or nvol) descriptions, copied. opt: NULL for defaults.
+ * stream: a cudaStream_t or NULL. On success *out owns all device memory it
+ * allocated (about 7 float32 volumes per volume). Errors: SPG_EINVAL for a
+ * non-positive size or parameter, SPG_ENOMEM, SPG_ECUDA. */
+spg_status spg_create(const spg_volume_params *params, const spg_options *opt, void *stream,
+                      spg_ctx **out);
+spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg_options *opt,
+                            void *stream, spg_ctx **out);
+
+/* Set the data volume b (the kernel-regression numerator over N(n), Eq. 28)
+ * and the weight volume w (N(n), Eq. 28) of volume `vol`. src_dtype is the
+ * dtype of the caller's arrays (SPG_F32 or SPG_BF16); they are converted with
+ * round-to-nearest-even when the context stores the other dtype. w must be
+ * finite and > 0, b finite: checked on the device, SPG_EINVAL / SPG_ENONFINITE
+ * otherwise. Synchronises (it reduces max w in double precision). */
+spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg_dtype src_dtype);
+
+/* Set / read the current iterate of volume `vol` (float32, nx*ny*nz).
+ * The initial iterate is 0. spg_set_x also sets x_{k-1} = x (momentum
+ * restart). spg_get_x is asynchronous unless `x` is pageable host memory. */
+spg_status spg_set_x(spg_ctx *ctx, int vol, const float *x);
+spg_status spg_get_x(spg_ctx *ctx, int vol, float *x);
+
+/* Start a round: re-set om1 and omtv from the current iterate of every
+ * volume (Eq. 11), reduce max omtv (and nnz, sums) in double precision, set
+ * tau = 1/L per volume and restart the extrapolation (t = 1, x_{-1} = x).
+ * Asynchronous; per-volume statistics are read with spg_round_stats. */
+spg_status spg_reweight(spg_ctx *ctx);
+
+/* Run k iterations (one fused launch each, replayed from a captured CUDA
+ * graph when k is large). Asynchronous. Errors: SPG_ENOTREADY before the
+ * first spg_reweight, SPG_EINVAL if the round would exceed
+ * max_iters_per_round. */
+spg_status spg_iterate(spg_ctx *ctx, int k);
+
+/* F at the current iterate of volume `vol`: out = {data, l1, tv, total}
+ * (host doubles). Synchronises. */
+spg_status spg_objective(spg_ctx *ctx, int vol, double out[4]);
+
+/* Objective history of volume `vol`: entries (k, data, l1, tv, total), 5
+ * doubles each, one per recorded iteration (F(x_k) is recorded by the launch
+ * that consumes x_k; k counts iterations since creation). Copies at most
+ * max_entries of the newest entries in increasing k to `host`, sets *n.
+ * Synchronises. */
+spg_status spg_history(spg_ctx *ctx, int vol, double *host, int max_entries, int *n);
+
+/* Statistics of the last spg_reweight for volume `vol`:
+ * out = {max omtv, nnz(x), sum om1, sum omtv, L, tau}. Synchronises. */
+spg_status spg_round_stats(spg_ctx *ctx, int vol, double out[6]);
+
+/* Strong-convexity certificate of the last iteration of volume `vol`:
+ * out = |r|^2 with r = grad f(x_{k+1}) - grad f(y_k) + (y_k - x_{k+1})/tau, an
+ * element of the subdifferential of F at x_{k+1}; F(x_{k+1}) - F* <=
+ * |r|^2 / (2 min w). Needs at least one iteration in the round. Synchronises. */
+spg_status spg_certificate(spg_ctx *ctx, int vol, double *out);
+
+/* Iteration counters: total iterations since creation and within the round. */
+spg_status spg_counters(spg_ctx *ctx, long long *k_total, int *k_round);
+
+/* Checkpoint / resume. A state blob holds, for every volume, x_k, x_{k-1},
+ * om1, omtv, tau, and the counters; spg_set_state on a context created with
+ * the same parameters continues bit-identically. With blob == NULL,
+ * spg_get_state only sets *size. Synchronise. */
+spg_status spg_get_state(spg_ctx *ctx, void *blob, size_t *size);
+spg_status spg_set_state(spg_ctx *ctx, const void *blob, size_t size);
+
+/* Adjoint of K unrolled iterations of one round with the current weights
+ * and tau held fixed, starting from the current iterate as x_0 (with
+ * x_{-1} = x_0), single volume contexts only. gx: dLoss/dx_K (float32
+ * volume). Writes gb = dLoss/db, gw = dLoss/dw (float32 volumes) and
+ * g_scalars = {dLoss/dlambda_l1, dLoss/dlambda_tv}. Recomputes the forward
+ * iterates from checkpoints of (x_k, x_{k-1}) taken every `ckpt_every`
+ * iterations (0 = 10). The context's own iterate is left unchanged.
+ * Synchronises. */
+spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *gw,
+                        double g_scalars[2], int ckpt_every);
+
+/* Run the forward part of spg_backward: K iterations from the current
+ * iterate with fixed weights and tau, writing x_K to `xK` (float32 volume);
+ * the context's iterate is left unchanged. Synchronises. */
+spg_status spg_unrolled(spg_ctx *ctx, int K, float *xK);
+
+/* Self-test of the bounded device-side wait used by the fused step: launches
+ * one CTA that waits on a barrier nothing ever completes, with a limit of
+ * `timeout_ns`. Returns SPG_ETIMEOUT when the wait gave up as designed (the
+ * context stays usable), SPG_OK if it did not time out. Synchronises. */
+spg_status spg_probe_timeout(spg_ctx *ctx, long long timeout_ns);
+
+/* Kernel launches issued by this context so far (for launch accounting). */
+long long spg_launch_count(const spg_ctx *ctx);
+
+/* Number of volumes, and the tile and work split chosen for the fused step:
+ * info = {vx*32, ty, zchunk, work items, grid size, ctas per SM}. */
+spg_status spg_plan_info(const spg_ctx *ctx, int info[6]);
+
+/* Message for the last failing call on ctx (or a global message if ctx is
+ * NULL); never NULL. */
+const char *spg_last_error(const spg_ctx *ctx);
+
+/* Free everything the context allocated. NULL is a no-op. */
+void spg_destroy(spg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPG_H */

@@ -1,0 +1,1021 @@
+// C ABI of the GB300 reweighted SPG solver (include/spg.h): contexts, device
+// layout, TMA tensor maps, the work plan of the fused step, CUDA-graph replay
+// of iterations, checkpoints and the adjoint driver.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "spg.h"
+#include "spg_internal.h"
+
+using namespace spg;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+constexpr long long kTimeoutNs = 2000000000LL;  // 2 s bound on any device-side wait
+constexpr int kGraphLen = 10;                   // iterations per captured graph
+constexpr uint64_t kStateMagic = 0x5350475354415445ull;  // "SPGSTATE"
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+}  // namespace
+
+struct spg_ctx {
+    int nvol = 0;
+    std::vector<spg_volume_params> vp;
+    spg_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+
+    std::vector<VolDesc> vols_h;
+    std::vector<int> plane_vol_h;
+    long long total = 0;  // elements per flat volume array
+    int nplanes = 0;
+
+    VolDesc *vols_d = nullptr;
+    WorkItem *items_d = nullptr;
+    TmapSet *tmaps_d = nullptr;
+    int *plane_vol_d = nullptr;
+    float *X[3] = {nullptr, nullptr, nullptr};
+    void *B = nullptr, *W = nullptr;
+    float *OM1 = nullptr, *OMTV = nullptr;
+    float *beta_d = nullptr;
+    DevState *st_d = nullptr;
+    double *partials_d = nullptr;
+    double *hist_d = nullptr;
+    double *plane_part_d = nullptr;
+    double *vol_out_d = nullptr;
+    double *maxw_d = nullptr;
+    double *rstats_d = nullptr;
+
+    StepVariant var{4, 8, 3, false};
+    int zchunk = 0, grid = 0, ctas_per_sm = 0, nitems = 0;
+    std::vector<WorkItem> items_h;
+
+    long long k_total = 0;  // host mirror of the device counters
+    int k_round = 0;
+    int cur0 = 0;           // x_k lives in X[(cur0 + k_total) % 3]
+    bool reweighted = false;
+    std::vector<char> data_set;
+    int hist_every = 1, hist_cap = 4096, max_iters = 100000;
+
+    cudaGraphExec_t gexec = nullptr;
+    long long launches = 0;
+    std::string err = "no error";
+
+    bool bf16() const { return opt.data_dtype == SPG_BF16; }
+    size_t data_es() const { return bf16() ? 2 : 4; }
+    int cur() const { return (int)(((cur0 + k_total) % 3 + 3) % 3); }
+};
+
+namespace {
+
+spg_status fail(spg_ctx *c, spg_status s, const std::string &msg)
+{
+    if (c)
+        c->err = msg;
+    else
+        g_last_error = msg;
+    return s;
+}
+
+spg_status cuda_fail(spg_ctx *c, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();  // clear a non-sticky error
+    return fail(c, e == cudaErrorMemoryAllocation ? SPG_ENOMEM : SPG_ECUDA, m);
+}
+
+#define CK(call, what)                                              \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what);     \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t bytes)
+{
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes ? bytes : 16);
+}
+
+void free_all(spg_ctx *c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    void *ps[] = {c->vols_d, c->items_d, c->tmaps_d, c->plane_vol_d, c->X[0], c->X[1], c->X[2], c->B, c->W,
+                  c->OM1, c->OMTV, c->beta_d, c->st_d, c->partials_d, c->hist_d, c->plane_part_d,
+                  c->vol_out_d, c->maxw_d, c->rstats_d};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+StepVariant variant_from_tile(int tile, bool bf16)
+{
+    switch (tile) {
+    case SPG_TILE_128x4: return {4, 4, 4, bf16};
+    case SPG_TILE_64x8: return {2, 8, 4, bf16};
+    case SPG_TILE_64x4: return {2, 4, 4, bf16};
+    case SPG_TILE_128x16: return {4, 16, 2, bf16};
+    case SPG_TILE_128x8:
+    default: return {4, 8, 3, bf16};
+    }
+}
+
+int tile_code(const StepVariant &v)
+{
+    if (v.vx == 4 && v.ty == 8) return SPG_TILE_128x8;
+    if (v.vx == 4 && v.ty == 4) return SPG_TILE_128x4;
+    if (v.vx == 2 && v.ty == 8) return SPG_TILE_64x8;
+    if (v.vx == 2 && v.ty == 4) return SPG_TILE_64x4;
+    if (v.vx == 4 && v.ty == 16) return SPG_TILE_128x16;
+    return 0;
+}
+
+// Built-in tile choice: the widest tile that the volumes fill well.
+StepVariant default_variant(const spg_ctx *c)
+{
+    long long vox = 0, waste128 = 0, waste64 = 0;
+    for (const auto &v : c->vols_h) {
+        const long long n = (long long)v.nx * v.ny * v.nz;
+        vox += n;
+        waste128 += (round_up(v.nx, 128) - v.nx) * (long long)v.ny * v.nz;
+        waste64 += (round_up(v.nx, 64) - v.nx) * (long long)v.ny * v.nz;
+    }
+    const bool wide = waste128 <= vox / 8;
+    if (wide) return {4, 8, 3, c->bf16()};
+    if (waste64 <= vox / 8) return {2, 8, 4, c->bf16()};
+    return {2, 4, 4, c->bf16()};
+}
+
+cudaError_t encode_map(CUtensorMap *m, CUtensorMapDataType dt, void *base, const VolDesc &v, size_t es, int bx,
+                       int by)
+{
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    cuuint64_t dims[3] = {(cuuint64_t)v.nx, (cuuint64_t)v.ny, (cuuint64_t)v.nz};
+    cuuint64_t strides[2] = {(cuuint64_t)v.pitch * es, (cuuint64_t)v.pitch * v.ny * es};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    char *addr = static_cast<char *>(base) + (size_t)v.off * es;
+    CUresult r = fn(m, dt, 3, addr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Work plan: tensor maps for the variant's boxes, work items, grid size.
+spg_status build_plan(spg_ctx *ctx, const StepVariant &v, int zchunk_opt)
+{
+    if (!step_variant_supported(v)) return fail(ctx, SPG_EINVAL, "unsupported tile variant");
+    int occ = 0;
+    CK(step_configure(v, &occ), "configure fused step");
+    if (occ < 1) return fail(ctx, SPG_ECUDA, "fused step does not fit on an SM");
+    if (ctx->opt.ctas_per_sm > 0) occ = std::min(occ, ctx->opt.ctas_per_sm);
+    const int TX = 32 * v.vx, TY = v.ty;
+    const long long slots = (long long)ctx->num_sms * occ;
+
+    long long columns = 0, plane_tiles = 0;
+    for (const auto &d : ctx->vols_h) {
+        const long long cols = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY);
+        columns += cols;
+        plane_tiles += cols * d.nz;
+    }
+    // Planes per work item: one wave of equal items when every column fits
+    // (each column split into slots/columns chunks), else ~4 items per slot.
+    int chunk;
+    if (zchunk_opt > 0) {
+        chunk = zchunk_opt;
+    } else if (columns <= slots) {
+        const long long nch = std::max<long long>(1, slots / columns);
+        int maxnz = 0;
+        for (const auto &d : ctx->vols_h) maxnz = std::max(maxnz, d.nz);
+        chunk = (int)((maxnz + nch - 1) / nch);
+    } else {
+        chunk = (int)std::max<long long>(8, plane_tiles / (slots * 4));
+    }
+    chunk = std::max(1, chunk);
+
+    std::vector<WorkItem> items;
+    for (int j = 0; j < ctx->nvol; j++) {
+        VolDesc &d = ctx->vols_h[j];
+        d.item_begin = (int)items.size();
+        const int nch = (d.nz + chunk - 1) / chunk;
+        for (int c = 0; c < nch; c++) {
+            const int z0 = (int)((long long)d.nz * c / nch), z1 = (int)((long long)d.nz * (c + 1) / nch);
+            if (z1 <= z0) continue;
+            for (int ty = 0; ty < (d.ny + TY - 1) / TY; ty++)
+                for (int tx = 0; tx < (d.nx + TX - 1) / TX; tx++)
+                    items.push_back(WorkItem{j, tx * TX, ty * TY, z0, z1, 0, 0, 0});
+        }
+        d.item_end = (int)items.size();
+    }
+
+    // tensor maps
+    std::vector<TmapSet> maps(ctx->nvol);
+    const CUtensorMapDataType dt_data = v.bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    for (int j = 0; j < ctx->nvol; j++) {
+        const VolDesc &d = ctx->vols_h[j];
+        TmapSet &m = maps[j];
+        std::memset(&m, 0, sizeof(m));
+        for (int q = 0; q < 3; q++)
+            CK(encode_map(&m.x[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ctx->X[q], d, 4, TX + 8, TY + 2), "tensor map x");
+        CK(encode_map(&m.omtv, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ctx->OMTV, d, 4, TX + 4, TY + 1), "tensor map omtv");
+        CK(encode_map(&m.b, dt_data, ctx->B, d, ctx->data_es(), TX, TY), "tensor map b");
+        CK(encode_map(&m.w, dt_data, ctx->W, d, ctx->data_es(), TX, TY), "tensor map w");
+        CK(encode_map(&m.om1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ctx->OM1, d, 4, TX, TY), "tensor map om1");
+    }
+
+    if (ctx->items_d) cudaFree(ctx->items_d);
+    if (ctx->partials_d) cudaFree(ctx->partials_d);
+    ctx->items_d = nullptr;
+    ctx->partials_d = nullptr;
+    CK(dalloc(&ctx->items_d, items.size() * sizeof(WorkItem)), "alloc items");
+    CK(dalloc(&ctx->partials_d, items.size() * 3 * sizeof(double)), "alloc partials");
+    CK(cudaMemcpyAsync(ctx->items_d, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                       ctx->stream),
+       "upload items");
+    CK(cudaMemcpyAsync(ctx->tmaps_d, maps.data(), maps.size() * sizeof(TmapSet), cudaMemcpyHostToDevice, ctx->stream),
+       "upload tensor maps");
+    // item ranges changed: refresh descriptors (tau is device-owned, keep it)
+    std::vector<VolDesc> dev(ctx->nvol);
+    CK(cudaMemcpyAsync(dev.data(), ctx->vols_d, ctx->nvol * sizeof(VolDesc), cudaMemcpyDeviceToHost, ctx->stream),
+       "read descriptors");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    for (int j = 0; j < ctx->nvol; j++) ctx->vols_h[j].tau = dev[j].tau;
+    CK(cudaMemcpyAsync(ctx->vols_d, ctx->vols_h.data(), ctx->nvol * sizeof(VolDesc), cudaMemcpyHostToDevice,
+                       ctx->stream),
+       "upload descriptors");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+
+    ctx->var = v;
+    ctx->zchunk = chunk;
+    ctx->items_h = items;
+    ctx->nitems = (int)items.size();
+    ctx->ctas_per_sm = occ;
+    ctx->grid = (int)std::min<long long>(ctx->nitems, slots);
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    return SPG_OK;
+}
+
+StepParams step_params(const spg_ctx *c)
+{
+    StepParams p;
+    p.vols = c->vols_d;
+    p.items = c->items_d;
+    p.tmaps = c->tmaps_d;
+    for (int q = 0; q < 3; q++) p.xbuf[q] = c->X[q];
+    p.beta = c->beta_d;
+    p.st = c->st_d;
+    p.partials = c->partials_d;
+    p.hist = c->hist_d;
+    p.nitems = c->nitems;
+    p.nvol = c->nvol;
+    p.hist_cap = c->hist_cap;
+    p.hist_every = c->hist_every;
+    p.timeout_ns = kTimeoutNs;
+    return p;
+}
+
+AuxParams aux_params(const spg_ctx *c)
+{
+    AuxParams a;
+    a.vols = c->vols_d;
+    a.plane_vol = c->plane_vol_d;
+    a.nplanes = c->nplanes;
+    a.nvol = c->nvol;
+    a.st = c->st_d;
+    a.plane_part = c->plane_part_d;
+    a.vol_out = c->vol_out_d;
+    return a;
+}
+
+// Read the device error word (synchronises); returns and clears it.
+spg_status device_status(spg_ctx *ctx)
+{
+    DevState st;
+    CK(cudaMemcpyAsync(&st, ctx->st_d, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream), "read state");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    if (st.err != 0) {
+        int zero = 0;
+        cudaMemcpyAsync(&ctx->st_d->err, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        if (st.err == SPG_ETIMEOUT) return fail(ctx, SPG_ETIMEOUT, "a device-side wait timed out");
+        if (st.err == SPG_ENONFINITE) return fail(ctx, SPG_ENONFINITE, "non-finite objective value");
+        return fail(ctx, (spg_status)st.err, "device error");
+    }
+    return SPG_OK;
+}
+
+bool params_ok(const spg_volume_params &p)
+{
+    auto pos = [](float v) { return std::isfinite(v) && v > 0.f; };
+    auto nonneg = [](float v) { return std::isfinite(v) && v >= 0.f; };
+    return p.nx > 0 && p.ny > 0 && p.nz > 0 && nonneg(p.lambda_l1) && nonneg(p.lambda_tv) && pos(p.mu) &&
+           pos(p.eps) && pos(p.eps_tv) && (long long)p.nx * p.ny < (1LL << 31);
+}
+
+spg_status copy_volume_in(spg_ctx *ctx, void *dst_base, size_t es, const VolDesc &d, const void *src)
+{
+    char *dst = static_cast<char *>(dst_base) + (size_t)d.off * es;
+    CK(cudaMemcpy2DAsync(dst, (size_t)d.pitch * es, src, (size_t)d.nx * es, (size_t)d.nx * es, (size_t)d.ny * d.nz,
+                         cudaMemcpyDefault, ctx->stream),
+       "copy volume in");
+    return SPG_OK;
+}
+
+spg_status copy_volume_out(spg_ctx *ctx, void *dst, const void *src_base, size_t es, const VolDesc &d)
+{
+    const char *src = static_cast<const char *>(src_base) + (size_t)d.off * es;
+    CK(cudaMemcpy2DAsync(dst, (size_t)d.nx * es, src, (size_t)d.pitch * es, (size_t)d.nx * es, (size_t)d.ny * d.nz,
+                         cudaMemcpyDefault, ctx->stream),
+       "copy volume out");
+    return SPG_OK;
+}
+
+spg_status launch_steps(spg_ctx *ctx, int k)
+{
+    const StepParams p = step_params(ctx);
+    if (k >= kGraphLen && !ctx->gexec) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        for (int i = 0; i < kGraphLen; i++) {
+            cudaError_t e = step_launch(ctx->var, ctx->grid, p, ctx->stream);
+            if (e != cudaSuccess) {
+                cudaStreamEndCapture(ctx->stream, &g);
+                if (g) cudaGraphDestroy(g);
+                return cuda_fail(ctx, e, "capture fused step");
+            }
+        }
+        CK(cudaStreamEndCapture(ctx->stream, &g), "end capture");
+        cudaError_t e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+        cudaGraphDestroy(g);
+        CK(e, "instantiate graph");
+    }
+    while (k >= kGraphLen && ctx->gexec) {
+        CK(cudaGraphLaunch(ctx->gexec, ctx->stream), "graph launch");
+        ctx->launches += kGraphLen;
+        k -= kGraphLen;
+    }
+    for (int i = 0; i < k; i++) {
+        CK(step_launch(ctx->var, ctx->grid, p, ctx->stream), "fused step launch");
+        ctx->launches += 1;
+    }
+    return SPG_OK;
+}
+
+}  // namespace
+
+namespace {
+struct StateHeader {
+    uint64_t magic;
+    int32_t version, nvol, k_round, reweighted;
+    int64_t k_total;
+    int32_t dtype, momentum;
+};
+static_assert(sizeof(StateHeader) == 40, "state blob header layout");
+}  // namespace
+
+namespace {
+
+struct Scratch {
+    std::vector<void *> ptrs;
+    ~Scratch()
+    {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <class T>
+    cudaError_t get(T **p, size_t bytes)
+    {
+        cudaError_t e = dalloc(p, bytes);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+};
+
+std::vector<float> beta_table_host(const spg_ctx *ctx, int K)
+{
+    std::vector<float> b(std::max(K, 1));
+    double t = 1.0;
+    for (int k = 0; k < K; k++) {
+        const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+        b[k] = ctx->opt.momentum == SPG_ISTA ? 0.f : (float)((t - 1.0) / tn);
+        t = tn;
+    }
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg_options *opt, void *stream,
+                            spg_ctx **out)
+{
+    if (!out || !params || nvol < 1) return fail(nullptr, SPG_EINVAL, "spg_create: bad arguments");
+    *out = nullptr;
+    for (int j = 0; j < nvol; j++)
+        if (!params_ok(params[j])) return fail(nullptr, SPG_EINVAL, "spg_create: invalid volume parameters");
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, SPG_ECUDA, std::string("spg_create: no usable CUDA device: ") + cudaGetErrorString(e));
+    }
+    int major = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    if (major < 10) return fail(nullptr, SPG_ECUDA, "spg_create: needs a Blackwell (sm_10x) GPU");
+    if (!encode_fn()) return fail(nullptr, SPG_ECUDA, "spg_create: cuTensorMapEncodeTiled unavailable");
+
+    spg_ctx *ctx = new spg_ctx();
+    ctx->nvol = nvol;
+    ctx->vp.assign(params, params + nvol);
+    if (opt) ctx->opt = *opt;
+    if (ctx->opt.data_dtype != SPG_F32 && ctx->opt.data_dtype != SPG_BF16) {
+        delete ctx;
+        return fail(nullptr, SPG_EINVAL, "spg_create: bad data dtype");
+    }
+    ctx->hist_every = ctx->opt.hist_every > 0 ? ctx->opt.hist_every : 1;
+    ctx->hist_cap = ctx->opt.hist_capacity > 0 ? ctx->opt.hist_capacity : 4096;
+    ctx->max_iters = ctx->opt.max_iters_per_round > 0 ? ctx->opt.max_iters_per_round : 100000;
+    ctx->num_sms = nsm;
+    ctx->data_set.assign(nvol, 0);
+    if (stream) {
+        ctx->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        e = cudaStreamCreate(&ctx->stream);
+        if (e != cudaSuccess) {
+            delete ctx;
+            return fail(nullptr, SPG_ECUDA, "spg_create: stream creation failed");
+        }
+        ctx->own_stream = true;
+    }
+
+    // layout
+    long long off = 0;
+    int plane = 0;
+    for (int j = 0; j < nvol; j++) {
+        const auto &p = params[j];
+        VolDesc d{};
+        d.nx = p.nx;
+        d.ny = p.ny;
+        d.nz = p.nz;
+        d.pitch = (int)round_up(p.nx, 8);
+        d.off = off;
+        d.lambda_l1 = p.lambda_l1;
+        d.lambda_tv = p.lambda_tv;
+        d.mu = p.mu;
+        d.eps = p.eps;
+        d.eps_tv = p.eps_tv;
+        d.tau = 0.f;
+        d.plane_begin = plane;
+        ctx->vols_h.push_back(d);
+        for (int z = 0; z < p.nz; z++) ctx->plane_vol_h.push_back(j);
+        off += round_up((long long)d.pitch * d.ny * d.nz, 64);
+        plane += p.nz;
+    }
+    ctx->total = off;
+    ctx->nplanes = plane;
+
+    auto bail = [&](cudaError_t err, const char *what) {
+        std::string m = std::string("spg_create: ") + what + ": " + cudaGetErrorString(err);
+        spg_status s = err == cudaErrorMemoryAllocation ? SPG_ENOMEM : SPG_ECUDA;
+        cudaGetLastError();
+        free_all(ctx);
+        delete ctx;
+        return fail(nullptr, s, m);
+    };
+    const size_t vb = (size_t)ctx->total * 4, db = (size_t)ctx->total * ctx->data_es();
+    if ((e = dalloc(&ctx->vols_d, nvol * sizeof(VolDesc))) != cudaSuccess) return bail(e, "alloc");
+    if ((e = dalloc(&ctx->tmaps_d, nvol * sizeof(TmapSet))) != cudaSuccess) return bail(e, "alloc");
+    if ((e = dalloc(&ctx->plane_vol_d, plane * sizeof(int))) != cudaSuccess) return bail(e, "alloc");
+    for (int q = 0; q < 3; q++)
+        if ((e = dalloc(&ctx->X[q], vb)) != cudaSuccess) return bail(e, "alloc iterates");
+    if ((e = dalloc(&ctx->B, db)) != cudaSuccess) return bail(e, "alloc b");
+    if ((e = dalloc(&ctx->W, db)) != cudaSuccess) return bail(e, "alloc w");
+    if ((e = dalloc(&ctx->OM1, vb)) != cudaSuccess) return bail(e, "alloc om1");
+    if ((e = dalloc(&ctx->OMTV, vb)) != cudaSuccess) return bail(e, "alloc omtv");
+    if ((e = dalloc(&ctx->beta_d, ctx->max_iters * sizeof(float))) != cudaSuccess) return bail(e, "alloc beta");
+    if ((e = dalloc(&ctx->st_d, sizeof(DevState))) != cudaSuccess) return bail(e, "alloc state");
+    if ((e = dalloc(&ctx->hist_d, (size_t)ctx->hist_cap * nvol * 5 * sizeof(double))) != cudaSuccess)
+        return bail(e, "alloc history");
+    if ((e = dalloc(&ctx->plane_part_d, (size_t)plane * 4 * sizeof(double))) != cudaSuccess)
+        return bail(e, "alloc partials");
+    if ((e = dalloc(&ctx->vol_out_d, (size_t)nvol * 8 * sizeof(double))) != cudaSuccess) return bail(e, "alloc");
+    if ((e = dalloc(&ctx->maxw_d, (size_t)nvol * sizeof(double))) != cudaSuccess) return bail(e, "alloc");
+    if ((e = dalloc(&ctx->rstats_d, (size_t)nvol * 6 * sizeof(double))) != cudaSuccess) return bail(e, "alloc");
+
+    for (int q = 0; q < 3; q++) cudaMemsetAsync(ctx->X[q], 0, vb, ctx->stream);
+    cudaMemsetAsync(ctx->B, 0, db, ctx->stream);
+    cudaMemsetAsync(ctx->W, 0, db, ctx->stream);
+    cudaMemsetAsync(ctx->OM1, 0, vb, ctx->stream);
+    cudaMemsetAsync(ctx->OMTV, 0, vb, ctx->stream);
+    cudaMemsetAsync(ctx->st_d, 0, sizeof(DevState), ctx->stream);
+    cudaMemsetAsync(ctx->hist_d, 0, (size_t)ctx->hist_cap * nvol * 5 * sizeof(double), ctx->stream);
+    cudaMemsetAsync(ctx->rstats_d, 0, (size_t)nvol * 6 * sizeof(double), ctx->stream);
+    // extrapolation table, FP64 recurrence, stored as float32
+    std::vector<float> beta(ctx->max_iters);
+    double t = 1.0;
+    for (int k = 0; k < ctx->max_iters; k++) {
+        const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+        beta[k] = ctx->opt.momentum == SPG_ISTA ? 0.f : (float)((t - 1.0) / tn);
+        t = tn;
+    }
+    if ((e = cudaMemcpyAsync(ctx->beta_d, beta.data(), beta.size() * sizeof(float), cudaMemcpyHostToDevice,
+                             ctx->stream)) != cudaSuccess)
+        return bail(e, "upload beta");
+    if ((e = cudaMemcpyAsync(ctx->plane_vol_d, ctx->plane_vol_h.data(), plane * sizeof(int), cudaMemcpyHostToDevice,
+                             ctx->stream)) != cudaSuccess)
+        return bail(e, "upload plane map");
+    if ((e = cudaMemcpyAsync(ctx->vols_d, ctx->vols_h.data(), nvol * sizeof(VolDesc), cudaMemcpyHostToDevice,
+                             ctx->stream)) != cudaSuccess)
+        return bail(e, "upload descriptors");
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail(e, "synchronise");
+
+    const StepVariant v = ctx->opt.tile ? variant_from_tile(ctx->opt.tile, ctx->bf16()) : default_variant(ctx);
+    spg_status s = build_plan(ctx, v, ctx->opt.zchunk);
+    if (s != SPG_OK) {
+        std::string m = "spg_create: " + ctx->err;
+        free_all(ctx);
+        delete ctx;
+        return fail(nullptr, s, m);
+    }
+    *out = ctx;
+    return SPG_OK;
+}
+
+spg_status spg_create(const spg_volume_params *params, const spg_options *opt, void *stream, spg_ctx **out)
+{
+    return spg_create_batch(1, params, opt, stream, out);
+}
+
+spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg_dtype src)
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || !b || !w) return fail(ctx, SPG_EINVAL, "spg_set_data: bad arguments");
+    if (src != SPG_F32 && src != SPG_BF16) return fail(ctx, SPG_EINVAL, "spg_set_data: bad dtype");
+    const VolDesc &d = ctx->vols_h[vol];
+    const long long n = (long long)d.pitch * d.ny * d.nz;
+    const bool store_bf16 = ctx->bf16();
+    spg_status s;
+    if ((src == SPG_BF16) == store_bf16) {
+        if ((s = copy_volume_in(ctx, ctx->B, ctx->data_es(), d, b)) != SPG_OK) return s;
+        if ((s = copy_volume_in(ctx, ctx->W, ctx->data_es(), d, w)) != SPG_OK) return s;
+    } else {
+        // stage in the weight buffers (they are re-set by the next spg_reweight)
+        const size_t ses = src == SPG_BF16 ? 2 : 4;
+        if ((s = copy_volume_in(ctx, ctx->OM1, ses, d, b)) != SPG_OK) return s;
+        if ((s = copy_volume_in(ctx, ctx->OMTV, ses, d, w)) != SPG_OK) return s;
+        if (store_bf16) {
+            CK(launch_convert_to_bf16(ctx->OM1 + d.off, static_cast<uint16_t *>(ctx->B) + d.off, n, ctx->stream),
+               "convert b");
+            CK(launch_convert_to_bf16(ctx->OMTV + d.off, static_cast<uint16_t *>(ctx->W) + d.off, n, ctx->stream),
+               "convert w");
+        } else {
+            CK(launch_convert_to_f32(reinterpret_cast<const uint16_t *>(ctx->OM1) + d.off,
+                                     static_cast<float *>(ctx->B) + d.off, n, ctx->stream),
+               "convert b");
+            CK(launch_convert_to_f32(reinterpret_cast<const uint16_t *>(ctx->OMTV) + d.off,
+                                     static_cast<float *>(ctx->W) + d.off, n, ctx->stream),
+               "convert w");
+        }
+        ctx->reweighted = false;
+    }
+    ctx->launches += 1;
+    CK(launch_validate(aux_params(ctx), vol, d.nz, ctx->B, ctx->W, store_bf16, ctx->maxw_d, ctx->stream),
+       "validate");
+    double o[8];
+    CK(cudaMemcpyAsync(o, ctx->vol_out_d + (size_t)vol * 8, sizeof(o), cudaMemcpyDeviceToHost, ctx->stream),
+       "read validation");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    if (o[3] > 0) return fail(ctx, SPG_ENONFINITE, "spg_set_data: b has non-finite values");
+    if (o[2] > 0) return fail(ctx, SPG_EINVAL, "spg_set_data: w must be finite and > 0");
+    ctx->data_set[vol] = 1;
+    return SPG_OK;
+}
+
+spg_status spg_set_x(spg_ctx *ctx, int vol, const float *x)
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || !x) return fail(ctx, SPG_EINVAL, "spg_set_x: bad arguments");
+    const VolDesc &d = ctx->vols_h[vol];
+    const int c = ctx->cur();
+    spg_status s;
+    if ((s = copy_volume_in(ctx, ctx->X[c], 4, d, x)) != SPG_OK) return s;
+    if ((s = copy_volume_in(ctx, ctx->X[(c + 2) % 3], 4, d, x)) != SPG_OK) return s;
+    return SPG_OK;
+}
+
+spg_status spg_get_x(spg_ctx *ctx, int vol, float *x)
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || !x) return fail(ctx, SPG_EINVAL, "spg_get_x: bad arguments");
+    return copy_volume_out(ctx, x, ctx->X[ctx->cur()], 4, ctx->vols_h[vol]);
+}
+
+spg_status spg_reweight(spg_ctx *ctx)
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    for (int j = 0; j < ctx->nvol; j++)
+        if (!ctx->data_set[j]) return fail(ctx, SPG_ENOTREADY, "spg_reweight: data not set for every volume");
+    const float *xb[1] = {ctx->X[ctx->cur()]};
+    CK(launch_reweight(aux_params(ctx), xb, ctx->OM1, ctx->OMTV, ctx->maxw_d, ctx->rstats_d, ctx->vols_d, ctx->stream),
+       "reweight");
+    ctx->launches += 1;
+    ctx->k_round = 0;
+    ctx->reweighted = true;
+    return SPG_OK;
+}
+
+spg_status spg_iterate(spg_ctx *ctx, int k)
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (k < 0) return fail(ctx, SPG_EINVAL, "spg_iterate: negative count");
+    if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_iterate: call spg_reweight first");
+    if ((long long)ctx->k_round + k > ctx->max_iters)
+        return fail(ctx, SPG_EINVAL, "spg_iterate: round longer than max_iters_per_round");
+    spg_status s = launch_steps(ctx, k);
+    if (s != SPG_OK) return s;
+    ctx->k_round += k;
+    ctx->k_total += k;
+    return SPG_OK;
+}
+
+spg_status spg_objective(spg_ctx *ctx, int vol, double out[4])
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_objective: bad arguments");
+    if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_objective: weights not set (call spg_reweight)");
+    const float *xb[1] = {ctx->X[ctx->cur()]};
+    CK(launch_objective(aux_params(ctx), xb, ctx->B, ctx->W, ctx->bf16(), ctx->OM1, ctx->OMTV, ctx->stream),
+       "objective");
+    ctx->launches += 1;
+    double o[8];
+    CK(cudaMemcpyAsync(o, ctx->vol_out_d + (size_t)vol * 8, sizeof(o), cudaMemcpyDeviceToHost, ctx->stream),
+       "read objective");
+    spg_status s = device_status(ctx);
+    if (s != SPG_OK) return s;
+    for (int q = 0; q < 4; q++) out[q] = o[q];
+    if (!std::isfinite(o[3])) return fail(ctx, SPG_ENONFINITE, "non-finite objective");
+    return SPG_OK;
+}
+
+spg_status spg_history(spg_ctx *ctx, int vol, double *host, int max_entries, int *n)
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || !n || max_entries < 0 || (max_entries > 0 && !host))
+        return fail(ctx, SPG_EINVAL, "spg_history: bad arguments");
+    DevState st;
+    CK(cudaMemcpyAsync(&st, ctx->st_d, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream), "read state");
+    std::vector<double> ring((size_t)ctx->hist_cap * ctx->nvol * 5);
+    CK(cudaMemcpyAsync(ring.data(), ctx->hist_d, ring.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+       "read history");
+    spg_status s = device_status(ctx);
+    if (s != SPG_OK) return s;
+    const long long total = st.hist_count;
+    const long long avail = std::min<long long>(total, ctx->hist_cap);
+    const long long take = std::min<long long>(avail, max_entries);
+    for (long long i = 0; i < take; i++) {
+        const long long e = total - take + i;
+        const double *src = ring.data() + ((size_t)(e % ctx->hist_cap) * ctx->nvol + vol) * 5;
+        std::memcpy(host + i * 5, src, 5 * sizeof(double));
+    }
+    *n = (int)take;
+    return SPG_OK;
+}
+
+spg_status spg_round_stats(spg_ctx *ctx, int vol, double out[6])
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_round_stats: bad arguments");
+    CK(cudaMemcpyAsync(out, ctx->rstats_d + (size_t)vol * 6, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+       "read round stats");
+    return device_status(ctx);
+}
+
+spg_status spg_certificate(spg_ctx *ctx, int vol, double *out)
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_certificate: bad arguments");
+    if (!ctx->reweighted || ctx->k_round < 1)
+        return fail(ctx, SPG_ENOTREADY, "spg_certificate: needs one iteration in the current round");
+    const int c = ctx->cur();
+    const float *xb[3] = {ctx->X[c], ctx->X[(c + 2) % 3], ctx->X[(c + 1) % 3]};
+    CK(launch_certificate(aux_params(ctx), xb, ctx->beta_d, ctx->B, ctx->W, ctx->bf16(), ctx->OMTV, ctx->stream),
+       "certificate");
+    ctx->launches += 1;
+    double o[8];
+    CK(cudaMemcpyAsync(o, ctx->vol_out_d + (size_t)vol * 8, sizeof(o), cudaMemcpyDeviceToHost, ctx->stream),
+       "read certificate");
+    spg_status s = device_status(ctx);
+    if (s != SPG_OK) return s;
+    *out = o[4];
+    return SPG_OK;
+}
+
+spg_status spg_counters(spg_ctx *ctx, long long *k_total, int *k_round)
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (k_total) *k_total = ctx->k_total;
+    if (k_round) *k_round = ctx->k_round;
+    return SPG_OK;
+}
+
+// ---------------- checkpoint / resume ----------------
+
+spg_status spg_get_state(spg_ctx *ctx, void *blob, size_t *size)
+{
+    if (!ctx || !size) return fail(ctx, SPG_EINVAL, "spg_get_state: bad arguments");
+    size_t need = sizeof(StateHeader);
+    for (const auto &d : ctx->vols_h) need += 4 * (size_t)d.nx * d.ny * d.nz * 4 + sizeof(float) + 6 * sizeof(double);
+    if (!blob) {
+        *size = need;
+        return SPG_OK;
+    }
+    if (*size < need) return fail(ctx, SPG_EINVAL, "spg_get_state: buffer too small");
+    char *p = static_cast<char *>(blob);
+    StateHeader h{kStateMagic, 1, ctx->nvol, ctx->k_round, ctx->reweighted ? 1 : 0, ctx->k_total,
+                  (int32_t)ctx->opt.data_dtype, (int32_t)ctx->opt.momentum};
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    std::vector<VolDesc> dev(ctx->nvol);
+    CK(cudaMemcpyAsync(dev.data(), ctx->vols_d, ctx->nvol * sizeof(VolDesc), cudaMemcpyDeviceToHost, ctx->stream),
+       "read descriptors");
+    const int c = ctx->cur();
+    for (int j = 0; j < ctx->nvol; j++) {
+        const VolDesc &d = ctx->vols_h[j];
+        const size_t vb = (size_t)d.nx * d.ny * d.nz * 4;
+        spg_status s;
+        if ((s = copy_volume_out(ctx, p, ctx->X[c], 4, d)) != SPG_OK) return s;
+        p += vb;
+        if ((s = copy_volume_out(ctx, p, ctx->X[(c + 2) % 3], 4, d)) != SPG_OK) return s;
+        p += vb;
+        if ((s = copy_volume_out(ctx, p, ctx->OM1, 4, d)) != SPG_OK) return s;
+        p += vb;
+        if ((s = copy_volume_out(ctx, p, ctx->OMTV, 4, d)) != SPG_OK) return s;
+        p += vb;
+        CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+        std::memcpy(p, &dev[j].tau, sizeof(float));
+        p += sizeof(float);
+        CK(cudaMemcpyAsync(p, ctx->rstats_d + (size_t)j * 6, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+           "read stats");
+        p += 6 * sizeof(double);
+    }
+    return device_status(ctx);
+}
+
+spg_status spg_set_state(spg_ctx *ctx, const void *blob, size_t size)
+{
+    if (!ctx || !blob) return fail(ctx, SPG_EINVAL, "spg_set_state: bad arguments");
+    size_t need = 0;
+    spg_get_state(ctx, nullptr, &need);
+    if (size < need) return fail(ctx, SPG_EINVAL, "spg_set_state: blob too small");
+    const char *p = static_cast<const char *>(blob);
+    StateHeader h;
+    std::memcpy(&h, p, sizeof(h));
+    p += sizeof(h);
+    if (h.magic != kStateMagic || h.version != 1 || h.nvol != ctx->nvol || h.dtype != (int)ctx->opt.data_dtype ||
+        h.momentum != (int)ctx->opt.momentum)
+        return fail(ctx, SPG_EINVAL, "spg_set_state: blob does not match this context");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    // x_k goes to X[0], x_{k-1} to X[2]; the device state names X[0] as current
+    std::vector<VolDesc> dev(ctx->nvol);
+    CK(cudaMemcpy(dev.data(), ctx->vols_d, ctx->nvol * sizeof(VolDesc), cudaMemcpyDeviceToHost), "read descriptors");
+    for (int j = 0; j < ctx->nvol; j++) {
+        const VolDesc &d = ctx->vols_h[j];
+        const size_t vb = (size_t)d.nx * d.ny * d.nz * 4;
+        spg_status s;
+        if ((s = copy_volume_in(ctx, ctx->X[0], 4, d, p)) != SPG_OK) return s;
+        p += vb;
+        if ((s = copy_volume_in(ctx, ctx->X[2], 4, d, p)) != SPG_OK) return s;
+        p += vb;
+        if ((s = copy_volume_in(ctx, ctx->OM1, 4, d, p)) != SPG_OK) return s;
+        p += vb;
+        if ((s = copy_volume_in(ctx, ctx->OMTV, 4, d, p)) != SPG_OK) return s;
+        p += vb;
+        std::memcpy(&dev[j].tau, p, sizeof(float));
+        ctx->vols_h[j].tau = dev[j].tau;
+        p += sizeof(float);
+        CK(cudaMemcpyAsync(ctx->rstats_d + (size_t)j * 6, p, 6 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
+           "write stats");
+        CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+        p += 6 * sizeof(double);
+    }
+    CK(cudaMemcpy(ctx->vols_d, dev.data(), ctx->nvol * sizeof(VolDesc), cudaMemcpyHostToDevice), "write descriptors");
+    DevState st;
+    CK(cudaMemcpy(&st, ctx->st_d, sizeof(st), cudaMemcpyDeviceToHost), "read state");
+    st.cur = 0;
+    st.k_round = h.k_round;
+    st.k_total = h.k_total;
+    st.ticket = 0;
+    st.ticket_aux = 0;
+    st.err = 0;
+    CK(cudaMemcpy(ctx->st_d, &st, sizeof(st), cudaMemcpyHostToDevice), "write state");
+    ctx->k_round = h.k_round;
+    ctx->k_total = h.k_total;
+    ctx->cur0 = (int)(((-h.k_total) % 3 + 3) % 3);
+    ctx->reweighted = h.reweighted != 0;
+    return SPG_OK;
+}
+
+// ---------------- unrolled forward and adjoint (single volume) ----------------
+
+spg_status spg_unrolled(spg_ctx *ctx, int K, float *xK)
+{
+    if (!ctx || !xK || K < 0) return fail(ctx, SPG_EINVAL, "spg_unrolled: bad arguments");
+    if (ctx->nvol != 1) return fail(ctx, SPG_EINVAL, "spg_unrolled: single-volume contexts only");
+    if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_unrolled: call spg_reweight first");
+    const VolDesc &d = ctx->vols_h[0];
+    const size_t vb = (size_t)ctx->total * 4;
+    Scratch sc;
+    float *buf[3];
+    for (int q = 0; q < 3; q++) CK(sc.get(&buf[q], vb), "alloc");
+    CK(cudaMemcpyAsync(buf[0], ctx->X[ctx->cur()], vb, cudaMemcpyDeviceToDevice, ctx->stream), "copy x0");
+    CK(cudaMemcpyAsync(buf[2], buf[0], vb, cudaMemcpyDeviceToDevice, ctx->stream), "copy x0");
+    const auto beta = beta_table_host(ctx, K);
+    int c = 0;
+    for (int k = 0; k < K; k++) {
+        CK(launch_plain_step(ctx->vols_d, d.nz, buf[c], buf[(c + 2) % 3], beta[k], ctx->B, ctx->W, ctx->bf16(),
+                             ctx->OM1, ctx->OMTV, buf[(c + 1) % 3], ctx->stream),
+           "plain step");
+        ctx->launches += 1;
+        c = (c + 1) % 3;
+    }
+    spg_status s = copy_volume_out(ctx, xK, buf[c], 4, d);
+    if (s != SPG_OK) return s;
+    return device_status(ctx);
+}
+
+spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *gw, double g_scalars[2],
+                        int ckpt_every)
+{
+    if (!ctx || !gx || !gb || !gw || !g_scalars || K < 1) return fail(ctx, SPG_EINVAL, "spg_backward: bad arguments");
+    if (ctx->nvol != 1) return fail(ctx, SPG_EINVAL, "spg_backward: single-volume contexts only");
+    if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_backward: call spg_reweight first");
+    const int C = ckpt_every > 0 ? ckpt_every : 10;
+    const VolDesc &d = ctx->vols_h[0];
+    const size_t vb = (size_t)ctx->total * 4;
+    const int nck = (K + C - 1) / C;  // checkpoints at k = 0, C, 2C, ... (< K)
+    Scratch sc;
+    float *ck = nullptr, *seg = nullptr, *ga[3], *m = nullptr, *accb = nullptr, *accw = nullptr;
+    double *pp = nullptr;
+    CK(sc.get(&ck, vb * 2 * nck), "alloc checkpoints");
+    CK(sc.get(&seg, vb * (C + 2)), "alloc segment");
+    for (int q = 0; q < 3; q++) CK(sc.get(&ga[q], vb), "alloc adjoint");
+    CK(sc.get(&m, vb), "alloc");
+    CK(sc.get(&accb, vb), "alloc");
+    CK(sc.get(&accw, vb), "alloc");
+    CK(sc.get(&pp, (size_t)K * d.nz * 4 * sizeof(double)), "alloc scalar partials");
+    const auto beta = beta_table_host(ctx, K);
+    auto vol_at = [&](float *base, int i) { return base + (size_t)i * ctx->total; };
+
+    // forward sweep, keeping (x_k, x_{k-1}) at every checkpoint
+    {
+        float *b3[3];
+        for (int q = 0; q < 3; q++) b3[q] = vol_at(seg, q);
+        CK(cudaMemcpyAsync(b3[0], ctx->X[ctx->cur()], vb, cudaMemcpyDeviceToDevice, ctx->stream), "copy x0");
+        CK(cudaMemcpyAsync(b3[2], b3[0], vb, cudaMemcpyDeviceToDevice, ctx->stream), "copy x0");
+        int c = 0;
+        for (int k = 0; k < K; k++) {
+            if (k % C == 0) {
+                CK(cudaMemcpyAsync(vol_at(ck, 2 * (k / C)), b3[c], vb, cudaMemcpyDeviceToDevice, ctx->stream), "ckpt");
+                CK(cudaMemcpyAsync(vol_at(ck, 2 * (k / C) + 1), b3[(c + 2) % 3], vb, cudaMemcpyDeviceToDevice,
+                                   ctx->stream),
+                   "ckpt");
+            }
+            CK(launch_plain_step(ctx->vols_d, d.nz, b3[c], b3[(c + 2) % 3], beta[k], ctx->B, ctx->W, ctx->bf16(),
+                                 ctx->OM1, ctx->OMTV, b3[(c + 1) % 3], ctx->stream),
+               "plain step");
+            ctx->launches += 1;
+            c = (c + 1) % 3;
+        }
+    }
+    // adjoint sweep
+    CK(cudaMemsetAsync(accb, 0, vb, ctx->stream), "memset");
+    CK(cudaMemsetAsync(accw, 0, vb, ctx->stream), "memset");
+    CK(cudaMemsetAsync(ga[0], 0, vb, ctx->stream), "memset");
+    CK(cudaMemsetAsync(ga[1], 0, vb, ctx->stream), "memset");
+    CK(cudaMemsetAsync(ga[2], 0, vb, ctx->stream), "memset");
+    spg_status s = copy_volume_in(ctx, ga[0], 4, d, gx);  // ga[0] = dL/dx_K
+    if (s != SPG_OK) return s;
+    int inext = 0, icur = 1, iprev = 2;
+    for (int sgm = nck - 1; sgm >= 0; sgm--) {
+        const int k0 = sgm * C, k1 = std::min(K, k0 + C);
+        // seg[0] = x_{k0-1}, seg[1] = x_{k0}, seg[i+1] = x_{k0+i}
+        CK(cudaMemcpyAsync(vol_at(seg, 0), vol_at(ck, 2 * sgm + 1), vb, cudaMemcpyDeviceToDevice, ctx->stream), "rst");
+        CK(cudaMemcpyAsync(vol_at(seg, 1), vol_at(ck, 2 * sgm), vb, cudaMemcpyDeviceToDevice, ctx->stream), "rst");
+        for (int k = k0; k < k1 - 1; k++) {
+            const int i = k - k0 + 1;
+            CK(launch_plain_step(ctx->vols_d, d.nz, vol_at(seg, i), vol_at(seg, i - 1), beta[k], ctx->B, ctx->W,
+                                 ctx->bf16(), ctx->OM1, ctx->OMTV, vol_at(seg, i + 1), ctx->stream),
+               "recompute");
+            ctx->launches += 1;
+        }
+        for (int k = k1 - 1; k >= k0; k--) {
+            const int i = k - k0 + 1;
+            AdjParams a;
+            a.vols = ctx->vols_d;
+            a.nplanes = d.nz;
+            a.xk = vol_at(seg, i);
+            a.xkm1 = vol_at(seg, i - 1);
+            a.beta = beta[k];
+            a.b = ctx->B;
+            a.w = ctx->W;
+            a.bf16 = ctx->bf16();
+            a.om1 = ctx->OM1;
+            a.omtv = ctx->OMTV;
+            a.gnext = ga[inext];
+            a.m = m;
+            a.gcur = ga[icur];
+            // x_{-1} = x_0: the k = 0 step's extrapolation cotangent folds into dL/dx_0
+            a.gprev = k >= 1 ? ga[iprev] : ga[icur];
+            a.gb = accb;
+            a.gw = accw;
+            a.plane_part = pp + (size_t)k * d.nz * 4;
+            CK(launch_adjoint_mask(a, ctx->stream), "adjoint mask");
+            CK(launch_adjoint_apply(a, ctx->stream), "adjoint apply");
+            ctx->launches += 2;
+            // rotate: dL/dx_k is complete; the old dL/dx_{k+1} buffer becomes dL/dx_{k-2}
+            const int t = inext;
+            inext = icur;
+            icur = iprev;
+            iprev = t;
+            CK(cudaMemsetAsync(ga[iprev], 0, vb, ctx->stream), "memset");
+        }
+    }
+    if ((s = copy_volume_out(ctx, gb, accb, 4, d)) != SPG_OK) return s;
+    if ((s = copy_volume_out(ctx, gw, accw, 4, d)) != SPG_OK) return s;
+    std::vector<double> hp((size_t)K * d.nz * 4);
+    CK(cudaMemcpyAsync(hp.data(), pp, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "read");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    double s1 = 0, s2 = 0;
+    for (int k = K - 1; k >= 0; k--)
+        for (int z = 0; z < d.nz; z++) {
+            s1 += hp[((size_t)k * d.nz + z) * 4 + 0];
+            s2 += hp[((size_t)k * d.nz + z) * 4 + 1];
+        }
+    g_scalars[0] = s1;
+    g_scalars[1] = s2;
+    return device_status(ctx);
+}
+
+spg_status spg_probe_timeout(spg_ctx *ctx, long long timeout_ns)
+{
+    if (!ctx || timeout_ns <= 0 || timeout_ns > kTimeoutNs) return fail(ctx, SPG_EINVAL, "spg_probe_timeout: bad arguments");
+    CK(launch_timeout_probe(ctx->st_d, timeout_ns, ctx->stream), "timeout probe");
+    ctx->launches += 1;
+    return device_status(ctx);
+}
+
+long long spg_launch_count(const spg_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+spg_status spg_plan_info(const spg_ctx *ctx, int info[6])
+{
+    if (!ctx || !info) return SPG_EINVAL;
+    info[0] = 32 * ctx->var.vx;
+    info[1] = ctx->var.ty;
+    info[2] = ctx->zchunk;
+    info[3] = ctx->nitems;
+    info[4] = ctx->grid;
+    info[5] = ctx->ctas_per_sm;
+    return SPG_OK;
+}
+
+const char *spg_last_error(const spg_ctx *ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
+
+void spg_destroy(spg_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,567 @@
+// Auxiliary kernels of the GB300 SPG solver: input validation and dtype
+// conversion, the re-weighting pass (Eq. 11), the objective (Eq. 14 / 31),
+// the strong-convexity certificate, a plain (untiled) step used to recompute
+// forward iterates, and the two passes of the adjoint of one step.
+//
+// All of them run once per round or less, so they use plain global loads;
+// every reduction keeps one partial per z-plane (one CTA per plane) and the
+// last CTA to finish sums the partials of each volume in plane order, so the
+// results are deterministic. No kernel here waits on another CTA.
+#include <cuda_bf16.h>
+
+#include "spg_internal.h"
+
+namespace spg {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int AUX_THREADS = 256;
+
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        float y = v - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+__device__ __forceinline__ float ld_data(const void *p, bool bf16, long long i)
+{
+    if (bf16) return __uint_as_float(((uint32_t) reinterpret_cast<const uint16_t *>(p)[i]) << 16);
+    return reinterpret_cast<const float *>(p)[i];
+}
+
+// Block-wide sum of up to 4 doubles in a fixed order; result valid in thread 0.
+template <int N>
+__device__ void block_sum(double (&v)[N], double *scratch /* 32*N */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < N; q++) v[q] += __shfl_down_sync(FULL, v[q], o);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < N; q++) scratch[warp * N + q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x / 32;
+        for (int q = 0; q < N; q++) {
+            double a = 0;
+            for (int k = 0; k < nw; k++) a += scratch[k * N + q];
+            v[q] = a;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double block_max(double v, double *scratch)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(FULL, v, o));
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x / 32;
+        for (int k = 0; k < nw; k++) v = fmax(v, scratch[k]);
+    }
+    __syncthreads();
+    return v;
+}
+
+// Last-CTA election on a counter; returns true in every thread of the last CTA.
+__device__ bool last_block(unsigned int *ticket, int *flag_smem)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        *flag_smem = (t == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    const bool last = *flag_smem != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+// ---------------- validation ----------------
+// One CTA per z-plane of volume `vol`: max w, min w, count(w <= 0 or w not
+// finite), count(b not finite).
+__global__ void validate_kernel(AuxParams a, int vol, const void *b, const void *w, bool bf16, double *maxw_out)
+{
+    __shared__ double scratch[32 * 4];
+    __shared__ int flag;
+    const VolDesc V = a.vols[vol];
+    const int z = blockIdx.x;
+    double mx = 0.0, mn = INFINITY;
+    double bad_w = 0, bad_b = 0;
+    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
+        const int x = t % V.nx, y = t / V.nx;
+        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+        const float wv = ld_data(w, bf16, i), bv = ld_data(b, bf16, i);
+        if (!(wv > 0.f) || !isfinite(wv)) bad_w += 1;
+        if (!isfinite(bv)) bad_b += 1;
+        if (isfinite(wv)) {
+            mx = fmax(mx, (double)wv);
+            mn = fmin(mn, (double)wv);
+        }
+    }
+    mx = block_max(mx, scratch);
+    const double nmn = block_max(-mn, scratch);
+    double c[2] = {bad_w, bad_b};
+    block_sum<2>(c, scratch);
+    if (threadIdx.x == 0) {
+        double *pp = a.plane_part + (long long)z * 4;
+        pp[0] = mx;
+        pp[1] = -nmn;
+        pp[2] = c[0];
+        pp[3] = c[1];
+    }
+    if (!last_block(&a.st->ticket_aux, &flag)) return;
+    if (threadIdx.x == 0) {
+        double m = 0, n = INFINITY, bw = 0, bb = 0;
+        for (int q = 0; q < V.nz; q++) {
+            const double *pp = a.plane_part + (long long)q * 4;
+            m = fmax(m, __ldcg(pp + 0));
+            n = fmin(n, __ldcg(pp + 1));
+            bw += __ldcg(pp + 2);
+            bb += __ldcg(pp + 3);
+        }
+        double *o = a.vol_out + (long long)vol * 8;
+        o[0] = m;
+        o[1] = n;
+        o[2] = bw;
+        o[3] = bb;
+        maxw_out[vol] = m;
+        a.st->ticket_aux = 0;
+        __threadfence();
+    }
+}
+
+__global__ void to_bf16_kernel(const float *src, uint16_t *dst, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        __nv_bfloat16 h = __float2bfloat16_rn(src[i]);
+        dst[i] = *reinterpret_cast<uint16_t *>(&h);
+    }
+}
+
+__global__ void to_f32_kernel(const uint16_t *src, float *dst, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = __uint_as_float(((uint32_t)src[i]) << 16);
+}
+
+// ---------------- stencil helpers (plain global loads) ----------------
+
+// Value of u = x_k + beta (x_k - x_{k-1}) is never formed; differences are
+// taken of x_k and of d = x_k - x_{k-1} separately (one rounding each).
+struct Field {
+    const float *xk, *xkm1;   // xkm1 may be null (then d = 0)
+    float beta;
+    __device__ __forceinline__ float x(long long i) const { return xk[i]; }
+    __device__ __forceinline__ float d(long long i) const { return xkm1 ? xk[i] - xkm1[i] : 0.f; }
+};
+
+// D u at (x, y, z) in volume V (Eq. 12, zero first planes).
+__device__ __forceinline__ void grad_at(const VolDesc &V, const Field &F, int x, int y, int z, float g[3])
+{
+    const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+    const float xc = F.x(i), dc = F.d(i);
+    g[0] = x >= 1 ? (xc - F.x(i - 1)) + F.beta * (dc - F.d(i - 1)) : 0.f;
+    g[1] = y >= 1 ? (xc - F.x(i - V.pitch)) + F.beta * (dc - F.d(i - V.pitch)) : 0.f;
+    const long long ps = (long long)V.pitch * V.ny;
+    g[2] = z >= 1 ? (xc - F.x(i - ps)) + F.beta * (dc - F.d(i - ps)) : 0.f;
+}
+
+// p = omtv * D u / max(mu, |D u|) at (x, y, z); zero outside the volume.
+__device__ __forceinline__ void p_at(const VolDesc &V, const Field &F, const float *omtv, int x, int y, int z,
+                                     float p[3])
+{
+    if (x < 0 || y < 0 || z < 0 || x >= V.nx || y >= V.ny || z >= V.nz) {
+        p[0] = p[1] = p[2] = 0.f;
+        return;
+    }
+    float g[3];
+    grad_at(V, F, x, y, z, g);
+    const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+    const float s2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    const float sc = omtv[i] * fminf(1.0f / V.mu, rsqrtf(s2));
+    p[0] = g[0] * sc;
+    p[1] = g[1] * sc;
+    p[2] = g[2] * sc;
+}
+
+// (D^T p)(x, y, z) with p evaluated on the fly (Eq. 17).
+__device__ __forceinline__ float div_at(const VolDesc &V, const Field &F, const float *omtv, int x, int y, int z)
+{
+    float pc[3], px[3], pyv[3], pz[3];
+    p_at(V, F, omtv, x, y, z, pc);
+    p_at(V, F, omtv, x + 1, y, z, px);
+    p_at(V, F, omtv, x, y + 1, z, pyv);
+    p_at(V, F, omtv, x, y, z + 1, pz);
+    return (pc[0] - px[0]) + (pc[1] - pyv[1]) + (pc[2] - pz[2]);
+}
+
+// ---------------- re-weighting (Eq. 11, eps scaling of Sec. 2.5) ----------------
+__global__ void reweight_kernel(AuxParams a, const float *xcur, float *om1, float *omtv, const double *maxw,
+                                double *rstats, VolDesc *vols_rw)
+{
+    __shared__ double scratch[32 * 4];
+    __shared__ int flag;
+    const int plane = blockIdx.x;
+    const int vol = a.plane_vol[plane];
+    const VolDesc V = a.vols[vol];
+    const int z = plane - V.plane_begin;
+    const Field F{xcur, nullptr, 0.f};
+    double mx = 0.0;
+    KSum c1, c2;
+    float nnz = 0.f;
+    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
+        const int x = t % V.nx, y = t / V.nx;
+        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+        float g[3];
+        grad_at(V, F, x, y, z, g);
+        const float gn = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        const float xv = xcur[i];
+        const float o1 = V.eps / (fabsf(xv) + V.eps);
+        const float ot = V.eps_tv / (gn + V.eps_tv);
+        om1[i] = o1;
+        omtv[i] = ot;
+        mx = fmax(mx, (double)ot);
+        nnz += xv != 0.f ? 1.f : 0.f;
+        c1.add(o1);
+        c2.add(ot);
+    }
+    mx = block_max(mx, scratch);
+    double s[3] = {(double)nnz, c1.value(), c2.value()};
+    block_sum<3>(s, scratch);
+    if (threadIdx.x == 0) {
+        double *pp = a.plane_part + (long long)plane * 4;
+        pp[0] = mx;
+        pp[1] = s[0];
+        pp[2] = s[1];
+        pp[3] = s[2];
+    }
+    if (!last_block(&a.st->ticket_aux, &flag)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int v = warp; v < a.nvol; v += blockDim.x / 32) {
+        const VolDesc W = a.vols[v];
+        double m = 0, n = 0, s1 = 0, s2 = 0;
+        if (lane == 0) {
+            for (int q = W.plane_begin; q < W.plane_begin + W.nz; q++) {
+                const double *pp = a.plane_part + (long long)q * 4;
+                m = fmax(m, __ldcg(pp + 0));
+                n += __ldcg(pp + 1);
+                s1 += __ldcg(pp + 2);
+                s2 += __ldcg(pp + 3);
+            }
+            const double L = maxw[v] + 12.0 * (double)W.lambda_tv * m / (double)W.mu;
+            const double tau = 1.0 / L;
+            double *o = rstats + (long long)v * 6;
+            o[0] = m;
+            o[1] = n;
+            o[2] = s1;
+            o[3] = s2;
+            o[4] = L;
+            o[5] = tau;
+            vols_rw[v].tau = (float)tau;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.st->k_round = 0;
+        a.st->ticket_aux = 0;
+        __threadfence();
+    }
+}
+
+// ---------------- objective F(x) at the current iterate ----------------
+__global__ void objective_kernel(AuxParams a, const float *xcur, const void *b, const void *w, bool bf16,
+                                 const float *om1, const float *omtv)
+{
+    __shared__ double scratch[32 * 4];
+    __shared__ int flag;
+    const int plane = blockIdx.x;
+    const int vol = a.plane_vol[plane];
+    const VolDesc V = a.vols[vol];
+    const int z = plane - V.plane_begin;
+    const Field F{xcur, nullptr, 0.f};
+    KSum kd, kl, kt;
+    const float mu = V.mu;
+    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
+        const int x = t % V.nx, y = t / V.nx;
+        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+        float g[3];
+        grad_at(V, F, x, y, z, g);
+        const float q = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        const float h = q <= mu * mu ? q * (0.5f / mu) : sqrtf(q) - 0.5f * mu;
+        const float xv = xcur[i];
+        const float r = xv - ld_data(b, bf16, i);
+        kd.add(0.5f * ld_data(w, bf16, i) * r * r);
+        kl.add(om1[i] * fabsf(xv));
+        kt.add(omtv[i] * h);
+    }
+    double s[3] = {kd.value(), kl.value(), kt.value()};
+    block_sum<3>(s, scratch);
+    if (threadIdx.x == 0) {
+        double *pp = a.plane_part + (long long)plane * 4;
+        pp[0] = s[0];
+        pp[1] = s[1];
+        pp[2] = s[2];
+        pp[3] = 0;
+    }
+    if (!last_block(&a.st->ticket_aux, &flag)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int v = warp; v < a.nvol; v += blockDim.x / 32) {
+        if (lane != 0) continue;
+        const VolDesc W = a.vols[v];
+        double d = 0, l = 0, t = 0;
+        for (int q = W.plane_begin; q < W.plane_begin + W.nz; q++) {
+            const double *pp = a.plane_part + (long long)q * 4;
+            d += __ldcg(pp + 0);
+            l += __ldcg(pp + 1);
+            t += __ldcg(pp + 2);
+        }
+        double *o = a.vol_out + (long long)v * 8;
+        o[0] = d;
+        o[1] = (double)W.lambda_l1 * l;
+        o[2] = (double)W.lambda_tv * t;
+        o[3] = o[0] + o[1] + o[2];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.st->ticket_aux = 0;
+        __threadfence();
+    }
+}
+
+// ---------------- certificate |r|^2 of the last step ----------------
+// r = grad f(x+) - grad f(y) + (y - x+)/tau
+//   = (y - x+)(1/tau - w) + lambda_tv (D^T p(x+) - D^T p(y)),  y - x+ = (x_k - x+) + beta d.
+__global__ void certificate_kernel(AuxParams a, const float *xplus, const float *xk, const float *xkm1,
+                                   const float *beta_tab, const void *b, const void *w, bool bf16,
+                                   const float *omtv)
+{
+    __shared__ double scratch[32 * 4];
+    __shared__ int flag;
+    const int plane = blockIdx.x;
+    const int vol = a.plane_vol[plane];
+    const VolDesc V = a.vols[vol];
+    const int z = plane - V.plane_begin;
+    const int kr = a.st->k_round;
+    const float beta = kr >= 1 ? beta_tab[kr - 1] : 0.f;
+    const Field Fy{xk, xkm1, beta};
+    const Field Fx{xplus, nullptr, 0.f};
+    (void)b;
+    KSum ks;
+    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
+        const int x = t % V.nx, y = t / V.nx;
+        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+        const float dy = (xk[i] - xplus[i]) + beta * (xk[i] - xkm1[i]);
+        const float dv = div_at(V, Fx, omtv, x, y, z) - div_at(V, Fy, omtv, x, y, z);
+        const float r = dy * (1.0f / V.tau - ld_data(w, bf16, i)) + V.lambda_tv * dv;
+        ks.add(r * r);
+    }
+    double s[1] = {ks.value()};
+    block_sum<1>(s, scratch);
+    if (threadIdx.x == 0) a.plane_part[(long long)plane * 4] = s[0];
+    if (!last_block(&a.st->ticket_aux, &flag)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int v = warp; v < a.nvol; v += blockDim.x / 32) {
+        if (lane != 0) continue;
+        const VolDesc W = a.vols[v];
+        double acc = 0;
+        for (int q = W.plane_begin; q < W.plane_begin + W.nz; q++) acc += __ldcg(a.plane_part + (long long)q * 4);
+        a.vol_out[(long long)v * 8 + 4] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.st->ticket_aux = 0;
+        __threadfence();
+    }
+}
+
+// ---------------- plain step (forward recomputation for the adjoint) ----------------
+__global__ void plain_step_kernel(const VolDesc *vols, const float *xk, const float *xkm1, float beta,
+                                  const void *b, const void *w, bool bf16, const float *om1, const float *omtv,
+                                  float *xout)
+{
+    const VolDesc V = vols[0];
+    const int z = blockIdx.x;
+    const Field F{xk, xkm1, beta};
+    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
+        const int x = t % V.nx, y = t / V.nx;
+        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+        const float d = xk[i] - xkm1[i];
+        const float g = ld_data(w, bf16, i) * ((xk[i] - ld_data(b, bf16, i)) + beta * d) +
+                        V.lambda_tv * div_at(V, F, omtv, x, y, z);
+        const float delta = beta * d - V.tau * g;
+        const float zz = xk[i] + delta;
+        const float th = V.tau * V.lambda_l1 * om1[i];
+        xout[i] = fabsf(zz) < th ? 0.f : xk[i] + (zz > 0.f ? delta - th : delta + th);
+    }
+}
+
+// ---------------- adjoint of one step ----------------
+// Pass 1: m = gnext * [soft-threshold passes], the l1 and TV scalar partials,
+// gb += tau w m, gw += -tau (y - b) m.
+__global__ void adjoint_mask_kernel(AdjParams a)
+{
+    __shared__ double scratch[32 * 4];
+    const VolDesc V = a.vols[0];
+    const int z = blockIdx.x;
+    const Field F{a.xk, a.xkm1, a.beta};
+    KSum k1, k2;
+    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
+        const int x = t % V.nx, y = t / V.nx;
+        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+        const float d = a.xk[i] - a.xkm1[i];
+        const float bv = ld_data(a.b, a.bf16, i), wv = ld_data(a.w, a.bf16, i);
+        const float tvg = div_at(V, F, a.omtv, x, y, z);
+        const float g = wv * ((a.xk[i] - bv) + a.beta * d) + V.lambda_tv * tvg;
+        const float delta = a.beta * d - V.tau * g;
+        const float zz = a.xk[i] + delta;
+        const float th = V.tau * V.lambda_l1 * a.om1[i];
+        const bool pass = fabsf(zz) > th || th <= 0.f;
+        const float m = pass ? a.gnext[i] : 0.f;
+        a.m[i] = m;
+        const float sg = zz > 0.f ? 1.f : (zz < 0.f ? -1.f : 0.f);
+        k1.add(-V.tau * a.om1[i] * sg * m);
+        k2.add(-V.tau * tvg * m);
+        a.gb[i] += V.tau * wv * m;
+        a.gw[i] += -V.tau * ((a.xk[i] - bv) + a.beta * d) * m;
+    }
+    double s[2] = {k1.value(), k2.value()};
+    block_sum<2>(s, scratch);
+    if (threadIdx.x == 0) {
+        a.plane_part[(long long)z * 4 + 0] = s[0];
+        a.plane_part[(long long)z * 4 + 1] = s[1];
+    }
+}
+
+// omtv * H_mu(D y) (D m) at (x, y, z), zero outside; H_mu = I/mu inside the
+// smoothing ball, (I - e e^T)/|Dy| outside (the Hessian of Eq. 14).
+__device__ __forceinline__ void hv_at(const VolDesc &V, const Field &F, const float *m, const float *omtv, int x,
+                                      int y, int z, float h[3])
+{
+    if (x < 0 || y < 0 || z < 0 || x >= V.nx || y >= V.ny || z >= V.nz) {
+        h[0] = h[1] = h[2] = 0.f;
+        return;
+    }
+    float g[3];
+    grad_at(V, F, x, y, z, g);
+    const Field M{m, nullptr, 0.f};
+    float q[3];
+    grad_at(V, M, x, y, z, q);
+    const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+    const float s = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    const float om = omtv[i];
+    if (s <= V.mu) {
+        const float c = om / V.mu;
+        h[0] = q[0] * c;
+        h[1] = q[1] * c;
+        h[2] = q[2] * c;
+    } else {
+        const float inv = 1.0f / s;
+        const float e0 = g[0] * inv, e1 = g[1] * inv, e2 = g[2] * inv;
+        const float eq = e0 * q[0] + e1 * q[1] + e2 * q[2];
+        const float c = om * inv;
+        h[0] = (q[0] - e0 * eq) * c;
+        h[1] = (q[1] - e1 * eq) * c;
+        h[2] = (q[2] - e2 * eq) * c;
+    }
+}
+
+// Pass 2: ybar = m - tau (w m + lambda_tv D^T(omtv H Dm)); gcur += (1+beta) ybar,
+// gprev += -beta ybar.
+__global__ void adjoint_apply_kernel(AdjParams a)
+{
+    const VolDesc V = a.vols[0];
+    const int z = blockIdx.x;
+    const Field F{a.xk, a.xkm1, a.beta};
+    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
+        const int x = t % V.nx, y = t / V.nx;
+        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+        float hc[3], hx[3], hy[3], hz[3];
+        hv_at(V, F, a.m, a.omtv, x, y, z, hc);
+        hv_at(V, F, a.m, a.omtv, x + 1, y, z, hx);
+        hv_at(V, F, a.m, a.omtv, x, y + 1, z, hy);
+        hv_at(V, F, a.m, a.omtv, x, y, z + 1, hz);
+        const float dtv = (hc[0] - hx[0]) + (hc[1] - hy[1]) + (hc[2] - hz[2]);
+        const float mv = a.m[i];
+        const float ybar = mv - V.tau * (ld_data(a.w, a.bf16, i) * mv + V.lambda_tv * dtv);
+        a.gcur[i] += (1.f + a.beta) * ybar;
+        a.gprev[i] += -a.beta * ybar;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_validate(const AuxParams &a, int vol, int nz, const void *b, const void *w, bool bf16,
+                            double *maxw_out, cudaStream_t s)
+{
+    validate_kernel<<<nz, AUX_THREADS, 0, s>>>(a, vol, b, w, bf16, maxw_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_to_bf16(const float *src, uint16_t *dst, long long n, cudaStream_t s)
+{
+    to_bf16_kernel<<<1024, 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_to_f32(const uint16_t *src, float *dst, long long n, cudaStream_t s)
+{
+    to_f32_kernel<<<1024, 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reweight(const AuxParams &a, const float *const *xbuf, float *om1, float *omtv,
+                            const double *maxw, double *rstats, VolDesc *vols_rw, cudaStream_t s)
+{
+    reweight_kernel<<<a.nplanes, AUX_THREADS, 0, s>>>(a, xbuf[0], om1, omtv, maxw, rstats, vols_rw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective(const AuxParams &a, const float *const *xbuf, const void *b, const void *w,
+                             bool bf16, const float *om1, const float *omtv, cudaStream_t s)
+{
+    objective_kernel<<<a.nplanes, AUX_THREADS, 0, s>>>(a, xbuf[0], b, w, bf16, om1, omtv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_certificate(const AuxParams &a, const float *const *xbuf, const float *beta, const void *b,
+                               const void *w, bool bf16, const float *omtv, cudaStream_t s)
+{
+    // xbuf = {x_{k+1}, x_k, x_{k-1}}
+    certificate_kernel<<<a.nplanes, AUX_THREADS, 0, s>>>(a, xbuf[0], xbuf[1], xbuf[2], beta, b, w, bf16, omtv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_step(const VolDesc *vols, int nplanes, const float *xk, const float *xkm1, float beta,
+                              const void *b, const void *w, bool bf16, const float *om1, const float *omtv,
+                              float *xout, cudaStream_t s)
+{
+    plain_step_kernel<<<nplanes, AUX_THREADS, 0, s>>>(vols, xk, xkm1, beta, b, w, bf16, om1, omtv, xout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_mask(const AdjParams &a, cudaStream_t s)
+{
+    adjoint_mask_kernel<<<a.nplanes, AUX_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_apply(const AdjParams &a, cudaStream_t s)
+{
+    adjoint_apply_kernel<<<a.nplanes, AUX_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace spg

@@ -1,0 +1,131 @@
+// Internal layout shared by the host side (spg_api.cu) and the kernels
+// (spg_step.cu, spg_aux.cu) of the GB300 reweighted SPG solver.
+//
+// Device layout of a context with V volumes:
+//  - every volume-shaped array is one flat allocation holding all V volumes
+//    back to back; volume j starts at element VolDesc::off (a multiple of 64
+//    elements, so every volume starts on a 256-byte boundary);
+//  - inside a volume, rows of nx elements are padded to `pitch` elements
+//    (a multiple of 8: 32-byte rows for float32, 16-byte for bfloat16), the
+//    layout the TMA tensor maps and the 16-byte vector stores need;
+//  - X[0..2] rotate as x_{k-1}, x_k, x_{k+1}; DevState::cur names x_k.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spg.h"
+
+namespace spg {
+
+struct VolDesc {
+    int nx, ny, nz, pitch;
+    long long off;           // element offset of the volume in every flat array
+    float lambda_l1, lambda_tv, mu, eps, eps_tv;
+    float tau;               // 1/L of the current round (written by the re-weighting kernel)
+    int item_begin, item_end;    // work items of the fused step that belong to this volume
+    int plane_begin;             // index of the volume's first z-plane among all planes
+    int pad0;
+};
+
+// One work item of the fused step: an x-y tile [x0, x0+TX) x [y0, y0+TY) of
+// volume `vol`, marching over the z-planes [z0, z1).
+struct WorkItem {
+    int vol, x0, y0, z0, z1, pad0, pad1, pad2;
+};
+
+// Tensor maps of one volume (device memory, 64-byte aligned).
+struct TmapSet {
+    CUtensorMap x[3];   // iterate buffers, box (TX+8) x (TY+2) x 1, origin (x0-4, y0-1, z)
+    CUtensorMap omtv;   // TV weights,      box (TX+4) x (TY+1) x 1, origin (x0, y0, z)
+    CUtensorMap b, w;   // data and weight, box TX x TY x 1,         origin (x0, y0, z-1)
+    CUtensorMap om1;    // l1 weights,      box TX x TY x 1
+    CUtensorMap spare;
+};
+
+// Device-resident solver state; the last CTA of each fused step advances it,
+// so the same launch (or captured graph node) serves every iteration.
+struct DevState {
+    int cur;                 // buffer holding x_k
+    int k_round;             // iterations done in the current round
+    long long k_total;       // iterations since creation
+    unsigned int ticket;     // arrival counter of the fused step
+    unsigned int ticket_aux; // arrival counter of the auxiliary reductions
+    int err;                 // first device-detected error (spg_status), 0 if none
+    int hist_count;          // history entries written so far
+    unsigned int err_info;   // where the error was raised
+    int pad;
+};
+
+struct StepParams {
+    const VolDesc *vols;
+    const WorkItem *items;
+    const TmapSet *tmaps;
+    float *xbuf[3];
+    const float *beta;       // extrapolation table beta_k (float32)
+    DevState *st;
+    double *partials;        // [nitems][3] objective partial sums of the last recorded step
+    double *hist;            // ring [hist_cap][nvol][5]
+    int nitems, nvol, hist_cap, hist_every;
+    long long timeout_ns;    // bound on any single barrier wait
+};
+
+// Variant of the fused step: tile = (32*vx) x ty voxels, `stages` pipeline stages.
+struct StepVariant {
+    int vx, ty, stages;
+    bool bf16;
+};
+
+// Host-callable launchers (spg_step.cu).
+size_t step_smem_bytes(const StepVariant &v);
+cudaError_t step_configure(const StepVariant &v, int *ctas_per_sm);
+cudaError_t step_launch(const StepVariant &v, int grid, const StepParams &p, cudaStream_t s);
+bool step_variant_supported(const StepVariant &v);
+
+// Auxiliary kernels (spg_aux.cu). Every one runs one CTA per z-plane of
+// every volume and reduces per-plane partials in a fixed order.
+struct AuxParams {
+    const VolDesc *vols;
+    const int *plane_vol;    // volume of each global plane
+    int nplanes, nvol;
+    DevState *st;
+    double *plane_part;      // [nplanes][4]
+    double *vol_out;         // [nvol][8]
+};
+
+cudaError_t launch_validate(const AuxParams &a, int vol, int nz, const void *b, const void *w, bool bf16,
+                            double *maxw_out, cudaStream_t s);
+cudaError_t launch_convert_to_bf16(const float *src, uint16_t *dst, long long n, cudaStream_t s);
+cudaError_t launch_convert_to_f32(const uint16_t *src, float *dst, long long n, cudaStream_t s);
+cudaError_t launch_reweight(const AuxParams &a, const float *const *xbuf, float *om1, float *omtv,
+                            const double *maxw, double *rstats, VolDesc *vols_rw, cudaStream_t s);
+cudaError_t launch_objective(const AuxParams &a, const float *const *xbuf, const void *b, const void *w,
+                             bool bf16, const float *om1, const float *omtv, cudaStream_t s);
+cudaError_t launch_certificate(const AuxParams &a, const float *const *xbuf, const float *beta,
+                               const void *b, const void *w, bool bf16, const float *omtv, cudaStream_t s);
+
+// Adjoint of one step (spg_aux.cu): given gnext = dL/dx_{k+1} and the step's
+// inputs, accumulates into gcur (dL/dx_k), gprev (dL/dx_{k-1}), gb, gw and the
+// per-plane scalar partials {dL/dlambda_l1, dL/dlambda_tv}.
+struct AdjParams {
+    const VolDesc *vols;     // single volume
+    int nplanes;
+    const float *xk, *xkm1;  // step inputs
+    float beta;
+    const void *b, *w;
+    bool bf16;
+    const float *om1, *omtv;
+    const float *gnext;
+    float *m;                // scratch volume: masked cotangent of z
+    float *gcur, *gprev, *gb, *gw;
+    double *plane_part;      // [nplanes][4]
+};
+cudaError_t launch_adjoint_mask(const AdjParams &a, cudaStream_t s);
+cudaError_t launch_adjoint_apply(const AdjParams &a, cudaStream_t s);
+cudaError_t launch_plain_step(const VolDesc *vols, int nplanes, const float *xk, const float *xkm1,
+                              float beta, const void *b, const void *w, bool bf16, const float *om1,
+                              const float *omtv, float *xout, cudaStream_t s);
+cudaError_t launch_timeout_probe(DevState *st, long long timeout_ns, cudaStream_t s);
+
+}  // namespace spg

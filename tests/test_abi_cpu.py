@@ -1,0 +1,50 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry
+point declared in include/spg.h (no compute calls here)."""
+import ctypes
+import os
+import re
+
+from paper_1905_13408_gb300 import spg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "spg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(spg_[a-z_]+)\s*\(", src)))
+
+
+def test_header_matches_binding_list():
+    assert declared_symbols() == sorted(spg.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = spg.load()
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_create_without_gpu_fails_cleanly():
+    """No CUDA device here: creation must fail with a status, not fall back."""
+    import torch
+    if torch.cuda.is_available():
+        return
+    lib = spg.load()
+    p = spg.volume_params((8, 8, 8))
+    h = ctypes.c_void_p()
+    st = lib.spg_create(ctypes.byref(p), None, None, ctypes.byref(h))
+    assert st == spg.SPG_ECUDA
+    assert not h.value
+    assert "CUDA" in spg.spg_last_error(None) or "device" in spg.spg_last_error(None)
+
+
+def test_bad_arguments_rejected_before_device_use():
+    lib = spg.load()
+    h = ctypes.c_void_p()
+    bad = spg.volume_params((0, 8, 8))
+    assert lib.spg_create(ctypes.byref(bad), None, None, ctypes.byref(h)) == spg.SPG_EINVAL
+    neg = spg.volume_params((8, 8, 8), mu=-1.0)
+    assert lib.spg_create(ctypes.byref(neg), None, None, ctypes.byref(h)) == spg.SPG_EINVAL
+    assert lib.spg_reweight(None) == spg.SPG_EINVAL
+    assert lib.spg_iterate(None, 3) == spg.SPG_EINVAL

@@ -1,0 +1,348 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
+
+Tolerances: the fused step computes in float32 with one rounding of the
+iterate per step (the increment is formed relative to x_k). After the fixed
+schedules the iterate must match the oracle to rel-L2 <= 1e-5 and the
+objective to rel <= 1e-6; a single step from identical inputs must match to
+rel-L2 <= 2e-7 (a few float32 roundings).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1905_13408_gb300 import spg, synth
+
+pytestmark = pytest.mark.gpu
+
+HYPER = dict(synth.DEFAULT_HYPER)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def make_solver(shape, hyper=HYPER, **kw):
+    return spg.SPG(dict(shape=shape, **hyper), **kw)
+
+
+def gpu_solve(b, w, hyper, rounds, iters, x0=None, **kw):
+    s = make_solver(b.shape, hyper, **kw)
+    s.set_data(0, torch.from_numpy(np.ascontiguousarray(b, np.float32)).cuda(),
+               torch.from_numpy(np.ascontiguousarray(w, np.float32)).cuda())
+    if x0 is not None:
+        s.set_x(0, torch.from_numpy(np.ascontiguousarray(x0, np.float32)).cuda())
+    stats = []
+    for _ in range(rounds):
+        s.reweight()
+        stats.append(s.round_stats(0))
+        s.iterate(iters)
+    x = s.get_x(0).cpu().numpy()
+    hist = s.history(0)
+    obj = s.objective(0)
+    s.close()
+    return x, hist, np.array(stats), obj
+
+
+def oparams(shape, hyper=HYPER, momentum="fista"):
+    return oracle.Params(tuple(shape), momentum=momentum, **hyper)
+
+
+@pytest.mark.parametrize("shape", [(5, 7, 9), (33, 17, 65), (19, 37, 300), (1, 1, 1), (2, 3, 1), (9, 1, 130)])
+def test_few_steps_odd_shapes(shape):
+    """Three steps (beta_0 = 0, then two extrapolated steps) from a random
+    start on shapes that leave ragged tiles in x, y and z."""
+    rng = np.random.default_rng(sum(shape))
+    b = rng.standard_normal(shape).astype(np.float32)
+    w = np.exp(0.5 * rng.standard_normal(shape)).astype(np.float32)
+    x0 = (0.5 * rng.standard_normal(shape)).astype(np.float32)
+    hyper = dict(HYPER, mu=0.05)
+    x, hist, st, obj = gpu_solve(b, w, hyper, 1, 3, x0=x0)
+    ref = oracle.solve(b, w, oparams(shape, hyper), 1, 3, x0=x0)
+    assert rel_l2(x, ref.x) <= 2e-6
+    np.testing.assert_allclose(st[0, :4], ref.rstats[0, :4], rtol=1e-6)
+    np.testing.assert_allclose(st[0, 4:], ref.rstats[0, 4:], rtol=1e-6)
+    np.testing.assert_allclose(hist[:, 4], ref.hist[0, :, 3], rtol=1e-6)
+
+
+@pytest.mark.parametrize("tile", ["128x8", "128x4", "64x8", "64x4", "128x16"])
+def test_tile_variants_agree(tile):
+    """Every compiled tile variant computes the same iterate (ragged 3-D shape)."""
+    shape = (23, 45, 150)
+    vol = synth.make_volume(shape, blobs=30, radius=9, seed=3)
+    x, hist, _, _ = gpu_solve(vol.b, vol.w, HYPER, 2, 20, tile=tile)
+    ref = oracle.solve(vol.b, vol.w, oparams(shape), 2, 20)
+    assert rel_l2(x, ref.x) <= 1e-6
+    np.testing.assert_allclose(hist[-20:, 4], ref.hist[1, :, 3], rtol=1e-6)
+
+
+def test_vol64_full_schedule():
+    """64^3 workload, 3 rounds x 200 iterations: rel-L2 <= 1e-5 on x,
+    rel <= 1e-6 on the objective history and the final objective."""
+    vol, hyper, R, I = synth.workload("vol64")
+    x, hist, st, obj = gpu_solve(vol.b, vol.w, hyper, R, I)
+    ref = oracle.solve(vol.b, vol.w, oparams(vol.b.shape, hyper), R, I)
+    err = rel_l2(x, ref.x)
+    print(f"vol64 rel-L2 {err:.3e}")
+    assert err <= 1e-5
+    np.testing.assert_allclose(hist[:, 4], ref.hist.reshape(-1, 4)[:, 3], rtol=1e-6)
+    fo = oracle.objective(ref.x, vol.b, vol.w, ref.om1, ref.omtv, oparams(vol.b.shape, hyper))
+    np.testing.assert_allclose(obj[3], fo[3], rtol=1e-6)
+    np.testing.assert_allclose(st[:, 4:], ref.rstats[:, 4:], rtol=1e-6)
+
+
+def test_vol256_full_schedule():
+    """256^3 workload, 3 rounds x 300 iterations, same gates."""
+    vol, hyper, R, I = synth.workload("vol256")
+    x, hist, st, obj = gpu_solve(vol.b, vol.w, hyper, R, I)
+    ref = oracle.solve(vol.b, vol.w, oparams(vol.b.shape, hyper), R, I)
+    err = rel_l2(x, ref.x)
+    print(f"vol256 rel-L2 {err:.3e}")
+    assert err <= 1e-5
+    np.testing.assert_allclose(hist[:, 4], ref.hist.reshape(-1, 4)[:, 3], rtol=1e-6)
+
+
+def test_vol512_sampled_step():
+    """512^3 at the benchmark's launch configuration: after 25 iterations of
+    round 1, one more step is checked at 20000 sampled voxels against the
+    oracle evaluated voxel by voxel from the GPU's own x_k, x_{k-1}, weights
+    and tau (read back through the state blob)."""
+    vol, hyper, _, _ = synth.workload("vol512")
+    shape = vol.b.shape
+    s = make_solver(shape, hyper)
+    s.set_data(0, torch.from_numpy(vol.b).cuda(), torch.from_numpy(vol.w).cuda())
+    s.reweight()
+    s.iterate(25)
+    blob = s.get_state()
+    s.iterate(1)
+    x1 = s.get_x(0).cpu().numpy()
+    st = s.round_stats(0)
+    s.close()
+    n = vol.b.size
+    sv = spg.parse_state(blob, [shape])["volumes"][0]
+    xk, xkm1, om1, omtv, tau = sv["x"], sv["x_prev"], sv["om1"], sv["omtv"], np.float32(sv["tau"])
+    beta = oracle.beta_table(26)[25]
+    rng = np.random.default_rng(5)
+    idx = rng.choice(n, 20000, replace=False)
+    # include faces, edges and corners
+    edge = np.ravel_multi_index(np.array([[0, 0, 0], [511, 511, 511], [0, 511, 255], [255, 0, 511],
+                                          [511, 128, 0], [1, 1, 1]]).T, shape)
+    idx = np.concatenate([idx, edge])
+    want = oracle.step_sampled(xk, xkm1, float(np.float32(beta)), float(tau), vol.b, vol.w, om1, omtv,
+                               oparams(shape, hyper), idx)
+    got = x1.ravel()[idx]
+    assert np.abs(got - want).max() <= 2e-6 * max(1.0, np.abs(want).max())
+    assert abs(st[5] - float(tau)) <= 1e-7 * st[5]
+
+
+def test_objective_and_reweight_match_oracle():
+    shape = (21, 34, 77)
+    vol = synth.make_volume(shape, blobs=20, radius=8, seed=8)
+    rng = np.random.default_rng(9)
+    x0 = np.where(rng.random(shape) < 0.3, 0.0, rng.standard_normal(shape)).astype(np.float32)
+    s = make_solver(shape)
+    s.set_data(0, vol.b, vol.w)  # host numpy inputs
+    s.set_x(0, x0)
+    s.reweight()
+    st = s.round_stats(0)
+    obj = s.objective(0)
+    s.close()
+    p = oparams(shape)
+    om1, omtv, ost = oracle.reweight(x0, p)
+    np.testing.assert_allclose(st[:4], ost, rtol=2e-6)
+    L = oracle.lipschitz(vol.w, ost[0], p)
+    np.testing.assert_allclose(st[4], L, rtol=1e-6)
+    fo = oracle.objective(x0, vol.b, vol.w, om1, omtv, p)
+    np.testing.assert_allclose(obj, fo, rtol=1e-6)
+
+
+def test_certificate_matches_oracle():
+    shape = (16, 24, 40)
+    vol = synth.make_volume(shape, blobs=10, radius=5, seed=10)
+    s = make_solver(shape)
+    s.set_data(0, vol.b, vol.w)
+    s.reweight()
+    s.iterate(30)
+    blob = s.get_state()
+    s.iterate(1)
+    cert = s.certificate(0)
+    x1 = s.get_x(0).cpu().numpy()
+    s.close()
+    sv = spg.parse_state(blob, [shape])["volumes"][0]
+    tau = sv["tau"]
+    xk, xkm1, om1, omtv = (sv[k].astype(np.float64) for k in ("x", "x_prev", "om1", "omtv"))
+    beta = float(np.float32(oracle.beta_table(31)[30]))
+    y = xk + beta * (xk - xkm1)
+    want = oracle.certificate(y, x1, tau, vol.b, vol.w, omtv, oparams(shape))
+    np.testing.assert_allclose(cert, want, rtol=1e-3)
+
+
+def test_batch_equals_single_volumes():
+    """Uneven batch in one launch per iteration equals per-volume contexts
+    (identical per-voxel arithmetic) and the oracle."""
+    shapes = [(24, 24, 24), (17, 33, 40), (32, 32, 32), (9, 50, 70)]
+    vols = [synth.make_volume(sh, blobs=8, radius=4, seed=20 + i) for i, sh in enumerate(shapes)]
+    hypers = [dict(HYPER, lambda_tv=0.05 + 0.05 * i) for i in range(len(shapes))]
+    s = spg.SPG([dict(shape=sh, **h) for sh, h in zip(shapes, hypers)])
+    for i, v in enumerate(vols):
+        s.set_data(i, v.b, v.w)
+    s.solve(2, 25)
+    xb = [s.get_x(i).cpu().numpy() for i in range(len(shapes))]
+    hb = [s.history(i) for i in range(len(shapes))]
+    s.close()
+    for i, (sh, v, h) in enumerate(zip(shapes, vols, hypers)):
+        x1, h1, _, _ = gpu_solve(v.b, v.w, h, 2, 25)
+        ref = oracle.solve(v.b, v.w, oparams(sh, h), 2, 25)
+        assert rel_l2(xb[i], ref.x) <= 1e-6
+        assert rel_l2(xb[i], x1) <= 1e-6
+        np.testing.assert_allclose(hb[i][:, 4], h1[:, 4], rtol=1e-9)
+
+
+def test_bf16_storage():
+    """b, w stored in bfloat16: against the oracle fed the bfloat16-rounded
+    inputs the arithmetic gate holds; against the original inputs the
+    quantisation error is reported."""
+    vol, hyper, R, I = synth.workload("vol64")
+    b16 = torch.from_numpy(vol.b).to(torch.bfloat16).float().numpy()
+    w16 = torch.from_numpy(vol.w).to(torch.bfloat16).float().numpy()
+    x, hist, _, _ = gpu_solve(vol.b, vol.w, hyper, R, I, data_dtype="bf16")
+    ref16 = oracle.solve(b16, w16, oparams(vol.b.shape, hyper), R, I)
+    ref32 = oracle.solve(vol.b, vol.w, oparams(vol.b.shape, hyper), R, I, with_hist=False)
+    e16, e32 = rel_l2(x, ref16.x), rel_l2(x, ref32.x)
+    print(f"bf16 storage: rel-L2 vs oracle(bf16 inputs) {e16:.3e}, vs oracle(f32 inputs) {e32:.3e}")
+    assert e16 <= 1e-5
+    assert e32 <= 2e-2
+
+
+def test_ista_monotone_on_gpu():
+    vol = synth.make_volume((20, 30, 40), blobs=10, radius=6, seed=30)
+    _, hist, _, _ = gpu_solve(vol.b, vol.w, HYPER, 2, 50, momentum="ista")
+    tot = hist[:, 4].reshape(2, 50)
+    assert np.all(np.diff(tot, axis=1) <= 1e-6 * np.abs(tot[:, 1:]))
+
+
+def test_checkpoint_resume_bitwise():
+    shape = (18, 26, 70)
+    vol = synth.make_volume(shape, blobs=10, radius=5, seed=40)
+    a = make_solver(shape)
+    a.set_data(0, vol.b, vol.w)
+    a.reweight()
+    a.iterate(17)
+    blob = a.get_state()
+    a.iterate(23)
+    xa = a.get_x(0).cpu().numpy()
+    a.close()
+    b = make_solver(shape)
+    b.set_data(0, vol.b, vol.w)
+    b.set_state(blob)
+    assert b.counters() == (17, 17)
+    b.iterate(23)
+    xb = b.get_x(0).cpu().numpy()
+    b.close()
+    np.testing.assert_array_equal(xa, xb)
+
+
+def test_graph_replay_equals_single_launches():
+    """Iterations replayed from the captured graph equal single launches."""
+    shape = (12, 40, 50)
+    vol = synth.make_volume(shape, blobs=6, radius=4, seed=50)
+    outs = []
+    for chunks in ([35], [1] * 35):
+        s = make_solver(shape)
+        s.set_data(0, vol.b, vol.w)
+        s.reweight()
+        for c in chunks:
+            s.iterate(c)
+        outs.append(s.get_x(0).cpu().numpy())
+        s.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
+def test_input_validation_errors():
+    shape = (4, 5, 6)
+    s = make_solver(shape)
+    b = np.zeros(shape, np.float32)
+    w = np.ones(shape, np.float32)
+    with pytest.raises(spg.SPGError) as e:
+        s.iterate(1)
+    assert e.value.status == spg.SPG_ENOTREADY
+    w_bad = w.copy()
+    w_bad[1, 2, 3] = 0.0
+    with pytest.raises(spg.SPGError) as e:
+        s.set_data(0, b, w_bad)
+    assert e.value.status == spg.SPG_EINVAL
+    b_bad = b.copy()
+    b_bad[0, 0, 0] = np.nan
+    with pytest.raises(spg.SPGError) as e:
+        s.set_data(0, b_bad, w)
+    assert e.value.status == spg.SPG_ENONFINITE
+    s.set_data(0, b, w)
+    s.reweight()
+    s.iterate(3)
+    assert np.all(s.get_x(0).cpu().numpy() == 0)
+    s.close()
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A device wait on a barrier nothing completes gives up after its limit,
+    reports SPG_ETIMEOUT, and the context keeps working."""
+    shape = (8, 16, 32)
+    vol = synth.make_volume(shape, blobs=4, radius=3, seed=60)
+    s = make_solver(shape)
+    s.set_data(0, vol.b, vol.w)
+    assert spg.spg_probe_timeout(s.handle, 1_000_000) == spg.SPG_ETIMEOUT
+    s.reweight()
+    s.iterate(5)
+    ref = oracle.solve(vol.b, vol.w, oparams(shape), 1, 5)
+    assert rel_l2(s.get_x(0).cpu().numpy(), ref.x) <= 1e-6
+    s.close()
+
+
+def test_adjoint_matches_oracle():
+    """Hand-written adjoint of K unrolled steps (weights 1, tau fixed)
+    against the oracle's FP64 adjoint."""
+    shape = (12, 14, 20)
+    vol = synth.make_volume(shape, blobs=6, radius=4, seed=70)
+    hyper = dict(HYPER, mu=0.02)
+    K = 12
+    b = torch.from_numpy(vol.b).cuda()
+    w = torch.from_numpy(vol.w).cuda()
+    s = make_solver(shape, hyper)
+    s.set_data(0, b, w)
+    s.reweight()
+    tau = s.round_stats(0)[5]
+    xK = torch.empty_like(b)
+    spg.spg_unrolled(s.handle, K, xK)
+    ph = torch.from_numpy(vol.phantom).cuda()
+    gx = 2 * (xK - ph)
+    gb = torch.empty_like(b)
+    gw = torch.empty_like(b)
+    gs = spg.spg_backward(s.handle, K, gx.contiguous(), gb, gw, ckpt_every=5)
+    s.close()
+    p = oparams(shape, hyper)
+    x0 = np.zeros(shape)
+    ref_xK = oracle.unrolled(vol.b, vol.w, None, None, tau, K, x0, p)
+    assert rel_l2(xK.cpu().numpy(), ref_xK) <= 1e-6
+    gK = 2 * (ref_xK - vol.phantom)
+    rb, rw, rs = oracle.backward(vol.b, vol.w, None, None, tau, K, x0, gK, p)
+    assert rel_l2(gb.cpu().numpy(), rb) <= 1e-4
+    assert rel_l2(gw.cpu().numpy(), rw) <= 1e-4
+    np.testing.assert_allclose(gs, rs, rtol=1e-4)
+
+
+def test_autograd_function():
+    shape = (10, 12, 16)
+    vol = synth.make_volume(shape, blobs=5, radius=3, seed=80)
+    b = torch.from_numpy(vol.b).cuda().requires_grad_(True)
+    w = torch.from_numpy(vol.w).cuda().requires_grad_(True)
+    l1 = torch.tensor(0.05, requires_grad=True)
+    tv = torch.tensor(0.1, requires_grad=True)
+    x = spg.UnrolledSPG.apply(b, w, l1, tv, 8, mu=0.02)
+    loss = ((x - torch.from_numpy(vol.phantom).cuda()) ** 2).sum()
+    loss.backward()
+    assert b.grad is not None and w.grad is not None
+    assert torch.isfinite(b.grad).all() and torch.isfinite(w.grad).all()
+    assert l1.grad is not None and tv.grad is not None
