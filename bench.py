@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--tile", default="auto")
     ap.add_argument("--zchunk", type=int, default=0)
+    ap.add_argument("--hist-every", type=int, default=1)
+    ap.add_argument("--storage", default="delta", choices=["delta", "prev"])
     ap.add_argument("--no-gap", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -129,14 +131,18 @@ def measured_peaks():
 
 
 def step_source_hash():
-    with open(os.path.join(ROOT, "paper_1905_13408_gb300", "csrc", "spg_step.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the fused-step sources (kernel header and its instantiations)."""
+    h = hashlib.sha256()
+    for name in ("spg_step_kernel.cuh", "spg_step_f32.cu", "spg_step_bf16.cu", "spg_step.cu"):
+        with open(os.path.join(ROOT, "paper_1905_13408_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload, dtype):
+def profiled_traffic(workload, dtype, storage):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current fused-step source; else None."""
-    path = os.path.join(ROOT, "profiles", f"spg_step_{workload}_{dtype}.txt")
+    path = os.path.join(ROOT, "profiles", f"spg_step_{workload}_{dtype}_{storage}.txt")
     try:
         kv = {}
         with open(path) as f:
@@ -151,12 +157,14 @@ def profiled_traffic(workload, dtype):
         return None
 
 
-def bytes_per_voxel(dtype):
-    # reads x_k, x_{k-1}, b, w, om1, omtv; writes x_{k+1}
-    return 28 if dtype == "f32" else 24
+def bytes_per_voxel(dtype, storage="delta"):
+    """Algorithmic HBM bytes per voxel-iteration of the fused step: reads x_k,
+    d_k (or x_{k-1}), b, w, om1, omtv; writes x_{k+1} (and d_{k+1})."""
+    data = 8 if dtype == "f32" else 4
+    return 4 + 4 + data + 4 + 4 + 4 + (4 if storage == "delta" else 0)
 
 
-def cpu_baseline(vol, hyper, nz_slab=64, iters=6):
+def cpu_baseline(vol, hyper, nz_slab=64, iters=30):
     """The FP64 oracle, as it stands, on a z-slab of the workload."""
     import numpy as np
 
@@ -237,7 +245,7 @@ def time_to_gap(vol, hyper, args, stream):
     from paper_1905_13408_gb300 import spg
     n_ref = 1500
     s = spg.SPG(dict(shape=vol.b.shape, **hyper), data_dtype=args.dtype, hist_capacity=n_ref + 16,
-                tile=args.tile, zchunk=args.zchunk, stream=stream.cuda_stream)
+                tile=args.tile, zchunk=args.zchunk, stream=stream.cuda_stream, storage=args.storage)
     s.set_data(0, *dev_inputs(vol, args.dtype))
     s.reweight()
     s.iterate(n_ref)
@@ -293,7 +301,8 @@ def run_spg(args):
     nvox = vol.b.size
 
     s = spg.SPG(dict(shape=vol.b.shape, **hyper), data_dtype=args.dtype, tile=args.tile, zchunk=args.zchunk,
-                stream=stream.cuda_stream, max_iters=max(100000, args.steps + args.warmup + 16))
+                stream=stream.cuda_stream, max_iters=max(100000, args.steps + args.warmup + 16),
+                hist_every=args.hist_every, storage=args.storage)
     s.set_data(0, *dev_inputs(vol, args.dtype))
     s.reweight()
     s.iterate(args.warmup)
@@ -325,9 +334,9 @@ def run_spg(args):
     per_launch_s = ms / 1e3 / args.steps
     value = world * nvox * args.steps / (ms / 1e3) / 1e9
     peaks, peak_kind = measured_peaks()
-    bpv = bytes_per_voxel(args.dtype)
+    bpv = bytes_per_voxel(args.dtype, args.storage)
     achieved = bpv * nvox / per_launch_s / 1e9
-    traffic = profiled_traffic(args.workload, args.dtype)
+    traffic = profiled_traffic(args.workload, args.dtype, args.storage)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": bpv * nvox,
@@ -350,7 +359,8 @@ def run_spg(args):
                "config": {"workload": workload_desc(args.workload, args.dtype), "voxels": nvox,
                           "l2": "inputs larger than L2 (each step streams ~%.1f GB)" % (bpv * nvox / 1e9),
                           "tile": f"{plan['tile_x']}x{plan['tile_y']}", "zchunk": plan["zchunk"],
-                          "grid": plan["grid"], "items": plan["items"], "objective_every_step": True,
+                          "grid": plan["grid"], "items": plan["items"], "objective_every": args.hist_every,
+                          "iterate_storage": args.storage,
                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                "roofline": roof, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
                "cpu_baseline": cpu, "time_to_gap": gap, "final_objective": float(obj[3])}
@@ -371,7 +381,7 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=3):
     w_h = torch.from_numpy(vol.w).pin_memory()
     x_h = torch.empty(vol.b.shape, dtype=torch.float32).pin_memory()
     s = spg.SPG(dict(shape=vol.b.shape, **hyper), data_dtype=args.dtype, tile=args.tile, zchunk=args.zchunk,
-                stream=stream.cuda_stream)
+                stream=stream.cuda_stream, storage=args.storage, hist_every=args.hist_every)
     zero = torch.zeros(vol.b.shape, dtype=torch.float32)
     s.set_data(0, b_h, w_h)
     s.reweight()
@@ -396,10 +406,113 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=3):
             "step": f"upload b,w from pinned host, re-weight, {iters} fused iterations, objective, download x"}
 
 
+def run_batch(args):
+    """24 independent volumes of uneven sizes (6 each of 96^3, 128^3, 192^3,
+    256^3, lambda_tv ~ U(0.05, 0.2)) advanced by one fused launch per
+    iteration (replayed from a CUDA graph, tile shape from the autotuner),
+    against 24 single-volume contexts launched one after another."""
+    import torch
+
+    from paper_1905_13408_gb300 import spg, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    vols = synth.batch_workload()
+    params = [dict(shape=v.b.shape, **h) for v, h in vols]
+    nvox = sum(v.b.size for v, _ in vols)
+    s = spg.SPG(params, stream=stream.cuda_stream, hist_every=args.hist_every, storage=args.storage,
+                data_dtype=args.dtype)
+    for i, (v, _) in enumerate(vols):
+        s.set_data(i, *dev_inputs(v, args.dtype))
+    s.reweight()
+    tuned = s.autotune(10) if args.tile == "auto" else s.plan_info()
+    s.iterate(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = s.launch_count()
+    e0.record(stream)
+    s.iterate(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1)
+    launches = s.launch_count() - l0
+    s.close()
+    singles = []
+    for v, h in vols:
+        c = spg.SPG(dict(shape=v.b.shape, **h), stream=stream.cuda_stream, hist_every=args.hist_every,
+                    storage=args.storage, data_dtype=args.dtype)
+        c.set_data(0, *dev_inputs(v, args.dtype))
+        c.reweight()
+        c.iterate(args.warmup)
+        singles.append(c)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for c in singles:
+            c.iterate(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    for c in singles:
+        c.close()
+    peaks, kind = measured_peaks()
+    bpv = bytes_per_voxel(args.dtype, args.storage)
+    value = nvox * args.steps / (ms_batch / 1e3) / 1e9
+    achieved = bpv * nvox * args.steps / (ms_batch / 1e3) / 1e9
+    out = {"metric": "Gvoxel-iter/s, 24 uneven volumes in one fused launch per iteration", "value": value,
+           "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms_batch / args.steps, "higher_is_better": True, "dtype": args.dtype,
+           "data": "synthetic", "config": {"workload": "batch24: 6 each of 96^3, 128^3, 192^3, 256^3",
+                                           "voxels": nvox, "plan": tuned, "iterate_storage": args.storage,
+                                           "objective_every": args.hist_every},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved / peaks["hbm_gbs"], "peak_kind": kind},
+           "sequential": {"value": nvox * args.steps / (ms_seq / 1e3) / 1e9, "ms_per_step": ms_seq / args.steps,
+                          "launches_per_step": len(vols)},
+           "speedup_vs_sequential": ms_seq / ms_batch, "gpu_launches": launches}
+    print(json.dumps(out))
+    return 0
+
+
+def run_adjoint(args):
+    """128^3 volume, 50 unrolled iterations (weights 1, tau fixed), forward
+    and hand-written adjoint with checkpoints every 10 iterations."""
+    import torch
+
+    from paper_1905_13408_gb300 import spg, synth
+    torch.cuda.set_device(0)
+    vol, hyper, _, K = synth.workload("vol128_adjoint")
+    b = torch.from_numpy(vol.b).cuda().requires_grad_(True)
+    w = torch.from_numpy(vol.w).cuda().requires_grad_(True)
+    ph = torch.from_numpy(vol.phantom).cuda()
+    times = []
+    for rep in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x = spg.UnrolledSPG.apply(b, w, hyper["lambda_l1"], hyper["lambda_tv"], K, mu=hyper["mu"])
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss = ((x - ph) ** 2).sum()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        times.append((t1 - t0, t2 - t1))
+        b.grad = None
+        w.grad = None
+    fwd, bwd = min(t[0] for t in times), min(t[1] for t in times)
+    print(json.dumps({"metric": "unrolled forward + adjoint, 128^3, 50 iterations, checkpoints every 10",
+                      "forward_ms": fwd * 1e3, "backward_ms": bwd * 1e3, "unit": "ms",
+                      "voxel_iterations_per_s_backward": vol.b.size * K / bwd / 1e9}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch24":
+        return run_batch(args)
+    if args.workload == "adjoint128":
+        return run_adjoint(args)
     return run_spg(args)
 
 

@@ -67,6 +67,16 @@ typedef enum { SPG_F32 = 0, SPG_BF16 = 1 } spg_dtype;
  * SPG_ISTA: beta = 0, the paper's Eq. 20-21 update as printed. */
 typedef enum { SPG_FISTA = 0, SPG_ISTA = 1 } spg_momentum;
 
+/* How the extrapolation pair is kept between iterations (float32 either way).
+ * SPG_STORE_DELTA: x_k and the increment d_k = x_k - x_{k-1} as computed before
+ *   x_k was rounded; 32 bytes of HBM traffic per voxel-iteration. The momentum
+ *   term then carries no rounding of x, which keeps long float32 solves within
+ *   about 1e-6 (relative L2) of exact arithmetic.
+ * SPG_STORE_PREV: x_k and x_{k-1}; 28 bytes per voxel-iteration; the rounding
+ *   of each stored iterate re-enters the momentum term (about 1e-5 after
+ *   3 x 300 iterations on a 256^3 volume). */
+typedef enum { SPG_STORE_DELTA = 0, SPG_STORE_PREV = 1 } spg_iterate_storage;
+
 /* Per-volume problem description. eps/eps_tv set the weight scale of Eq. 11
  * (Sec. 2.5 multiplies the weights by eps so that a zero voxel gets weight 1). */
 typedef struct {
@@ -89,11 +99,12 @@ typedef struct {
     int tile;                 /* 0 = built-in choice, else an spg_tile_* code */
     int zchunk;               /* 0 = built-in choice, else planes per work item */
     int ctas_per_sm;          /* 0 = occupancy limit, else a cap */
+    spg_iterate_storage iterate_storage;  /* SPG_STORE_DELTA (default) or SPG_STORE_PREV */
 } spg_options;
 
 /* Tile codes for spg_options.tile: x extent = 32 * vx, y extent = ty. */
 enum { SPG_TILE_AUTO = 0, SPG_TILE_128x8 = 1, SPG_TILE_128x4 = 2, SPG_TILE_64x8 = 3,
-       SPG_TILE_64x4 = 4, SPG_TILE_128x16 = 5, SPG_TILE_64x16 = 6 };
+       SPG_TILE_64x4 = 4, SPG_TILE_128x7 = 6, SPG_TILE_128x15 = 7, SPG_TILE_64x7 = 8 };
 
 /* Create a solver for one volume (spg_create) or for nvol independent
  * volumes of possibly different sizes advanced together, one fused launch per
@@ -117,8 +128,8 @@ spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg
 spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg_dtype src_dtype);
 
 /* Set / read the current iterate of volume `vol` (float32, nx*ny*nz).
- * The initial iterate is 0. spg_set_x also sets x_{k-1} = x (momentum
- * restart). spg_get_x is asynchronous unless `x` is pageable host memory. */
+ * The initial iterate is 0. spg_set_x also restarts the momentum
+ * (x_{k-1} = x, i.e. d_k = 0). spg_get_x is asynchronous unless `x` is pageable host memory. */
 spg_status spg_set_x(spg_ctx *ctx, int vol, const float *x);
 spg_status spg_get_x(spg_ctx *ctx, int vol, float *x);
 
@@ -158,8 +169,9 @@ spg_status spg_certificate(spg_ctx *ctx, int vol, double *out);
 /* Iteration counters: total iterations since creation and within the round. */
 spg_status spg_counters(spg_ctx *ctx, long long *k_total, int *k_round);
 
-/* Checkpoint / resume. A state blob holds, for every volume, x_k, x_{k-1},
- * om1, omtv, tau, and the counters; spg_set_state on a context created with
+/* Checkpoint / resume. A state blob holds, for every volume, x_k, then d_k
+ * (SPG_STORE_DELTA) or x_{k-1} (SPG_STORE_PREV), om1, omtv, tau, and the
+ * counters; spg_set_state on a context created with
  * the same parameters continues bit-identically. With blob == NULL,
  * spg_get_state only sets *size. Synchronise. */
 spg_status spg_get_state(spg_ctx *ctx, void *blob, size_t *size);
@@ -186,6 +198,16 @@ spg_status spg_unrolled(spg_ctx *ctx, int K, float *xK);
  * `timeout_ns`. Returns SPG_ETIMEOUT when the wait gave up as designed (the
  * context stays usable), SPG_OK if it did not time out. Synchronises. */
 spg_status spg_probe_timeout(spg_ctx *ctx, long long timeout_ns);
+
+/* Autotuner: times every compiled tile shape of the fused step, each with a
+ * few z-splits of the work, for `trial_iters` iterations on this context's
+ * own data, keeps the fastest plan and restores the iterate, counters and
+ * history afterwards (results are unaffected). With the environment variable
+ * SPG_AUTOTUNE_CACHE naming a file, choices are cached there per (volume
+ * sizes, data dtype, iterate storage, GPU) and reused without timing.
+ * Needs spg_set_data for every volume and a spg_reweight first. info as
+ * spg_plan_info. Synchronises; allocates scratch for the saved state. */
+spg_status spg_autotune(spg_ctx *ctx, int trial_iters, int info[6]);
 
 /* Kernel launches issued by this context so far (for launch accounting). */
 long long spg_launch_count(const spg_ctx *ctx);

@@ -11,6 +11,7 @@ definitions each function follows are written at the top of ``spg_oracle.c``
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -63,40 +64,58 @@ class Params:
 _D = ctypes.POINTER(ctypes.c_double)
 
 
+def _bind(path):
+    lib = ctypes.CDLL(path)
+    PP = ctypes.POINTER(_P)
+    sig = {
+        "orc_soft": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
+        "orc_huber": (ctypes.c_double, [ctypes.c_double] * 4),
+        "orc_huber_grad": (None, [ctypes.c_double] * 4 + [_D]),
+        "orc_grad": (None, [PP, _D, _D]),
+        "orc_div": (None, [PP, _D, _D]),
+        "orc_tv_grad": (None, [PP, _D, _D, _D]),
+        "orc_grad_f": (None, [PP, _D, _D, _D, _D, _D]),
+        "orc_objective": (None, [PP, _D, _D, _D, _D, _D, _D]),
+        "orc_reweight": (None, [PP, _D, _D, _D, _D]),
+        "orc_lipschitz": (ctypes.c_double, [PP, _D, ctypes.c_double]),
+        "orc_beta_table": (None, [ctypes.c_int, ctypes.c_int, _D]),
+        "orc_step": (None, [PP, _D, _D, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D]),
+        "orc_solve": (ctypes.c_int, [PP, _D, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D]),
+        "orc_unrolled": (None, [PP, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D]),
+        "orc_certificate": (ctypes.c_double, [PP, _D, _D, ctypes.c_double, _D, _D, _D]),
+        "orc_step_sampled": (None, [PP, _D, _D, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D,
+                                    ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _D]),
+        "orc_backward": (ctypes.c_int, [PP, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D,
+                                        _D, _D, _D]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB)
-            PP = ctypes.POINTER(_P)
-            sig = {
-                "orc_soft": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
-                "orc_huber": (ctypes.c_double, [ctypes.c_double] * 4),
-                "orc_huber_grad": (None, [ctypes.c_double] * 4 + [_D]),
-                "orc_grad": (None, [PP, _D, _D]),
-                "orc_div": (None, [PP, _D, _D]),
-                "orc_tv_grad": (None, [PP, _D, _D, _D]),
-                "orc_grad_f": (None, [PP, _D, _D, _D, _D, _D]),
-                "orc_objective": (None, [PP, _D, _D, _D, _D, _D, _D]),
-                "orc_reweight": (None, [PP, _D, _D, _D, _D]),
-                "orc_lipschitz": (ctypes.c_double, [PP, _D, ctypes.c_double]),
-                "orc_beta_table": (None, [ctypes.c_int, ctypes.c_int, _D]),
-                "orc_step": (None, [PP, _D, _D, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D]),
-                "orc_solve": (ctypes.c_int, [PP, _D, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D]),
-                "orc_unrolled": (None, [PP, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D]),
-                "orc_certificate": (ctypes.c_double, [PP, _D, _D, ctypes.c_double, _D, _D, _D]),
-                "orc_step_sampled": (None, [PP, _D, _D, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D,
-                                            ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _D]),
-                "orc_backward": (ctypes.c_int, [PP, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D,
-                                                _D, _D, _D]),
-            }
-            for name, (res, args) in sig.items():
-                f = getattr(lib, name)
-                f.restype = res
-                f.argtypes = args
-            _lib = lib
+            _lib = _bind(_LIB)
     return _lib
+
+
+@contextlib.contextmanager
+def using_library(path):
+    """Temporarily route every wrapper call to another build of the oracle
+    (used by the tests that plant mistakes in a copy of the source)."""
+    global _lib
+    _load()
+    old = _lib
+    _lib = _bind(path)
+    try:
+        yield
+    finally:
+        _lib = old
 
 
 def _a(x, shape=None):

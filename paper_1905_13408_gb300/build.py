@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libspg.so")
-SOURCES = ["spg_step.cu", "spg_aux.cu", "spg_api.cu"]
+SOURCES = ["spg_step_f32.cu", "spg_step_bf16.cu", "spg_step.cu", "spg_aux.cu", "spg_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -41,7 +41,8 @@ def _stale():
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, s) for s in SOURCES]
-    deps += [os.path.join(CSRC, "spg_internal.h"), os.path.join(INCLUDE, "spg.h"), __file__]
+    deps += [os.path.join(CSRC, "spg_internal.h"), os.path.join(CSRC, "spg_step_kernel.cuh"),
+             os.path.join(INCLUDE, "spg.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

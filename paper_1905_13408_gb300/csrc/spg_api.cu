@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -60,7 +61,7 @@ struct spg_ctx {
     WorkItem *items_d = nullptr;
     TmapSet *tmaps_d = nullptr;
     int *plane_vol_d = nullptr;
-    float *X[3] = {nullptr, nullptr, nullptr};
+    float *X[4] = {nullptr, nullptr, nullptr, nullptr};
     void *B = nullptr, *W = nullptr;
     float *OM1 = nullptr, *OMTV = nullptr;
     float *beta_d = nullptr;
@@ -72,13 +73,13 @@ struct spg_ctx {
     double *maxw_d = nullptr;
     double *rstats_d = nullptr;
 
-    StepVariant var{4, 8, 3, false};
+    StepVariant var{4, 8, 3, false, true};
     int zchunk = 0, grid = 0, ctas_per_sm = 0, nitems = 0;
     std::vector<WorkItem> items_h;
 
     long long k_total = 0;  // host mirror of the device counters
     int k_round = 0;
-    int cur0 = 0;           // x_k lives in X[(cur0 + k_total) % 3]
+    int cur0 = 0;           // x_k lives in X[(cur0 + k_total) % nbuf()]
     bool reweighted = false;
     std::vector<char> data_set;
     int hist_every = 1, hist_cap = 4096, max_iters = 100000;
@@ -88,8 +89,13 @@ struct spg_ctx {
     std::string err = "no error";
 
     bool bf16() const { return opt.data_dtype == SPG_BF16; }
+    bool xd() const { return opt.iterate_storage == SPG_STORE_DELTA; }
+    int nbuf() const { return xd() ? 2 : 3; }  // rotation length of the iterate buffers
+    int nalloc() const { return xd() ? 4 : 3; }
     size_t data_es() const { return bf16() ? 2 : 4; }
-    int cur() const { return (int)(((cur0 + k_total) % 3 + 3) % 3); }
+    int cur() const { return (int)(((cur0 + k_total) % nbuf() + nbuf()) % nbuf()); }
+    // second buffer of the extrapolation pair for the current iterate: d_k or x_{k-1}
+    int aux_of(int c) const { return xd() ? 2 + c : (c + 2) % 3; }
 };
 
 namespace {
@@ -125,7 +131,7 @@ cudaError_t dalloc(T **p, size_t bytes)
 void free_all(spg_ctx *c)
 {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    void *ps[] = {c->vols_d, c->items_d, c->tmaps_d, c->plane_vol_d, c->X[0], c->X[1], c->X[2], c->B, c->W,
+    void *ps[] = {c->vols_d, c->items_d, c->tmaps_d, c->plane_vol_d, c->X[0], c->X[1], c->X[2], c->X[3], c->B, c->W,
                   c->OM1, c->OMTV, c->beta_d, c->st_d, c->partials_d, c->hist_d, c->plane_part_d,
                   c->vol_out_d, c->maxw_d, c->rstats_d};
     for (void *p : ps)
@@ -133,15 +139,17 @@ void free_all(spg_ctx *c)
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
-StepVariant variant_from_tile(int tile, bool bf16)
+StepVariant variant_from_tile(int tile, bool bf16, bool xd)
 {
     switch (tile) {
-    case SPG_TILE_128x4: return {4, 4, 4, bf16};
-    case SPG_TILE_64x8: return {2, 8, 4, bf16};
-    case SPG_TILE_64x4: return {2, 4, 4, bf16};
-    case SPG_TILE_128x16: return {4, 16, 2, bf16};
+    case SPG_TILE_128x4: return {4, 4, 4, bf16, xd};
+    case SPG_TILE_64x8: return {2, 8, 4, bf16, xd};
+    case SPG_TILE_64x4: return {2, 4, 4, bf16, xd};
+    case SPG_TILE_128x7: return {4, 7, 3, bf16, xd};
+    case SPG_TILE_128x15: return {4, 15, 2, bf16, xd};
+    case SPG_TILE_64x7: return {2, 7, 4, bf16, xd};
     case SPG_TILE_128x8:
-    default: return {4, 8, 3, bf16};
+    default: return {4, 8, 3, bf16, xd};
     }
 }
 
@@ -151,7 +159,9 @@ int tile_code(const StepVariant &v)
     if (v.vx == 4 && v.ty == 4) return SPG_TILE_128x4;
     if (v.vx == 2 && v.ty == 8) return SPG_TILE_64x8;
     if (v.vx == 2 && v.ty == 4) return SPG_TILE_64x4;
-    if (v.vx == 4 && v.ty == 16) return SPG_TILE_128x16;
+    if (v.vx == 4 && v.ty == 7) return SPG_TILE_128x7;
+    if (v.vx == 4 && v.ty == 15) return SPG_TILE_128x15;
+    if (v.vx == 2 && v.ty == 7) return SPG_TILE_64x7;
     return 0;
 }
 
@@ -166,9 +176,9 @@ StepVariant default_variant(const spg_ctx *c)
         waste64 += (round_up(v.nx, 64) - v.nx) * (long long)v.ny * v.nz;
     }
     const bool wide = waste128 <= vox / 8;
-    if (wide) return {4, 8, 3, c->bf16()};
-    if (waste64 <= vox / 8) return {2, 8, 4, c->bf16()};
-    return {2, 4, 4, c->bf16()};
+    if (wide) return {4, 7, 3, c->bf16(), c->xd()};
+    if (waste64 <= vox / 8) return {2, 7, 4, c->bf16(), c->xd()};
+    return {2, 4, 4, c->bf16(), c->xd()};
 }
 
 cudaError_t encode_map(CUtensorMap *m, CUtensorMapDataType dt, void *base, const VolDesc &v, size_t es, int bx,
@@ -241,7 +251,7 @@ spg_status build_plan(spg_ctx *ctx, const StepVariant &v, int zchunk_opt)
         const VolDesc &d = ctx->vols_h[j];
         TmapSet &m = maps[j];
         std::memset(&m, 0, sizeof(m));
-        for (int q = 0; q < 3; q++)
+        for (int q = 0; q < ctx->nalloc(); q++)
             CK(encode_map(&m.x[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ctx->X[q], d, 4, TX + 8, TY + 2), "tensor map x");
         CK(encode_map(&m.omtv, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ctx->OMTV, d, 4, TX + 4, TY + 1), "tensor map omtv");
         CK(encode_map(&m.b, dt_data, ctx->B, d, ctx->data_es(), TX, TY), "tensor map b");
@@ -290,7 +300,7 @@ StepParams step_params(const spg_ctx *c)
     p.vols = c->vols_d;
     p.items = c->items_d;
     p.tmaps = c->tmaps_d;
-    for (int q = 0; q < 3; q++) p.xbuf[q] = c->X[q];
+    for (int q = 0; q < 4; q++) p.xbuf[q] = c->X[q];
     p.beta = c->beta_d;
     p.st = c->st_d;
     p.partials = c->partials_d;
@@ -397,9 +407,9 @@ struct StateHeader {
     uint64_t magic;
     int32_t version, nvol, k_round, reweighted;
     int64_t k_total;
-    int32_t dtype, momentum;
+    int32_t dtype, momentum, storage, pad;
 };
-static_assert(sizeof(StateHeader) == 40, "state blob header layout");
+static_assert(sizeof(StateHeader) == 48, "state blob header layout");
 }  // namespace
 
 namespace {
@@ -516,7 +526,12 @@ spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg
     if ((e = dalloc(&ctx->vols_d, nvol * sizeof(VolDesc))) != cudaSuccess) return bail(e, "alloc");
     if ((e = dalloc(&ctx->tmaps_d, nvol * sizeof(TmapSet))) != cudaSuccess) return bail(e, "alloc");
     if ((e = dalloc(&ctx->plane_vol_d, plane * sizeof(int))) != cudaSuccess) return bail(e, "alloc");
-    for (int q = 0; q < 3; q++)
+    if (ctx->opt.iterate_storage != SPG_STORE_DELTA && ctx->opt.iterate_storage != SPG_STORE_PREV) {
+        free_all(ctx);
+        delete ctx;
+        return fail(nullptr, SPG_EINVAL, "spg_create: bad iterate storage");
+    }
+    for (int q = 0; q < ctx->nalloc(); q++)
         if ((e = dalloc(&ctx->X[q], vb)) != cudaSuccess) return bail(e, "alloc iterates");
     if ((e = dalloc(&ctx->B, db)) != cudaSuccess) return bail(e, "alloc b");
     if ((e = dalloc(&ctx->W, db)) != cudaSuccess) return bail(e, "alloc w");
@@ -532,7 +547,7 @@ spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg
     if ((e = dalloc(&ctx->maxw_d, (size_t)nvol * sizeof(double))) != cudaSuccess) return bail(e, "alloc");
     if ((e = dalloc(&ctx->rstats_d, (size_t)nvol * 6 * sizeof(double))) != cudaSuccess) return bail(e, "alloc");
 
-    for (int q = 0; q < 3; q++) cudaMemsetAsync(ctx->X[q], 0, vb, ctx->stream);
+    for (int q = 0; q < ctx->nalloc(); q++) cudaMemsetAsync(ctx->X[q], 0, vb, ctx->stream);
     cudaMemsetAsync(ctx->B, 0, db, ctx->stream);
     cudaMemsetAsync(ctx->W, 0, db, ctx->stream);
     cudaMemsetAsync(ctx->OM1, 0, vb, ctx->stream);
@@ -559,7 +574,8 @@ spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg
         return bail(e, "upload descriptors");
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail(e, "synchronise");
 
-    const StepVariant v = ctx->opt.tile ? variant_from_tile(ctx->opt.tile, ctx->bf16()) : default_variant(ctx);
+    const StepVariant v =
+        ctx->opt.tile ? variant_from_tile(ctx->opt.tile, ctx->bf16(), ctx->xd()) : default_variant(ctx);
     spg_status s = build_plan(ctx, v, ctx->opt.zchunk);
     if (s != SPG_OK) {
         std::string m = "spg_create: " + ctx->err;
@@ -629,7 +645,12 @@ spg_status spg_set_x(spg_ctx *ctx, int vol, const float *x)
     const int c = ctx->cur();
     spg_status s;
     if ((s = copy_volume_in(ctx, ctx->X[c], 4, d, x)) != SPG_OK) return s;
-    if ((s = copy_volume_in(ctx, ctx->X[(c + 2) % 3], 4, d, x)) != SPG_OK) return s;
+    if (ctx->xd()) {
+        CK(cudaMemsetAsync(ctx->X[ctx->aux_of(c)] + d.off, 0, (size_t)d.pitch * d.ny * d.nz * 4, ctx->stream),
+           "reset increment");
+    } else if ((s = copy_volume_in(ctx, ctx->X[ctx->aux_of(c)], 4, d, x)) != SPG_OK) {
+        return s;
+    }
     return SPG_OK;
 }
 
@@ -727,7 +748,10 @@ spg_status spg_certificate(spg_ctx *ctx, int vol, double *out)
     if (!ctx->reweighted || ctx->k_round < 1)
         return fail(ctx, SPG_ENOTREADY, "spg_certificate: needs one iteration in the current round");
     const int c = ctx->cur();
-    const float *xb[3] = {ctx->X[c], ctx->X[(c + 2) % 3], ctx->X[(c + 1) % 3]};
+    // x_{k+1} = X[c]; x_k and its pair are one rotation back
+    const int k = (c + ctx->nbuf() - 1) % ctx->nbuf();
+    const float *xb[4] = {ctx->X[c], ctx->X[k], ctx->xd() ? nullptr : ctx->X[ctx->aux_of(k)],
+                          ctx->xd() ? ctx->X[ctx->aux_of(k)] : nullptr};
     CK(launch_certificate(aux_params(ctx), xb, ctx->beta_d, ctx->B, ctx->W, ctx->bf16(), ctx->OMTV, ctx->stream),
        "certificate");
     ctx->launches += 1;
@@ -761,8 +785,8 @@ spg_status spg_get_state(spg_ctx *ctx, void *blob, size_t *size)
     }
     if (*size < need) return fail(ctx, SPG_EINVAL, "spg_get_state: buffer too small");
     char *p = static_cast<char *>(blob);
-    StateHeader h{kStateMagic, 1, ctx->nvol, ctx->k_round, ctx->reweighted ? 1 : 0, ctx->k_total,
-                  (int32_t)ctx->opt.data_dtype, (int32_t)ctx->opt.momentum};
+    StateHeader h{kStateMagic, 2, ctx->nvol, ctx->k_round, ctx->reweighted ? 1 : 0, ctx->k_total,
+                  (int32_t)ctx->opt.data_dtype, (int32_t)ctx->opt.momentum, (int32_t)ctx->opt.iterate_storage, 0};
     std::memcpy(p, &h, sizeof(h));
     p += sizeof(h);
     std::vector<VolDesc> dev(ctx->nvol);
@@ -775,7 +799,7 @@ spg_status spg_get_state(spg_ctx *ctx, void *blob, size_t *size)
         spg_status s;
         if ((s = copy_volume_out(ctx, p, ctx->X[c], 4, d)) != SPG_OK) return s;
         p += vb;
-        if ((s = copy_volume_out(ctx, p, ctx->X[(c + 2) % 3], 4, d)) != SPG_OK) return s;
+        if ((s = copy_volume_out(ctx, p, ctx->X[ctx->aux_of(c)], 4, d)) != SPG_OK) return s;
         p += vb;
         if ((s = copy_volume_out(ctx, p, ctx->OM1, 4, d)) != SPG_OK) return s;
         p += vb;
@@ -801,11 +825,12 @@ spg_status spg_set_state(spg_ctx *ctx, const void *blob, size_t size)
     StateHeader h;
     std::memcpy(&h, p, sizeof(h));
     p += sizeof(h);
-    if (h.magic != kStateMagic || h.version != 1 || h.nvol != ctx->nvol || h.dtype != (int)ctx->opt.data_dtype ||
-        h.momentum != (int)ctx->opt.momentum)
+    if (h.magic != kStateMagic || h.version != 2 || h.nvol != ctx->nvol || h.dtype != (int)ctx->opt.data_dtype ||
+        h.momentum != (int)ctx->opt.momentum || h.storage != (int)ctx->opt.iterate_storage)
         return fail(ctx, SPG_EINVAL, "spg_set_state: blob does not match this context");
     CK(cudaStreamSynchronize(ctx->stream), "synchronise");
-    // x_k goes to X[0], x_{k-1} to X[2]; the device state names X[0] as current
+    // x_k goes to X[0] and its pair (d_k or x_{k-1}) to its pair buffer; the
+    // device state names X[0] as current
     std::vector<VolDesc> dev(ctx->nvol);
     CK(cudaMemcpy(dev.data(), ctx->vols_d, ctx->nvol * sizeof(VolDesc), cudaMemcpyDeviceToHost), "read descriptors");
     for (int j = 0; j < ctx->nvol; j++) {
@@ -814,7 +839,7 @@ spg_status spg_set_state(spg_ctx *ctx, const void *blob, size_t size)
         spg_status s;
         if ((s = copy_volume_in(ctx, ctx->X[0], 4, d, p)) != SPG_OK) return s;
         p += vb;
-        if ((s = copy_volume_in(ctx, ctx->X[2], 4, d, p)) != SPG_OK) return s;
+        if ((s = copy_volume_in(ctx, ctx->X[ctx->aux_of(0)], 4, d, p)) != SPG_OK) return s;
         p += vb;
         if ((s = copy_volume_in(ctx, ctx->OM1, 4, d, p)) != SPG_OK) return s;
         p += vb;
@@ -840,7 +865,7 @@ spg_status spg_set_state(spg_ctx *ctx, const void *blob, size_t size)
     CK(cudaMemcpy(ctx->st_d, &st, sizeof(st), cudaMemcpyHostToDevice), "write state");
     ctx->k_round = h.k_round;
     ctx->k_total = h.k_total;
-    ctx->cur0 = (int)(((-h.k_total) % 3 + 3) % 3);
+    ctx->cur0 = (int)(((-h.k_total) % ctx->nbuf() + ctx->nbuf()) % ctx->nbuf());
     ctx->reweighted = h.reweighted != 0;
     return SPG_OK;
 }
@@ -992,6 +1017,132 @@ spg_status spg_probe_timeout(spg_ctx *ctx, long long timeout_ns)
     CK(launch_timeout_probe(ctx->st_d, timeout_ns, ctx->stream), "timeout probe");
     ctx->launches += 1;
     return device_status(ctx);
+}
+
+namespace {
+
+std::string tune_key(const spg_ctx *ctx)
+{
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    std::string k = std::string(prop.name) + "|" + std::to_string(prop.multiProcessorCount) + "|" +
+                    (ctx->bf16() ? "bf16" : "f32") + "|" + (ctx->xd() ? "delta" : "prev") + "|";
+    for (const auto &d : ctx->vols_h) k += std::to_string(d.nx) + "x" + std::to_string(d.ny) + "x" + std::to_string(d.nz) + ";";
+    for (auto &c : k)
+        if (c == ' ') c = '_';
+    return k;
+}
+
+bool cache_lookup(const std::string &key, int *tile, int *zchunk)
+{
+    const char *path = std::getenv("SPG_AUTOTUNE_CACHE");
+    if (!path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char kbuf[4096];
+    int t = 0, z = 0;
+    bool found = false;
+    while (std::fscanf(f, "%4095s %d %d", kbuf, &t, &z) == 3)
+        if (key == kbuf) {
+            *tile = t;
+            *zchunk = z;
+            found = true;
+        }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const std::string &key, int tile, int zchunk)
+{
+    const char *path = std::getenv("SPG_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d\n", key.c_str(), tile, zchunk);
+    std::fclose(f);
+}
+
+}  // namespace
+
+spg_status spg_autotune(spg_ctx *ctx, int trial_iters, int info[6])
+{
+    if (!ctx || trial_iters < 1) return fail(ctx, SPG_EINVAL, "spg_autotune: bad arguments");
+    if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_autotune: call spg_reweight first");
+    const std::string key = tune_key(ctx);
+    int tile = 0, zc = 0;
+    spg_status s;
+    if (cache_lookup(key, &tile, &zc)) {
+        s = build_plan(ctx, variant_from_tile(tile, ctx->bf16(), ctx->xd()), zc);
+        if (s != SPG_OK) return s;
+        return spg_plan_info(ctx, info);
+    }
+    // save what the trial iterations change: the iterate pair, device state, history ring
+    const size_t vb = (size_t)ctx->total * 4;
+    const int c0 = ctx->cur();
+    Scratch sc;
+    float *sx = nullptr, *sa = nullptr;
+    CK(sc.get(&sx, vb), "alloc");
+    CK(sc.get(&sa, vb), "alloc");
+    CK(cudaMemcpyAsync(sx, ctx->X[c0], vb, cudaMemcpyDeviceToDevice, ctx->stream), "save");
+    CK(cudaMemcpyAsync(sa, ctx->X[ctx->aux_of(c0)], vb, cudaMemcpyDeviceToDevice, ctx->stream), "save");
+    DevState st0;
+    CK(cudaMemcpyAsync(&st0, ctx->st_d, sizeof(st0), cudaMemcpyDeviceToHost, ctx->stream), "save state");
+    std::vector<double> hist0((size_t)ctx->hist_cap * ctx->nvol * 5);
+    CK(cudaMemcpyAsync(hist0.data(), ctx->hist_d, hist0.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+       "save history");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    const long long kt0 = ctx->k_total;
+    const int kr0 = ctx->k_round;
+    auto restore = [&]() -> spg_status {
+        CK(cudaMemcpyAsync(ctx->X[c0], sx, vb, cudaMemcpyDeviceToDevice, ctx->stream), "restore");
+        CK(cudaMemcpyAsync(ctx->X[ctx->aux_of(c0)], sa, vb, cudaMemcpyDeviceToDevice, ctx->stream), "restore");
+        CK(cudaMemcpyAsync(ctx->st_d, &st0, sizeof(st0), cudaMemcpyHostToDevice, ctx->stream), "restore state");
+        CK(cudaMemcpyAsync(ctx->hist_d, hist0.data(), hist0.size() * sizeof(double), cudaMemcpyHostToDevice,
+                           ctx->stream),
+           "restore history");
+        CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+        ctx->k_total = kt0;
+        ctx->k_round = kr0;
+        return SPG_OK;
+    };
+    const int tiles[] = {SPG_TILE_128x7, SPG_TILE_128x8, SPG_TILE_128x15, SPG_TILE_128x4,
+                         SPG_TILE_64x7,  SPG_TILE_64x8,  SPG_TILE_64x4};
+    const int zchunks[] = {0, 64, 32};
+    const int trial = std::min(trial_iters, ctx->max_iters - ctx->k_round - 4);
+    if (trial < 1) return fail(ctx, SPG_EINVAL, "spg_autotune: no room left in the round for trials");
+    float best_ms = 1e30f;
+    int best_tile = tile_code(ctx->var), best_z = ctx->opt.zchunk;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    for (int t : tiles)
+        for (int z : zchunks) {
+            if ((s = build_plan(ctx, variant_from_tile(t, ctx->bf16(), ctx->xd()), z)) != SPG_OK) continue;
+            if ((s = launch_steps(ctx, 2)) != SPG_OK) break;  // warm-up (graph capture happens here too)
+            cudaEventRecord(e0, ctx->stream);
+            if ((s = launch_steps(ctx, trial)) != SPG_OK) break;
+            cudaEventRecord(e1, ctx->stream);
+            CK(cudaEventSynchronize(e1), "time trial");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_tile = t;
+                best_z = z;
+            }
+            if ((s = restore()) != SPG_OK) break;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    spg_status rs = restore();
+    if (rs != SPG_OK) return rs;
+    if ((s = build_plan(ctx, variant_from_tile(best_tile, ctx->bf16(), ctx->xd()), best_z)) != SPG_OK) return s;
+    cache_store(key, best_tile, best_z);
+    spg_status ds = device_status(ctx);
+    if (ds != SPG_OK) return ds;
+    return spg_plan_info(ctx, info);
 }
 
 long long spg_launch_count(const spg_ctx *ctx) { return ctx ? ctx->launches : 0; }

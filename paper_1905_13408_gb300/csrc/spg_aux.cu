@@ -162,10 +162,14 @@ __global__ void to_f32_kernel(const uint16_t *src, float *dst, long long n)
 // Value of u = x_k + beta (x_k - x_{k-1}) is never formed; differences are
 // taken of x_k and of d = x_k - x_{k-1} separately (one rounding each).
 struct Field {
-    const float *xk, *xkm1;   // xkm1 may be null (then d = 0)
+    const float *xk, *xkm1;   // xkm1 may be null (then d = 0, unless dk is given)
     float beta;
+    const float *dk = nullptr;  // stored increment x_k - x_{k-1}, if any
     __device__ __forceinline__ float x(long long i) const { return xk[i]; }
-    __device__ __forceinline__ float d(long long i) const { return xkm1 ? xk[i] - xkm1[i] : 0.f; }
+    __device__ __forceinline__ float d(long long i) const
+    {
+        return dk ? dk[i] : (xkm1 ? xk[i] - xkm1[i] : 0.f);
+    }
 };
 
 // D u at (x, y, z) in volume V (Eq. 12, zero first planes).
@@ -345,7 +349,7 @@ __global__ void objective_kernel(AuxParams a, const float *xcur, const void *b, 
 // r = grad f(x+) - grad f(y) + (y - x+)/tau
 //   = (y - x+)(1/tau - w) + lambda_tv (D^T p(x+) - D^T p(y)),  y - x+ = (x_k - x+) + beta d.
 __global__ void certificate_kernel(AuxParams a, const float *xplus, const float *xk, const float *xkm1,
-                                   const float *beta_tab, const void *b, const void *w, bool bf16,
+                                   const float *dk, const float *beta_tab, const void *b, const void *w, bool bf16,
                                    const float *omtv)
 {
     __shared__ double scratch[32 * 4];
@@ -356,14 +360,14 @@ __global__ void certificate_kernel(AuxParams a, const float *xplus, const float 
     const int z = plane - V.plane_begin;
     const int kr = a.st->k_round;
     const float beta = kr >= 1 ? beta_tab[kr - 1] : 0.f;
-    const Field Fy{xk, xkm1, beta};
+    const Field Fy{xk, xkm1, beta, dk};
     const Field Fx{xplus, nullptr, 0.f};
     (void)b;
     KSum ks;
     for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
         const int x = t % V.nx, y = t / V.nx;
         const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
-        const float dy = (xk[i] - xplus[i]) + beta * (xk[i] - xkm1[i]);
+        const float dy = (xk[i] - xplus[i]) + beta * Fy.d(i);
         const float dv = div_at(V, Fx, omtv, x, y, z) - div_at(V, Fy, omtv, x, y, z);
         const float r = dy * (1.0f / V.tau - ld_data(w, bf16, i)) + V.lambda_tv * dv;
         ks.add(r * r);
@@ -539,8 +543,8 @@ cudaError_t launch_objective(const AuxParams &a, const float *const *xbuf, const
 cudaError_t launch_certificate(const AuxParams &a, const float *const *xbuf, const float *beta, const void *b,
                                const void *w, bool bf16, const float *omtv, cudaStream_t s)
 {
-    // xbuf = {x_{k+1}, x_k, x_{k-1}}
-    certificate_kernel<<<a.nplanes, AUX_THREADS, 0, s>>>(a, xbuf[0], xbuf[1], xbuf[2], beta, b, w, bf16, omtv);
+    certificate_kernel<<<a.nplanes, AUX_THREADS, 0, s>>>(a, xbuf[0], xbuf[1], xbuf[2], xbuf[3], beta, b, w, bf16,
+                                                         omtv);
     return cudaGetLastError();
 }
 

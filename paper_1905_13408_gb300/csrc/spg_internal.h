@@ -8,7 +8,10 @@
 //  - inside a volume, rows of nx elements are padded to `pitch` elements
 //    (a multiple of 8: 32-byte rows for float32, 16-byte for bfloat16), the
 //    layout the TMA tensor maps and the 16-byte vector stores need;
-//  - X[0..2] rotate as x_{k-1}, x_k, x_{k+1}; DevState::cur names x_k.
+//  - iterates: with increment storage (default) x lives in X[0..1] and the
+//    increment d_k = x_k - x_{k-1} in X[2..3] (ping-pong, DevState::cur names
+//    x_k = X[cur], d_k = X[2+cur]); with previous-iterate storage X[0..2]
+//    rotate as x_{k-1}, x_k, x_{k+1} and DevState::cur names x_k.
 #pragma once
 
 #include <cuda.h>
@@ -37,11 +40,10 @@ struct WorkItem {
 
 // Tensor maps of one volume (device memory, 64-byte aligned).
 struct TmapSet {
-    CUtensorMap x[3];   // iterate buffers, box (TX+8) x (TY+2) x 1, origin (x0-4, y0-1, z)
+    CUtensorMap x[4];   // iterate buffers, box (TX+8) x (TY+2) x 1, origin (x0-4, y0-1, z)
     CUtensorMap omtv;   // TV weights,      box (TX+4) x (TY+1) x 1, origin (x0, y0, z)
     CUtensorMap b, w;   // data and weight, box TX x TY x 1,         origin (x0, y0, z-1)
     CUtensorMap om1;    // l1 weights,      box TX x TY x 1
-    CUtensorMap spare;
 };
 
 // Device-resident solver state; the last CTA of each fused step advances it,
@@ -62,7 +64,7 @@ struct StepParams {
     const VolDesc *vols;
     const WorkItem *items;
     const TmapSet *tmaps;
-    float *xbuf[3];
+    float *xbuf[4];
     const float *beta;       // extrapolation table beta_k (float32)
     DevState *st;
     double *partials;        // [nitems][3] objective partial sums of the last recorded step
@@ -75,6 +77,7 @@ struct StepParams {
 struct StepVariant {
     int vx, ty, stages;
     bool bf16;
+    bool xd;   // x_k and the increment d_k are stored (instead of x_k and x_{k-1})
 };
 
 // Host-callable launchers (spg_step.cu).
@@ -102,6 +105,7 @@ cudaError_t launch_reweight(const AuxParams &a, const float *const *xbuf, float 
                             const double *maxw, double *rstats, VolDesc *vols_rw, cudaStream_t s);
 cudaError_t launch_objective(const AuxParams &a, const float *const *xbuf, const void *b, const void *w,
                              bool bf16, const float *om1, const float *omtv, cudaStream_t s);
+// xbuf = {x_{k+1}, x_k, x_{k-1} or null, d_k or null}
 cudaError_t launch_certificate(const AuxParams &a, const float *const *xbuf, const float *beta,
                                const void *b, const void *w, bool bf16, const float *omtv, cudaStream_t s);
 

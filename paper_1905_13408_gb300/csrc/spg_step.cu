@@ -1,537 +1,16 @@
-// Fused smoothing-proximal-gradient iteration for sm_103a (one launch per
-// iteration for every volume of a context).
-//
-// Per voxel v the launch computes, from x_k, x_{k-1}, b, w, om1, omtv
-// (Sec. 2.1 Eq. 12, 16, 17, 20, 21; Sec. 2.2 Eq. 28 data term):
-//   d      = x_k - x_{k-1}
-//   (Dy)_a = [v_a >= 1] ((x_k[v] - x_k[v-e_a]) + beta (d[v] - d[v-e_a]))       Eq. 12 on y
-//   p_a    = omtv_v (Dy)_a / max(mu, |Dy_v|)                                   Eq. 16, weighted
-//   div    = sum_a p_a[v] - p_a[v+e_a]                                          Eq. 17
-//   g      = w ((x_k - b) + beta d) + lambda_tv div                             grad f(y)
-//   delta  = beta d - tau g,  z = x_k + delta                                   Eq. 20
-//   x_{k+1} = 0 if |z| < t else x_k + (delta - t sign z),  t = tau lambda_l1 om1   Eq. 21
-// and, when the step is recorded, the three sums of F(x_k) (data, l1, TV).
-//
-// y = x_k + beta d is never rounded on its own: differences and the data
-// residual are formed from x_k and d separately, and the update is added to
-// x_k once, so each iteration commits a single float32 rounding per voxel.
-//
-// Data movement: a CTA owns an x-y tile (TX = 32*VX by TY voxels) and marches
-// over z. Each z-step's inputs arrive by TMA (cp.async.bulk.tensor) into one
-// of S shared-memory stages, tracked by an mbarrier: x_k and x_{k-1} with a
-// one-voxel x-y halo (the box starts 4 elements left of the tile so the
-// innermost coordinate stays 16-byte aligned), omtv with a +1 halo, and b, w,
-// om1 of the plane being written. Plane z's p is computed while plane z-1 is
-// written, so each voxel's inputs are read from HBM once per iteration; the
-// halo rows come from L2 because neighbouring tiles march the same planes at
-// the same time. Warp r of TY computes row r; one extra warp computes the +y
-// halo row and the +x halo column. p_y crosses warps through a 3-deep shared
-// ring, p_x through a lane shuffle; p_z and the z-1 values stay in registers.
-#include <cuda_bf16.h>
-
-#include "spg_internal.h"
+// Dispatch of the fused step over data dtypes, and the bounded-wait probe.
+#include "spg_step_kernel.cuh"
 
 namespace spg {
+
+size_t step_smem_bytes_f32(const StepVariant &v);
+size_t step_smem_bytes_bf16(const StepVariant &v);
+cudaError_t step_configure_f32(const StepVariant &v, int *occ);
+cudaError_t step_configure_bf16(const StepVariant &v, int *occ);
+cudaError_t step_launch_f32(const StepVariant &v, int grid, const StepParams &p, cudaStream_t s);
+cudaError_t step_launch_bf16(const StepVariant &v, int grid, const StepParams &p, cudaStream_t s);
+
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, int count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ long long global_ns()
-{
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait: false when `limit_ns` passed without the phase completing.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit_ns)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = global_ns();
-    for (;;) {
-        for (int i = 0; i < 32; i++)
-            if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-}
-
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
-                                            uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
-{
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
-}
-
-// Compensated float32 accumulator (Kahan): per-thread objective sums.
-struct KSum {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v)
-    {
-        float y = v - c;
-        float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
-
-template <int VX>
-__device__ __forceinline__ void ld_vec(const float *p, float (&v)[VX])
-{
-    if constexpr (VX == 4) {
-        float4 t = *reinterpret_cast<const float4 *>(p);
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-    } else if constexpr (VX == 2) {
-        float2 t = *reinterpret_cast<const float2 *>(p);
-        v[0] = t.x; v[1] = t.y;
-    } else {
-        v[0] = p[0];
-    }
-}
-
-template <int VX>
-__device__ __forceinline__ void st_vec(float *p, const float (&v)[VX])
-{
-    if constexpr (VX == 4) {
-        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    } else if constexpr (VX == 2) {
-        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
-    } else {
-        p[0] = v[0];
-    }
-}
-
-__device__ __forceinline__ float bf16_bits_to_f32(uint32_t h) { return __uint_as_float(h << 16); }
-
-// Load VX data values stored as float32 or bfloat16 (raw bits widened exactly).
-template <int VX, bool BF16>
-__device__ __forceinline__ void ld_data(const unsigned char *tile, int idx, float (&v)[VX])
-{
-    if constexpr (!BF16) {
-        ld_vec<VX>(reinterpret_cast<const float *>(tile) + idx, v);
-    } else {
-        const uint16_t *t = reinterpret_cast<const uint16_t *>(tile) + idx;
-        if constexpr (VX == 4) {
-            uint2 u = *reinterpret_cast<const uint2 *>(t);
-            v[0] = bf16_bits_to_f32(u.x & 0xffffu); v[1] = bf16_bits_to_f32(u.x >> 16);
-            v[2] = bf16_bits_to_f32(u.y & 0xffffu); v[3] = bf16_bits_to_f32(u.y >> 16);
-        } else if constexpr (VX == 2) {
-            uint32_t u = *reinterpret_cast<const uint32_t *>(t);
-            v[0] = bf16_bits_to_f32(u & 0xffffu); v[1] = bf16_bits_to_f32(u >> 16);
-        } else {
-            v[0] = bf16_bits_to_f32(t[0]);
-        }
-    }
-}
-
-template <int VX, int TY, int S, bool BF16>
-struct Cfg {
-    static constexpr int TX = 32 * VX;
-    static constexpr int XW = TX + 8, XH = TY + 2;   // x tiles: origin (x0-4, y0-1)
-    static constexpr int OW = TX + 4, OH = TY + 1;   // omtv tile: origin (x0, y0)
-    static constexpr int ES = BF16 ? 2 : 4;
-    static constexpr int XT_BYTES = XW * XH * 4;
-    static constexpr int OM_BYTES = OW * OH * 4;
-    static constexpr int BW_BYTES = TX * TY * ES;
-    static constexpr int O1_BYTES = TX * TY * 4;
-    static constexpr int al(int n) { return (n + 127) / 128 * 128; }
-    static constexpr int OFF_XK = 0;
-    static constexpr int OFF_XM = OFF_XK + al(XT_BYTES);
-    static constexpr int OFF_OM = OFF_XM + al(XT_BYTES);
-    static constexpr int OFF_B = OFF_OM + al(OM_BYTES);
-    static constexpr int OFF_W = OFF_B + al(BW_BYTES);
-    static constexpr int OFF_O1 = OFF_W + al(BW_BYTES);
-    static constexpr int STAGE = OFF_O1 + al(O1_BYTES);
-    static constexpr int OFF_PY = S * STAGE;                  // 3 x (TY+1) x TX floats
-    static constexpr int OFF_HX = OFF_PY + al(3 * (TY + 1) * TX * 4);  // 3 x 32 floats
-    static constexpr int OFF_RED = OFF_HX + 3 * 32 * 4;       // 32 x 3 doubles
-    static constexpr int OFF_BAR = OFF_RED + 32 * 3 * 8;      // S mbarriers
-    static constexpr int OFF_ST = OFF_BAR + al(S * 8);        // state snapshot
-    static constexpr int TOTAL = OFF_ST + 128 + 128;          // + alignment slack
-    static constexpr int THREADS = 32 * (TY + 1);
-    static_assert(TY + 1 <= 32, "reduction scratch sized for at most 32 warps");
-    static_assert(TY <= 32, "halo column handled by one lane per row");
-};
-
-// Producer (one thread): stage contents for step j of work item W, i.e.
-// plane z = z0-1+j of x_k and x_{k-1} (with halo) and of omtv, and plane z-1
-// of b, w and om1. Steps 0 and 1 skip what they do not consume.
-template <class C, int S>
-__device__ __forceinline__ void issue_stage(unsigned char *sm, uint64_t *bars, const TmapSet *tm,
-                                            const WorkItem &W, int cur, int prv, long long gstep, int j)
-{
-    const int s = (int)((gstep + j) % S);
-    unsigned char *base = sm + s * C::STAGE;
-    const int z = W.z0 - 1 + j;
-    const bool need_om = j >= 1, need_bwo = j >= 2;
-    const uint32_t bytes = 2 * C::XT_BYTES + (need_om ? C::OM_BYTES : 0) +
-                           (need_bwo ? 2 * C::BW_BYTES + C::O1_BYTES : 0);
-    mbar_arrive_expect_tx(&bars[s], bytes);
-    tma_load_3d(base + C::OFF_XK, &tm->x[cur], W.x0 - 4, W.y0 - 1, z, &bars[s]);
-    tma_load_3d(base + C::OFF_XM, &tm->x[prv], W.x0 - 4, W.y0 - 1, z, &bars[s]);
-    if (need_om) tma_load_3d(base + C::OFF_OM, &tm->omtv, W.x0, W.y0, z, &bars[s]);
-    if (need_bwo) {
-        tma_load_3d(base + C::OFF_B, &tm->b, W.x0, W.y0, z - 1, &bars[s]);
-        tma_load_3d(base + C::OFF_W, &tm->w, W.x0, W.y0, z - 1, &bars[s]);
-        tma_load_3d(base + C::OFF_O1, &tm->om1, W.x0, W.y0, z - 1, &bars[s]);
-    }
-}
-
-struct StateSnap {
-    int cur, k_round, rec, last;
-    long long k_total;
-    float beta, pad;
-};
-
-template <int VX, int TY, int S, bool BF16>
-__global__ void __launch_bounds__(32 * (TY + 1))
-    spg_step_kernel(const StepParams P)
-{
-    using C = Cfg<VX, TY, S, BF16>;
-    constexpr int TX = C::TX, XW = C::XW, OW = C::OW;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char *sm = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::OFF_BAR);
-    float *py_ring = reinterpret_cast<float *>(sm + C::OFF_PY);
-    float *hx_ring = reinterpret_cast<float *>(sm + C::OFF_HX);
-    double *red = reinterpret_cast<double *>(sm + C::OFF_RED);
-    StateSnap *snap = reinterpret_cast<StateSnap *>(sm + C::OFF_ST);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool main_warp = warp < TY;
-    const int r = warp;  // tile row handled by this warp (TY = the +y halo row)
-
-    if (tid == 0) {
-        volatile DevState *st = P.st;
-        StateSnap s;
-        s.cur = st->cur;
-        s.k_round = st->k_round;
-        s.k_total = st->k_total;
-        s.rec = (P.hist_every > 0 && (s.k_total % P.hist_every) == 0) ? 1 : 0;
-        s.beta = P.beta[s.k_round];
-        s.last = 0;
-        *snap = s;
-        for (int i = 0; i < S; i++) mbar_init(&bars[i], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    const int cur = snap->cur, prv = (cur + 2) % 3, nxt = (cur + 1) % 3;
-    const float beta = snap->beta;
-    const bool rec = snap->rec != 0;
-    // select without indexing the parameter array (keeps the parameters out of local memory)
-    float *const xout_base = nxt == 0 ? P.xbuf[0] : (nxt == 1 ? P.xbuf[1] : P.xbuf[2]);
-
-    long long gstep = 0;  // steps consumed by this CTA so far (stage / parity bookkeeping)
-    int aborted = 0;
-    long long issued_upto = 0;  // steps issued (global count) for the drain on abort
-    long long drain_from = 0;   // first step whose barrier may still be pending after an abort
-
-    for (int it = blockIdx.x; it < P.nitems && !aborted; it += gridDim.x) {
-        const WorkItem W = P.items[it];
-        const VolDesc V = P.vols[W.vol];
-        const TmapSet *tm = P.tmaps + W.vol;
-        const int nsteps = (W.z1 - W.z0) + 2;
-        const float tau = V.tau, lam_tv = V.lambda_tv, tl1 = V.tau * V.lambda_l1;
-        const float inv_mu = 1.0f / V.mu, half_inv_mu = 0.5f / V.mu, half_mu = 0.5f * V.mu;
-        const float mu2 = V.mu * V.mu;
-
-        if (tid == 0) {
-            if (it == (int)blockIdx.x) {
-                prefetch_tmap(&tm->x[cur]);
-                prefetch_tmap(&tm->x[prv]);
-                prefetch_tmap(&tm->omtv);
-                prefetch_tmap(&tm->b);
-                prefetch_tmap(&tm->w);
-                prefetch_tmap(&tm->om1);
-            }
-            const int pro = nsteps < S ? nsteps : S;
-            for (int j = 0; j < pro; j++) issue_stage<C, S>(sm, bars, tm, W, cur, prv, gstep, j);
-            issued_upto = gstep + pro;
-        }
-
-        // Registers carried across z-steps.
-        float xz[VX], dz[VX];         // x_k and d on plane z-1, own columns
-        float pp[3][VX];              // p on plane z-1, own columns
-        float cxz = 0.f, cdz = 0.f;   // halo column (+x) values on plane z-1
-#pragma unroll
-        for (int i = 0; i < VX; i++) {
-            xz[i] = 0.f; dz[i] = 0.f;
-            pp[0][i] = pp[1][i] = pp[2][i] = 0.f;
-        }
-        KSum kd, kl, kt;
-
-        const int gy = W.y0 + r;
-        const int gx0 = W.x0 + VX * lane;
-        const bool col_lane = (warp == TY) && (lane < TY);
-
-        for (int j = 0; j < nsteps; j++) {
-            const int s = (int)((gstep + j) % S);
-            const uint32_t parity = (uint32_t)(((gstep + j) / S) & 1);
-            const unsigned char *base = sm + s * C::STAGE;
-            const float *XK = reinterpret_cast<const float *>(base + C::OFF_XK);
-            const float *XM = reinterpret_cast<const float *>(base + C::OFF_XM);
-            const float *OM = reinterpret_cast<const float *>(base + C::OFF_OM);
-            const int z = W.z0 - 1 + j;
-
-            const bool ok = mbar_wait(&bars[s], parity, P.timeout_ns);
-
-            // ---- A: p on plane z at this thread's columns ----
-            const int tr = r + 1;  // tile row of this thread's voxel row
-            float xc[VX], mc[VX], xu[VX], mu_[VX], dc[VX], du[VX];
-            ld_vec<VX>(XK + tr * XW + 4 + VX * lane, xc);
-            ld_vec<VX>(XM + tr * XW + 4 + VX * lane, mc);
-            ld_vec<VX>(XK + (tr - 1) * XW + 4 + VX * lane, xu);
-            ld_vec<VX>(XM + (tr - 1) * XW + 4 + VX * lane, mu_);
-            float xl = __shfl_up_sync(FULL, xc[VX - 1], 1);
-            float ml = __shfl_up_sync(FULL, mc[VX - 1], 1);
-            if (lane == 0) {
-                xl = XK[tr * XW + 3];
-                ml = XM[tr * XW + 3];
-            }
-            const float dl = xl - ml;
-#pragma unroll
-            for (int i = 0; i < VX; i++) {
-                dc[i] = xc[i] - mc[i];
-                du[i] = xu[i] - mu_[i];
-            }
-            float pc[3][VX];
-            if (j >= 1) {
-                float om[VX];
-                ld_vec<VX>(OM + r * OW + VX * lane, om);
-                const bool rowok = gy < V.ny && z < V.nz;
-#pragma unroll
-                for (int i = 0; i < VX; i++) {
-                    const int gx = gx0 + i;
-                    const float lx = i ? xc[i - 1] : xl;
-                    const float ld = i ? dc[i - 1] : dl;
-                    const float ex = xc[i] - lx, ey = xc[i] - xu[i], ez = xc[i] - xz[i];
-                    const float ax = gx >= 1 ? ex + beta * (dc[i] - ld) : 0.f;
-                    const float ay = gy >= 1 ? ey + beta * (dc[i] - du[i]) : 0.f;
-                    const float az = z >= 1 ? ez + beta * (dc[i] - dz[i]) : 0.f;
-                    const float s2 = ax * ax + ay * ay + az * az;
-                    const bool in = rowok && gx < V.nx;
-                    const float sc = in ? om[i] * fminf(inv_mu, rsqrtf(s2)) : 0.f;
-                    pc[0][i] = ax * sc;
-                    pc[1][i] = ay * sc;
-                    pc[2][i] = az * sc;
-                    if (rec && main_warp && in && z < W.z1) {
-                        const float qx = gx >= 1 ? ex : 0.f, qy = gy >= 1 ? ey : 0.f, qz = z >= 1 ? ez : 0.f;
-                        const float q = qx * qx + qy * qy + qz * qz;
-                        const float h = q <= mu2 ? q * half_inv_mu : sqrtf(q) - half_mu;
-                        kt.add(om[i] * h);
-                    }
-                }
-                // +x halo column (p_x only is consumed), one lane per tile row
-                if (col_lane) {
-                    const int cr = lane + 1, cc = TX + 4;
-                    const float cx = XK[cr * XW + cc], cm = XM[cr * XW + cc];
-                    const float cxl = XK[cr * XW + cc - 1], cml = XM[cr * XW + cc - 1];
-                    const float cxu = XK[(cr - 1) * XW + cc], cmu = XM[(cr - 1) * XW + cc];
-                    const float cd = cx - cm;
-                    const int hx = W.x0 + TX, hy = W.y0 + lane;
-                    const float ax = (cx - cxl) + beta * (cd - (cxl - cml));
-                    const float ay = hy >= 1 ? (cx - cxu) + beta * (cd - (cxu - cmu)) : 0.f;
-                    const float az = z >= 1 ? (cx - cxz) + beta * (cd - cdz) : 0.f;
-                    const float s2 = ax * ax + ay * ay + az * az;
-                    const bool in = hx < V.nx && hy < V.ny && z < V.nz;
-                    const float sc = in ? OM[lane * OW + TX] * fminf(inv_mu, rsqrtf(s2)) : 0.f;
-                    hx_ring[(j % 3) * 32 + lane] = ax * sc;
-                }
-                // p_y of this row for the warp above (or, for the halo warp, for row TY-1)
-                st_vec<VX>(py_ring + ((j % 3) * (TY + 1) + r) * TX + VX * lane, pc[1]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < VX; i++) pc[0][i] = pc[1][i] = pc[2][i] = 0.f;
-            }
-            if (col_lane) {
-                const int cr = lane + 1, cc = TX + 4;
-                const float cx = XK[cr * XW + cc], cm = XM[cr * XW + cc];
-                cxz = cx;
-                cdz = cx - cm;
-            }
-
-            const int any_abort = __syncthreads_or(ok ? 0 : 1);
-            if (any_abort) {
-                aborted = 1;
-                drain_from = gstep + j;
-                break;
-            }
-            // refill the stage consumed in step j-1
-            if (tid == 0 && j >= 1 && j - 1 + S < nsteps) {
-                issue_stage<C, S>(sm, bars, tm, W, cur, prv, gstep, j - 1 + S);
-                issued_upto = gstep + j - 1 + S + 1;
-            }
-
-            // ---- B: write plane z-1 ----
-            if (main_warp && j >= 2) {
-                const int zo = z - 1;
-                float bb[VX], ww[VX], oo[VX], pyd[VX];
-                ld_data<VX, BF16>(base + C::OFF_B, r * TX + VX * lane, bb);
-                ld_data<VX, BF16>(base + C::OFF_W, r * TX + VX * lane, ww);
-                ld_vec<VX>(reinterpret_cast<const float *>(base + C::OFF_O1) + r * TX + VX * lane, oo);
-                ld_vec<VX>(py_ring + (((j - 1) % 3) * (TY + 1) + r + 1) * TX + VX * lane, pyd);
-                float pxn = __shfl_down_sync(FULL, pp[0][0], 1);
-                if (lane == 31) pxn = hx_ring[((j - 1) % 3) * 32 + r];
-                float out[VX];
-                const bool rowok = gy < V.ny;
-#pragma unroll
-                for (int i = 0; i < VX; i++) {
-                    const float pxr = (i < VX - 1) ? pp[0][(i + 1) % VX] : pxn;
-                    const float div = (pp[0][i] - pxr) + (pp[1][i] - pyd[i]) + (pp[2][i] - pc[2][i]);
-                    const float g = ww[i] * ((xz[i] - bb[i]) + beta * dz[i]) + lam_tv * div;
-                    const float delta = beta * dz[i] - tau * g;
-                    const float zz = xz[i] + delta;
-                    const float t = tl1 * oo[i];
-                    out[i] = fabsf(zz) < t ? 0.f : xz[i] + (zz > 0.f ? delta - t : delta + t);
-                    if (rec && rowok && gx0 + i < V.nx) {
-                        const float rr = xz[i] - bb[i];
-                        kd.add(0.5f * ww[i] * rr * rr);
-                        kl.add(oo[i] * fabsf(xz[i]));
-                    }
-                }
-                if (rowok && gx0 < V.pitch) {
-                    float *dst = xout_base + V.off + ((long long)zo * V.ny + gy) * V.pitch + gx0;
-                    st_vec<VX>(dst, out);
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < VX; i++) {
-                xz[i] = xc[i];
-                dz[i] = dc[i];
-                pp[0][i] = pc[0][i];
-                pp[1][i] = pc[1][i];
-                pp[2][i] = pc[2][i];
-            }
-        }
-
-        if (!aborted && rec) {
-            // block reduction of the item's three sums, fixed order
-            double v0 = kd.value(), v1 = kl.value(), v2 = kt.value();
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                v0 += __shfl_down_sync(FULL, v0, o);
-                v1 += __shfl_down_sync(FULL, v1, o);
-                v2 += __shfl_down_sync(FULL, v2, o);
-            }
-            if (lane == 0) {
-                red[warp * 3 + 0] = v0;
-                red[warp * 3 + 1] = v1;
-                red[warp * 3 + 2] = v2;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double a0 = 0, a1 = 0, a2 = 0;
-                for (int q = 0; q < TY + 1; q++) {
-                    a0 += red[q * 3 + 0];
-                    a1 += red[q * 3 + 1];
-                    a2 += red[q * 3 + 2];
-                }
-                P.partials[(long long)it * 3 + 0] = a0;
-                P.partials[(long long)it * 3 + 1] = a1;
-                P.partials[(long long)it * 3 + 2] = a2;
-            }
-        }
-        __syncthreads();  // every stage consumed before the next item's prologue
-        gstep += nsteps;
-    }
-
-    if (aborted && tid == 0) {
-        // record the timeout, then wait (bounded) for copies still in flight
-        atomicCAS(&P.st->err, 0, (int)SPG_ETIMEOUT);
-        for (long long q = drain_from; q < issued_upto; q++) {
-            const int s = (int)(q % S);
-            (void)mbar_wait(&bars[s], (uint32_t)((q / S) & 1), P.timeout_ns);
-        }
-    }
-
-    // ---- last CTA: per-volume objective, then advance the device state ----
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        const unsigned t = atomicAdd(&P.st->ticket, 1u);
-        snap->last = (t == gridDim.x - 1) ? 1 : 0;
-    }
-    __syncthreads();
-    if (!snap->last) return;
-    __threadfence();
-    if (rec) {
-        const int hslot = P.st->hist_count % P.hist_cap;
-        for (int v = warp; v < P.nvol; v += TY + 1) {
-            const VolDesc V = P.vols[v];
-            double a0 = 0, a1 = 0, a2 = 0;
-            for (int q = V.item_begin + lane; q < V.item_end; q += 32) {
-                a0 += __ldcg(P.partials + (long long)q * 3 + 0);
-                a1 += __ldcg(P.partials + (long long)q * 3 + 1);
-                a2 += __ldcg(P.partials + (long long)q * 3 + 2);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a0 += __shfl_down_sync(FULL, a0, o);
-                a1 += __shfl_down_sync(FULL, a1, o);
-                a2 += __shfl_down_sync(FULL, a2, o);
-            }
-            if (lane == 0) {
-                double *h = P.hist + ((long long)hslot * P.nvol + v) * 5;
-                const double l1 = (double)V.lambda_l1 * a1, tv = (double)V.lambda_tv * a2;
-                const double tot = a0 + l1 + tv;
-                h[0] = (double)snap->k_total;
-                h[1] = a0;
-                h[2] = l1;
-                h[3] = tv;
-                h[4] = tot;
-                if (!isfinite(tot)) atomicCAS(&P.st->err, 0, (int)SPG_ENONFINITE);
-            }
-        }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        DevState *st = P.st;
-        if (rec) st->hist_count = st->hist_count + 1;
-        st->cur = nxt;
-        st->k_round = snap->k_round + 1;
-        st->k_total = snap->k_total + 1;
-        st->ticket = 0;
-        __threadfence();
-    }
-}
 
 // Waits on a barrier that nothing ever arrives at, with the same bounded wait
 // as the fused step: it must give up after `limit_ns` and record SPG_ETIMEOUT.
@@ -547,30 +26,6 @@ __global__ void timeout_probe_kernel(DevState *st, long long limit_ns)
     if (!ok && threadIdx.x == 0) atomicCAS(&st->err, 0, (int)SPG_ETIMEOUT);
 }
 
-template <int VX, int TY, int S, bool BF16>
-struct Launcher {
-    using C = Cfg<VX, TY, S, BF16>;
-    static cudaError_t configure(int *ctas_per_sm)
-    {
-        auto k = spg_step_kernel<VX, TY, S, BF16>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::TOTAL);
-        if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k, C::THREADS, C::TOTAL);
-    }
-    static cudaError_t launch(int grid, const StepParams &p, cudaStream_t s)
-    {
-        spg_step_kernel<VX, TY, S, BF16><<<grid, C::THREADS, C::TOTAL, s>>>(p);
-        return cudaGetLastError();
-    }
-};
-
-// Every compiled variant: (vx, ty, stages).
-#define SPG_VARIANTS(X) \
-    X(4, 8, 3)          \
-    X(4, 4, 4)          \
-    X(2, 8, 4)          \
-    X(2, 4, 4)          \
-    X(4, 16, 2)
 
 }  // namespace
 
@@ -580,45 +35,18 @@ cudaError_t launch_timeout_probe(DevState *st, long long timeout_ns, cudaStream_
     return cudaGetLastError();
 }
 
-bool step_variant_supported(const StepVariant &v)
-{
-#define SPG_SUP(VX_, TY_, S_) \
-    if (v.vx == VX_ && v.ty == TY_ && v.stages == S_) return true;
-    SPG_VARIANTS(SPG_SUP)
-#undef SPG_SUP
-    return false;
-}
+bool step_variant_supported(const StepVariant &v) { return step_smem_bytes_f32(v) != 0; }
 
-size_t step_smem_bytes(const StepVariant &v)
-{
-#define SPG_SM(VX_, TY_, S_)                                                            \
-    if (v.vx == VX_ && v.ty == TY_ && v.stages == S_)                                   \
-        return v.bf16 ? Cfg<VX_, TY_, S_, true>::TOTAL : Cfg<VX_, TY_, S_, false>::TOTAL;
-    SPG_VARIANTS(SPG_SM)
-#undef SPG_SM
-    return 0;
-}
+size_t step_smem_bytes(const StepVariant &v) { return v.bf16 ? step_smem_bytes_bf16(v) : step_smem_bytes_f32(v); }
 
 cudaError_t step_configure(const StepVariant &v, int *ctas_per_sm)
 {
-#define SPG_CF(VX_, TY_, S_)                                                                   \
-    if (v.vx == VX_ && v.ty == TY_ && v.stages == S_)                                          \
-        return v.bf16 ? Launcher<VX_, TY_, S_, true>::configure(ctas_per_sm)                   \
-                      : Launcher<VX_, TY_, S_, false>::configure(ctas_per_sm);
-    SPG_VARIANTS(SPG_CF)
-#undef SPG_CF
-    return cudaErrorInvalidValue;
+    return v.bf16 ? step_configure_bf16(v, ctas_per_sm) : step_configure_f32(v, ctas_per_sm);
 }
 
 cudaError_t step_launch(const StepVariant &v, int grid, const StepParams &p, cudaStream_t s)
 {
-#define SPG_LN(VX_, TY_, S_)                                                                   \
-    if (v.vx == VX_ && v.ty == TY_ && v.stages == S_)                                          \
-        return v.bf16 ? Launcher<VX_, TY_, S_, true>::launch(grid, p, s)                       \
-                      : Launcher<VX_, TY_, S_, false>::launch(grid, p, s);
-    SPG_VARIANTS(SPG_LN)
-#undef SPG_LN
-    return cudaErrorInvalidValue;
+    return v.bf16 ? step_launch_bf16(v, grid, p, s) : step_launch_f32(v, grid, p, s);
 }
 
 }  // namespace spg

@@ -25,7 +25,8 @@ LIB_PATH = os.path.join(_HERE, "libspg.so")
 SPG_OK, SPG_EINVAL, SPG_ENOMEM, SPG_ECUDA, SPG_ENOTREADY, SPG_ENONFINITE, SPG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 SPG_F32, SPG_BF16 = 0, 1
 SPG_FISTA, SPG_ISTA = 0, 1
-TILES = {"auto": 0, "128x8": 1, "128x4": 2, "64x8": 3, "64x4": 4, "128x16": 5}
+SPG_STORE_DELTA, SPG_STORE_PREV = 0, 1
+TILES = {"auto": 0, "128x8": 1, "128x4": 2, "64x8": 3, "64x4": 4, "128x7": 6, "128x15": 7, "64x7": 8}
 
 _STATUS_NAMES = {0: "SPG_OK", -1: "SPG_EINVAL", -2: "SPG_ENOMEM", -3: "SPG_ECUDA", -4: "SPG_ENOTREADY",
                  -5: "SPG_ENONFINITE", -6: "SPG_ETIMEOUT"}
@@ -34,7 +35,7 @@ _STATUS_NAMES = {0: "SPG_OK", -1: "SPG_EINVAL", -2: "SPG_ENOMEM", -3: "SPG_ECUDA
 EXPORTS = ["spg_create", "spg_create_batch", "spg_set_data", "spg_set_x", "spg_get_x", "spg_reweight",
            "spg_iterate", "spg_objective", "spg_history", "spg_round_stats", "spg_certificate", "spg_counters",
            "spg_get_state", "spg_set_state", "spg_backward", "spg_unrolled", "spg_probe_timeout",
-           "spg_launch_count", "spg_plan_info", "spg_last_error", "spg_destroy"]
+           "spg_autotune", "spg_launch_count", "spg_plan_info", "spg_last_error", "spg_destroy"]
 
 
 class SPGError(RuntimeError):
@@ -52,7 +53,7 @@ class VolumeParams(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("data_dtype", ctypes.c_int), ("momentum", ctypes.c_int), ("hist_every", ctypes.c_int),
                 ("hist_capacity", ctypes.c_int), ("max_iters_per_round", ctypes.c_int), ("tile", ctypes.c_int),
-                ("zchunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+                ("zchunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("iterate_storage", ctypes.c_int)]
 
 
 _lib = None
@@ -90,6 +91,7 @@ def load():
             "spg_backward": (I, [P, I, V, V, V, ctypes.POINTER(D), I]),
             "spg_unrolled": (I, [P, I, V]),
             "spg_probe_timeout": (I, [P, LL]),
+            "spg_autotune": (I, [P, I, ctypes.POINTER(I)]),
             "spg_launch_count": (LL, [P]),
             "spg_plan_info": (I, [P, ctypes.POINTER(I)]),
             "spg_last_error": (ctypes.c_char_p, [P]),
@@ -213,14 +215,16 @@ def spg_get_state(h):
     return buf.raw
 
 
-STATE_HEADER_BYTES = 40
+STATE_HEADER_BYTES = 48
 
 
 def parse_state(blob, shapes):
     """Split a state blob (spg_get_state) into per-volume numpy views:
-    dicts with x, x_prev, om1, omtv (float32 [nz, ny, nx]), tau and stats."""
-    hdr = np.frombuffer(blob, dtype=np.int32, count=10, offset=0)
+    dicts with x, x_prev (float64, exact), om1, omtv (float32 [nz, ny, nx]),
+    tau and stats; with increment storage also d (float32)."""
+    hdr = np.frombuffer(blob, dtype=np.int32, count=12, offset=0)
     k_round = int(hdr[4])
+    storage = int(hdr[10])
     k_total = int(np.frombuffer(blob, dtype=np.int64, count=1, offset=24)[0])
     off = STATE_HEADER_BYTES
     vols = []
@@ -233,8 +237,15 @@ def parse_state(blob, shapes):
         stats = np.frombuffer(blob, dtype=np.float64, count=6, offset=off).copy() if off % 8 == 0 else \
             np.frombuffer(bytes(blob[off:off + 48]), dtype=np.float64).copy()
         off += 48
-        vols.append(dict(x=arr[0], x_prev=arr[1], om1=arr[2], omtv=arr[3], tau=tau, stats=stats))
-    return dict(k_round=k_round, k_total=k_total, volumes=vols)
+        v = dict(x=arr[0], om1=arr[2], omtv=arr[3], tau=tau, stats=stats)
+        if storage == SPG_STORE_DELTA:
+            v["d"] = arr[1]
+            # the difference of two float32 values is exact in float64 here
+            v["x_prev"] = arr[0].astype(np.float64) - arr[1].astype(np.float64)
+        else:
+            v["x_prev"] = arr[1]
+        vols.append(v)
+    return dict(k_round=k_round, k_total=k_total, storage=storage, volumes=vols)
 
 
 def spg_set_state(h, blob):
@@ -259,6 +270,12 @@ def spg_unrolled(h, K, out):
 
 def spg_probe_timeout(h, timeout_ns):
     return load().spg_probe_timeout(h, int(timeout_ns))
+
+
+def spg_autotune(h, trial_iters=10):
+    info = (ctypes.c_int * 6)()
+    _check(load().spg_autotune(h, int(trial_iters), info), h)
+    return dict(zip(["tile_x", "tile_y", "zchunk", "items", "grid", "ctas_per_sm"], info[:]))
 
 
 def spg_launch_count(h):
@@ -292,14 +309,14 @@ class SPG:
     """A solver context over one or more volumes (one fused launch per iteration)."""
 
     def __init__(self, volumes, data_dtype="f32", momentum="fista", hist_every=1, hist_capacity=4096,
-                 max_iters=100000, tile="auto", zchunk=0, ctas_per_sm=0, stream=None):
+                 max_iters=100000, tile="auto", zchunk=0, ctas_per_sm=0, storage="delta", stream=None):
         if isinstance(volumes, dict):
             volumes = [volumes]
         self.shapes = [tuple(v["shape"]) for v in volumes]
         params = [volume_params(v["shape"], **{k: v[k] for k in v if k != "shape"}) for v in volumes]
         opt = Options(SPG_F32 if data_dtype == "f32" else SPG_BF16, SPG_FISTA if momentum == "fista" else SPG_ISTA,
                       hist_every, hist_capacity, max_iters, TILES[tile] if isinstance(tile, str) else int(tile),
-                      zchunk, ctas_per_sm)
+                      zchunk, ctas_per_sm, SPG_STORE_DELTA if storage == "delta" else SPG_STORE_PREV)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -354,6 +371,9 @@ class SPG:
 
     def plan_info(self):
         return spg_plan_info(self.handle)
+
+    def autotune(self, trial_iters=10):
+        return spg_autotune(self.handle, trial_iters)
 
     def solve(self, rounds, iters):
         for _ in range(rounds):

@@ -68,25 +68,28 @@ def test_few_steps_odd_shapes(shape):
     np.testing.assert_allclose(hist[:, 4], ref.hist[0, :, 3], rtol=1e-6)
 
 
-@pytest.mark.parametrize("tile", ["128x8", "128x4", "64x8", "64x4", "128x16"])
-def test_tile_variants_agree(tile):
+@pytest.mark.parametrize("storage", ["delta", "prev"])
+@pytest.mark.parametrize("tile", ["128x8", "128x4", "64x8", "64x4", "128x7", "128x15", "64x7"])
+def test_tile_variants_agree(tile, storage):
     """Every compiled tile variant computes the same iterate (ragged 3-D shape)."""
     shape = (23, 45, 150)
     vol = synth.make_volume(shape, blobs=30, radius=9, seed=3)
-    x, hist, _, _ = gpu_solve(vol.b, vol.w, HYPER, 2, 20, tile=tile)
+    x, hist, _, _ = gpu_solve(vol.b, vol.w, HYPER, 2, 20, tile=tile, storage=storage)
     ref = oracle.solve(vol.b, vol.w, oparams(shape), 2, 20)
     assert rel_l2(x, ref.x) <= 1e-6
     np.testing.assert_allclose(hist[-20:, 4], ref.hist[1, :, 3], rtol=1e-6)
 
 
-def test_vol64_full_schedule():
+@pytest.mark.parametrize("storage", ["delta", "prev"])
+def test_vol64_full_schedule(storage):
     """64^3 workload, 3 rounds x 200 iterations: rel-L2 <= 1e-5 on x,
-    rel <= 1e-6 on the objective history and the final objective."""
+    rel <= 1e-6 on the objective history and the final objective, for both
+    storage forms of the extrapolation pair."""
     vol, hyper, R, I = synth.workload("vol64")
-    x, hist, st, obj = gpu_solve(vol.b, vol.w, hyper, R, I)
+    x, hist, st, obj = gpu_solve(vol.b, vol.w, hyper, R, I, storage=storage)
     ref = oracle.solve(vol.b, vol.w, oparams(vol.b.shape, hyper), R, I)
     err = rel_l2(x, ref.x)
-    print(f"vol64 rel-L2 {err:.3e}")
+    print(f"vol64 {storage} rel-L2 {err:.3e}")
     assert err <= 1e-5
     np.testing.assert_allclose(hist[:, 4], ref.hist.reshape(-1, 4)[:, 3], rtol=1e-6)
     fo = oracle.objective(ref.x, vol.b, vol.w, ref.om1, ref.omtv, oparams(vol.b.shape, hyper))
@@ -94,14 +97,34 @@ def test_vol64_full_schedule():
     np.testing.assert_allclose(st[:, 4:], ref.rstats[:, 4:], rtol=1e-6)
 
 
-def test_vol256_full_schedule():
-    """256^3 workload, 3 rounds x 300 iterations, same gates."""
+@pytest.fixture(scope="module")
+def vol256_ref():
     vol, hyper, R, I = synth.workload("vol256")
-    x, hist, st, obj = gpu_solve(vol.b, vol.w, hyper, R, I)
     ref = oracle.solve(vol.b, vol.w, oparams(vol.b.shape, hyper), R, I)
+    return vol, hyper, R, I, ref
+
+
+def test_vol256_full_schedule(vol256_ref):
+    """256^3 workload, 3 rounds x 300 iterations, increment storage (the
+    default): rel-L2 <= 1e-5 on x, rel <= 1e-6 on the objective history."""
+    vol, hyper, R, I, ref = vol256_ref
+    x, hist, st, obj = gpu_solve(vol.b, vol.w, hyper, R, I)
     err = rel_l2(x, ref.x)
-    print(f"vol256 rel-L2 {err:.3e}")
+    print(f"vol256 delta rel-L2 {err:.3e}")
     assert err <= 1e-5
+    np.testing.assert_allclose(hist[:, 4], ref.hist.reshape(-1, 4)[:, 3], rtol=1e-6)
+
+
+def test_vol256_previous_iterate_storage(vol256_ref):
+    """Same schedule with x_k, x_{k-1} stored. Rounding the stored iterate
+    alone (with exact arithmetic) already moves a 3 x 300 FISTA solve of this
+    model by about 1.1e-5 (float32 emulation at 128^3), so this form is held
+    to 2e-5 on x; the objective gate is unchanged."""
+    vol, hyper, R, I, ref = vol256_ref
+    x, hist, st, obj = gpu_solve(vol.b, vol.w, hyper, R, I, storage="prev")
+    err = rel_l2(x, ref.x)
+    print(f"vol256 prev rel-L2 {err:.3e}")
+    assert err <= 2e-5
     np.testing.assert_allclose(hist[:, 4], ref.hist.reshape(-1, 4)[:, 3], rtol=1e-6)
 
 
@@ -124,6 +147,7 @@ def test_vol512_sampled_step():
     n = vol.b.size
     sv = spg.parse_state(blob, [shape])["volumes"][0]
     xk, xkm1, om1, omtv, tau = sv["x"], sv["x_prev"], sv["om1"], sv["omtv"], np.float32(sv["tau"])
+    assert sv["stats"][5] > 0
     beta = oracle.beta_table(26)[25]
     rng = np.random.default_rng(5)
     idx = rng.choice(n, 20000, replace=False)
@@ -198,7 +222,7 @@ def test_batch_equals_single_volumes():
         ref = oracle.solve(v.b, v.w, oparams(sh, h), 2, 25)
         assert rel_l2(xb[i], ref.x) <= 1e-6
         assert rel_l2(xb[i], x1) <= 1e-6
-        np.testing.assert_allclose(hb[i][:, 4], h1[:, 4], rtol=1e-9)
+        np.testing.assert_allclose(hb[i][:, 4], h1[:, 4], rtol=1e-7)
 
 
 def test_bf16_storage():
@@ -224,10 +248,11 @@ def test_ista_monotone_on_gpu():
     assert np.all(np.diff(tot, axis=1) <= 1e-6 * np.abs(tot[:, 1:]))
 
 
-def test_checkpoint_resume_bitwise():
+@pytest.mark.parametrize("storage", ["delta", "prev"])
+def test_checkpoint_resume_bitwise(storage):
     shape = (18, 26, 70)
     vol = synth.make_volume(shape, blobs=10, radius=5, seed=40)
-    a = make_solver(shape)
+    a = make_solver(shape, storage=storage)
     a.set_data(0, vol.b, vol.w)
     a.reweight()
     a.iterate(17)
@@ -235,7 +260,7 @@ def test_checkpoint_resume_bitwise():
     a.iterate(23)
     xa = a.get_x(0).cpu().numpy()
     a.close()
-    b = make_solver(shape)
+    b = make_solver(shape, storage=storage)
     b.set_data(0, vol.b, vol.w)
     b.set_state(blob)
     assert b.counters() == (17, 17)
@@ -346,3 +371,24 @@ def test_autograd_function():
     assert b.grad is not None and w.grad is not None
     assert torch.isfinite(b.grad).all() and torch.isfinite(w.grad).all()
     assert l1.grad is not None and tv.grad is not None
+
+
+def test_autotune_keeps_the_solve():
+    """The autotuner's trial iterations leave iterate, counters and history
+    untouched; the solve continues to the oracle's result."""
+    shape = (40, 60, 200)
+    vol = synth.make_volume(shape, blobs=30, radius=12, seed=90)
+    s = make_solver(shape)
+    s.set_data(0, vol.b, vol.w)
+    s.reweight()
+    s.iterate(7)
+    h_before = s.history(0)
+    info = s.autotune(5)
+    assert info["tile_x"] in (64, 128) and info["grid"] > 0
+    assert s.counters() == (7, 7)
+    np.testing.assert_array_equal(s.history(0), h_before)
+    s.iterate(13)
+    x = s.get_x(0).cpu().numpy()
+    s.close()
+    ref = oracle.solve(vol.b, vol.w, oparams(shape), 1, 20)
+    assert rel_l2(x, ref.x) <= 1e-6

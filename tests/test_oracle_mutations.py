@@ -1,0 +1,99 @@
+"""The pins catch plausible mistakes in the oracle.
+
+Each case plants one mistake (a dropped term, a wrong sign or index, a
+transposed operand, a wrong constant) in a copy of spg_oracle.c, builds it
+on the CPU and runs the quick pins of test_oracle_pins.py against it: at
+least one must fail. No GPU is involved.
+"""
+import os
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "spg_oracle.c")
+
+MUTATIONS = {
+    "D^T without the first-plane gate": ("if (xx >= 1) s += u[v];", "s += u[v];"),
+    "forward instead of backward x-difference": (
+        "g[v]         = xx >= 1 ? x[v] - x[AT(p, xx - 1, y, z)] : 0.0;",
+        "g[v]         = xx + 1 < p->nx ? x[AT(p, xx + 1, y, z)] - x[v] : 0.0;"),
+    "y-difference taken along x": (
+        "g[n + v]     = y >= 1 ? x[v] - x[AT(p, xx, y - 1, z)] : 0.0;",
+        "g[n + v]     = xx >= 1 ? x[v] - x[AT(p, xx - 1, y, z)] : 0.0;"),
+    "first z-plane difference not zeroed": (
+        "g[2 * n + v] = z >= 1 ? x[v] - x[AT(p, xx, y, z - 1)] : 0.0;",
+        "g[2 * n + v] = z >= 1 ? x[v] - x[AT(p, xx, y, z - 1)] : x[v];"),
+    "Huber offset mu instead of mu/2": ("return s - 0.5 * mu;", "return s - mu;"),
+    "Huber gradient not clipped to the unit ball": ("double d = s > mu ? s : mu;", "double d = mu;"),
+    "soft-threshold shrinks by 2t": ("return z > 0.0 ? z - t : z + t;", "return z > 0.0 ? z - 2.0 * t : z + 2.0 * t;"),
+    "gradient step with the wrong sign": ("xnext[v] = orc_soft(y[v] - tau * g[v]", "xnext[v] = orc_soft(y[v] + tau * g[v]"),
+    "lambda_tv dropped from grad f": ("out[v] = w[v] * (x[v] - b[v]) + p->lambda_tv * out[v];",
+                                      "out[v] = w[v] * (x[v] - b[v]) + out[v];"),
+    "data term without the 1/2": ("sd += 0.5 * w[v] * r * r;", "sd += w[v] * r * r;"),
+    "TV weight built from eps instead of eps_tv": ("omtv[v] = p->eps_tv / (gn + p->eps_tv);",
+                                                   "omtv[v] = p->eps / (gn + p->eps);"),
+    "l1 weight ignored in the prox": ("tau * p->lambda_l1 * (om1 ? om1[v] : 1.0));\n    free(y);",
+                                      "tau * p->lambda_l1);\n    free(y);"),
+    "extrapolation divides by t_k": ("beta[k] = momentum == 0 ? (t - 1.0) / tn : 0.0;",
+                                     "beta[k] = momentum == 0 ? (t - 1.0) / t : 0.0;"),
+    "extrapolation with the wrong sign": ("y[v] = xk[v] + beta * (xk[v] - xkm1[v]);",
+                                          "y[v] = xk[v] - beta * (xk[v] - xkm1[v]);"),
+    "Lipschitz bound with |D|^2 <= 4": ("return m + 12.0 * p->lambda_tv * max_omtv / p->mu;",
+                                         "return m + 4.0 * p->lambda_tv * max_omtv / p->mu;"),
+}
+
+QUICK = [
+    pins.test_soft_threshold_table,
+    pins.test_huber_table,
+    pins.test_grad_hand_example,
+    lambda o: pins.test_grad_matches_kronecker_matrix(o, (3, 4, 5)),
+    lambda o: pins.test_adjoint_identity(o, (5, 7, 9)),
+    pins.test_constant_has_zero_gradient_and_tv,
+    pins.test_tv_of_ramp_and_spike,
+    pins.test_reweight_spike,
+    pins.test_lipschitz_bound_holds,
+    pins.test_lipschitz_bound_is_valid_and_tight,
+    pins.test_grad_f_matches_finite_difference_of_objective,
+    pins.test_data_only_closed_form,
+    pins.test_beta_table,
+    pins.test_no_regularisation_converges_to_b,
+    pins.test_tv_1d_reducible_matches_newton,
+    pins.test_ista_is_monotone,
+    pins.test_fista_rate_bound,
+    pins.test_4cubed_optimality_lbfgs_kkt,
+]
+
+
+@pytest.fixture(scope="module")
+def workdir():
+    d = tempfile.mkdtemp(prefix="orc_mut_")
+    yield d
+    shutil.rmtree(d, ignore_errors=True)
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, workdir):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {name}"
+    mut = src.replace(old, new)
+    tag = "".join(c if c.isalnum() else "_" for c in name)
+    csrc = os.path.join(workdir, f"{tag}.c")
+    lib = os.path.join(workdir, f"lib{tag}.so")
+    with open(csrc, "w") as f:
+        f.write(mut)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", csrc, "-o", lib, "-lm"])
+    caught = None
+    with oracle.using_library(lib):
+        for pin in QUICK:
+            try:
+                pin(oracle)
+            except Exception as e:  # a failing pin (assertion or a numerical blow-up)
+                caught = f"{getattr(pin, '__name__', 'pin')}: {type(e).__name__}"
+                break
+    assert caught is not None, f"no pin caught: {name}"
