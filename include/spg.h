@@ -216,6 +216,33 @@ long long spg_launch_count(const spg_ctx *ctx);
  * info = {vx*32, ty, zchunk, work items, grid size, ctas per SM}. */
 spg_status spg_plan_info(const spg_ctx *ctx, int info[6]);
 
+/* Allocation-free objective (no counterpart in the paper; it exists for
+ * callers that cannot allocate device memory themselves: code whose device
+ * memory is owned entirely by another allocator, such as a framework's caching
+ * pool or a fixed arena sized at start-up, and latency-critical paths that
+ * must not trigger the device-wide synchronisation cudaMalloc can cause).
+ *
+ * Computes out = {data, l1, tv, total} of F at x exactly as spg_objective
+ * does, from caller-provided device arrays x, b, w, om1, omtv (float32,
+ * contiguous [nz][ny][nx], no padding) and the volume's lambda_l1, lambda_tv
+ * and mu; out is a device pointer to 4 doubles; stream is a cudaStream_t or
+ * NULL. Asynchronous. It calls no cudaMalloc, cudaFree or allocating routine:
+ * its scratch (one partial sum per z-plane and a counter) is a static device
+ * array of SPG_NOALLOC_MAX_PLANES planes (about 128 KiB) inside this library,
+ * which every GPU that loads the library holds until the process exits.
+ * nz > SPG_NOALLOC_MAX_PLANES is rejected with SPG_EINVAL.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the array, which keeps the previous call's contents (the
+ * counter is cleared at the start of each call): calls that overlap on the
+ * GPU, from other streams or threads, race and must be serialised by the
+ * caller. Errors: SPG_EINVAL, SPG_ECUDA; message in spg_noalloc_last_error(). */
+#define SPG_NOALLOC_MAX_PLANES 4096
+spg_status spg_objective_noalloc(int nx, int ny, int nz, float lambda_l1, float lambda_tv, float mu,
+                                 const float *x, const float *b, const float *w, const float *om1,
+                                 const float *omtv, double *out, void *stream);
+const char *spg_noalloc_last_error(void);
+
 /* Message for the last failing call on ctx (or a global message if ctx is
  * NULL); never NULL. */
 const char *spg_last_error(const spg_ctx *ctx);

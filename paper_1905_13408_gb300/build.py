@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libspg.so")
-SOURCES = ["spg_step_f32.cu", "spg_step_bf16.cu", "spg_step.cu", "spg_aux.cu", "spg_api.cu"]
+SOURCES = ["spg_step_f32.cu", "spg_step_bf16.cu", "spg_step.cu", "spg_aux.cu", "spg_api.cu", "spg_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -35,7 +35,8 @@ _STATUS_NAMES = {0: "SPG_OK", -1: "SPG_EINVAL", -2: "SPG_ENOMEM", -3: "SPG_ECUDA
 EXPORTS = ["spg_create", "spg_create_batch", "spg_set_data", "spg_set_x", "spg_get_x", "spg_reweight",
            "spg_iterate", "spg_objective", "spg_history", "spg_round_stats", "spg_certificate", "spg_counters",
            "spg_get_state", "spg_set_state", "spg_backward", "spg_unrolled", "spg_probe_timeout",
-           "spg_autotune", "spg_launch_count", "spg_plan_info", "spg_last_error", "spg_destroy"]
+           "spg_autotune", "spg_launch_count", "spg_plan_info", "spg_last_error", "spg_destroy",
+           "spg_objective_noalloc", "spg_noalloc_last_error"]
 
 
 class SPGError(RuntimeError):
@@ -96,6 +97,9 @@ def load():
             "spg_plan_info": (I, [P, ctypes.POINTER(I)]),
             "spg_last_error": (ctypes.c_char_p, [P]),
             "spg_destroy": (None, [P]),
+            "spg_objective_noalloc": (I, [I, I, I, ctypes.c_float, ctypes.c_float, ctypes.c_float, V, V, V, V, V,
+                                          V, P]),
+            "spg_noalloc_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
