@@ -184,6 +184,22 @@ def cpu_baseline(vol, hyper, nz_slab=64, iters=30):
             "seconds": dt}
 
 
+def max_over_ranks(ms, world, device="cuda"):
+    """Max of a per-rank time over all ranks (identity for one rank)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, steps, world, ms_max):
+    """Units processed by all ranks per second, in units of 1e9."""
+    return world * units_per_rank * steps / (ms_max / 1e3) / 1e9
+
+
 def dist_setup(args):
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -322,17 +338,15 @@ def run_spg(args):
     ms = e0.elapsed_time(e1)
     launches = s.launch_count() - l0
     clk = clocks.stop()
+    ms = max_over_ranks(ms, world)
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     obj = s.objective(0)
     plan = s.plan_info()
     s.close()
 
     per_launch_s = ms / 1e3 / args.steps
-    value = world * nvox * args.steps / (ms / 1e3) / 1e9
+    value = whole_job_rate(nvox, args.steps, world, ms)
     peaks, peak_kind = measured_peaks()
     bpv = bytes_per_voxel(args.dtype, args.storage)
     achieved = bpv * nvox / per_launch_s / 1e9

@@ -83,6 +83,7 @@ def _bind(path):
         "orc_solve": (ctypes.c_int, [PP, _D, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D]),
         "orc_unrolled": (None, [PP, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D]),
         "orc_certificate": (ctypes.c_double, [PP, _D, _D, ctypes.c_double, _D, _D, _D]),
+        "orc_unrolled_active": (ctypes.c_longlong, [PP, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D]),
         "orc_step_sampled": (None, [PP, _D, _D, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D,
                                     ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _D]),
         "orc_backward": (ctypes.c_int, [PP, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D,
@@ -262,6 +263,16 @@ def unrolled(b, w, om1, omtv, tau, iters, x0, p: Params):
     _load().orc_unrolled(ctypes.byref(p.c()), _ptr(b), _ptr(w), _ptr(o1), _ptr(ot), float(tau),
                          int(iters), _ptr(x0), _ptr(out))
     return out
+
+
+def unrolled_active(b, w, om1, omtv, tau, iters, x0, p: Params):
+    """(x_K, number of voxel-steps where the soft-threshold passed)."""
+    b, w, x0 = _a(b, p.shape), _a(w, p.shape), _a(x0, p.shape)
+    o1, ot = _opt(om1, p.shape), _opt(omtv, p.shape)
+    out = np.empty(p.shape)
+    n = _load().orc_unrolled_active(ctypes.byref(p.c()), _ptr(b), _ptr(w), _ptr(o1), _ptr(ot), float(tau),
+                                    int(iters), _ptr(x0), _ptr(out))
+    return out, int(n)
 
 
 def certificate(y, xplus, tau, b, w, omtv, p: Params):

@@ -351,6 +351,42 @@ void orc_unrolled(const orc_params *p, const double *b, const double *w, const d
     free(beta);
 }
 
+/* As orc_unrolled, and counts the voxel-steps where the soft-threshold
+ * passes (|z| > t, or t = 0): two runs with equal counts crossed no kink of
+ * Eq. 21 in different places unless changes cancel exactly. */
+long long orc_unrolled_active(const orc_params *p, const double *b, const double *w, const double *om1,
+                              const double *omtv, double tau, int iters, const double *x0, double *xK)
+{
+    const size_t n = NVOX(p);
+    double *xc = (double *)malloc(n * sizeof(double));
+    double *xp = (double *)malloc(n * sizeof(double));
+    double *y = (double *)malloc(n * sizeof(double));
+    double *g = (double *)malloc(n * sizeof(double));
+    double *beta = (double *)malloc((size_t)(iters > 0 ? iters : 1) * sizeof(double));
+    orc_beta_table(p->momentum, iters, beta);
+    memcpy(xc, x0, n * sizeof(double));
+    memcpy(xp, x0, n * sizeof(double));
+    long long active = 0;
+    for (int k = 0; k < iters; k++) {
+        for (size_t v = 0; v < n; v++) y[v] = xc[v] + beta[k] * (xc[v] - xp[v]);
+        orc_grad_f(p, y, b, w, omtv, g);
+        for (size_t v = 0; v < n; v++) {
+            double z = y[v] - tau * g[v];
+            double t = tau * p->lambda_l1 * (om1 ? om1[v] : 1.0);
+            if (fabs(z) > t || t <= 0.0) active++;
+            xp[v] = xc[v];
+            xc[v] = orc_soft(z, t);
+        }
+    }
+    memcpy(xK, xc, n * sizeof(double));
+    free(xc);
+    free(xp);
+    free(y);
+    free(g);
+    free(beta);
+    return active;
+}
+
 /* ---------- strong-convexity certificate ---------- */
 
 /* |r|^2 with r = grad f(x+) - grad f(y) + (y - x+)/tau, an element of the

@@ -358,6 +358,35 @@ def test_adjoint_matches_oracle():
     np.testing.assert_allclose(gs, rs, rtol=1e-4)
 
 
+def test_adjoint_differentiation_workload():
+    """128^3 volume, 50 unrolled iterations, checkpoints every 10: GPU
+    gradients w.r.t. b, w, lambda_l1, lambda_tv against the FP64 oracle's
+    adjoint (rel-L2 <= 1e-4)."""
+    vol, hyper, _, K = synth.workload("vol128_adjoint")
+    shape = vol.b.shape
+    b = torch.from_numpy(vol.b).cuda()
+    w = torch.from_numpy(vol.w).cuda()
+    s = make_solver(shape, hyper)
+    s.set_data(0, b, w)
+    s.reweight()
+    tau = s.round_stats(0)[5]
+    xK = torch.empty_like(b)
+    spg.spg_unrolled(s.handle, K, xK)
+    gx = 2 * (xK - torch.from_numpy(vol.phantom).cuda())
+    gb, gw = torch.empty_like(b), torch.empty_like(b)
+    gs = spg.spg_backward(s.handle, K, gx.contiguous(), gb, gw, ckpt_every=10)
+    s.close()
+    p = oparams(shape, hyper)
+    x0 = np.zeros(shape)
+    ref_xK = oracle.unrolled(vol.b, vol.w, None, None, tau, K, x0, p)
+    assert rel_l2(xK.cpu().numpy(), ref_xK) <= 1e-5
+    rb, rw, rs = oracle.backward(vol.b, vol.w, None, None, tau, K, x0, 2 * (ref_xK - vol.phantom), p)
+    eb, ew = rel_l2(gb.cpu().numpy(), rb), rel_l2(gw.cpu().numpy(), rw)
+    print(f"adjoint 128^3 x 50: rel-L2 gb {eb:.2e}, gw {ew:.2e}, scalars {gs} vs {rs}")
+    assert eb <= 1e-4 and ew <= 1e-4
+    np.testing.assert_allclose(gs, rs, rtol=1e-4)
+
+
 def test_autograd_function():
     shape = (10, 12, 16)
     vol = synth.make_volume(shape, blobs=5, radius=3, seed=80)

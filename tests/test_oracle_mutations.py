@@ -43,6 +43,9 @@ MUTATIONS = {
                                      "beta[k] = momentum == 0 ? (t - 1.0) / t : 0.0;"),
     "extrapolation with the wrong sign": ("y[v] = xk[v] + beta * (xk[v] - xkm1[v]);",
                                           "y[v] = xk[v] - beta * (xk[v] - xkm1[v]);"),
+    "adjoint drops the (1 + beta) factor": ("a_cur[v] += (1.0 + beta[k]) * ybar;", "a_cur[v] += ybar;"),
+    "adjoint Hessian projection with the wrong sign": ("h0 = (q0 - e0 * eq) / s;", "h0 = (q0 + e0 * eq) / s;"),
+    "adjoint of w uses b - y": ("gw[v] += -tau * (y[v] - b[v]) * m[v];", "gw[v] += tau * (y[v] - b[v]) * m[v];"),
     "Lipschitz bound with |D|^2 <= 4": ("return m + 12.0 * p->lambda_tv * max_omtv / p->mu;",
                                          "return m + 4.0 * p->lambda_tv * max_omtv / p->mu;"),
 }
@@ -66,6 +69,8 @@ QUICK = [
     pins.test_ista_is_monotone,
     pins.test_fista_rate_bound,
     pins.test_4cubed_optimality_lbfgs_kkt,
+    pins.test_adjoint_identity_of_one_linear_step,
+    pins.test_adjoint_matches_central_differences,
 ]
 
 

@@ -405,3 +405,80 @@ def test_beta_table(orc):
     assert np.all(np.diff(bt) > 0) and bt[-1] < 1
     assert bt[1999] == pytest.approx(1998 / 2001, rel=2e-3)
     assert np.all(orc.beta_table(10, "ista") == 0)
+
+
+# ---------- differentiation (adjoint of K unrolled steps) ----------
+
+def _adjoint_case(orc, shape=(8, 9, 10), K=10, seed=31):
+    vol = synth.make_volume(shape, blobs=5, radius=2.5, seed=seed)
+    b, w = vol.b.astype(np.float64), vol.w.astype(np.float64)
+    p = P(orc, shape, mu=0.02, lambda_tv=0.1, lambda_l1=0.05)
+    tau = 1.0 / orc.lipschitz(w, 1.0, p)
+    x0 = np.zeros(shape)
+    return vol, b, w, p, tau, x0, K
+
+
+def test_adjoint_matches_central_differences(orc):
+    """The FP64 adjoint of K unrolled steps (tau and weights fixed) agrees with
+    central differences (step 1e-4) of L = |x_K - phantom|^2 in 64 random
+    single-voxel directions of b and w and in both scalars; directions whose
+    perturbed runs cross a soft-threshold kink in a different place are left
+    out, as the map is not differentiable across them."""
+    vol, b, w, p, tau, x0, K = _adjoint_case(orc)
+    ph = vol.phantom.astype(np.float64)
+
+    def loss(bb, ww, pp):
+        xk, act = orc.unrolled_active(bb, ww, None, None, tau, K, x0, pp)
+        return float(((xk - ph) ** 2).sum()), act
+
+    L0, act0 = loss(b, w, p)
+    xK = orc.unrolled(b, w, None, None, tau, K, x0, p)
+    gb, gw, gs = orc.backward(b, w, None, None, tau, K, x0, 2 * (xK - ph), p)
+    rng = np.random.default_rng(32)
+    h = 1e-4
+    checked = 0
+    for which, grad, base in (("b", gb, b), ("w", gw, w)):
+        for v in rng.choice(b.size, 32, replace=False):
+            e = np.zeros(b.size)
+            e[v] = h
+            e = e.reshape(b.shape)
+            if which == "b":
+                (lp, ap), (lm, am) = loss(b + e, w, p), loss(b - e, w, p)
+            else:
+                (lp, ap), (lm, am) = loss(b, w + e, p), loss(b, w - e, p)
+            if ap != act0 or am != act0:
+                continue
+            fd = (lp - lm) / (2 * h)
+            assert grad.ravel()[v] == pytest.approx(fd, rel=1e-6, abs=1e-9), (which, v)
+            checked += 1
+    assert checked >= 48
+    # a scalar moves every threshold at once, so a step of 1e-4 may cross a
+    # kink somewhere; the step is shrunk until the active set is unchanged
+    for i, name in enumerate(("lambda_l1", "lambda_tv")):
+        done = False
+        for hs in (1e-4, 1e-5, 1e-6, 1e-7):
+            hp = P(orc, b.shape, mu=p.mu, lambda_tv=p.lambda_tv, lambda_l1=p.lambda_l1)
+            hm = P(orc, b.shape, mu=p.mu, lambda_tv=p.lambda_tv, lambda_l1=p.lambda_l1)
+            setattr(hp, name, getattr(p, name) + hs)
+            setattr(hm, name, getattr(p, name) - hs)
+            (lp, ap), (lm, am) = loss(b, w, hp), loss(b, w, hm)
+            if ap == act0 and am == act0:
+                assert gs[i] == pytest.approx((lp - lm) / (2 * hs), rel=1e-6), name
+                done = True
+                break
+        assert done, name
+
+
+def test_adjoint_identity_of_one_linear_step(orc):
+    """With lambda_l1 = 0 and every |Dy| below mu one step is linear in
+    (x_k, x_{k-1}, b): the adjoint's b-gradient equals tau w g for a loss
+    <g, x_1> (transposed-operand check)."""
+    shape = (5, 6, 7)
+    rng = np.random.default_rng(33)
+    b = 1e-5 * rng.standard_normal(shape)
+    w = rng.uniform(0.5, 2, shape)
+    p = P(orc, shape, mu=1.0, lambda_tv=0.3, lambda_l1=0.0)
+    tau = 1.0 / orc.lipschitz(w, 1.0, p)
+    g = rng.standard_normal(shape)
+    gb, gw, gs = orc.backward(b, w, None, None, tau, 1, np.zeros(shape), g, p)
+    np.testing.assert_allclose(gb, tau * w * g, rtol=1e-12, atol=1e-15)
