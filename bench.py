@@ -253,43 +253,54 @@ def run_reference(args):
 
 def time_to_gap(vol, hyper, args, stream):
     """Round-1 subproblem from x_0 = 0: iterations and wall time (CUDA events)
-    until F(x_k) <= F* (1 + 1e-3), F* the best objective of a run with about
-    10x as many iterations (same code, FP64 reductions)."""
+    until F(x_k) <= F* (1 + 1e-3). F* is the best objective of 1500-iteration
+    reference runs (about 10x the iterations needed) of the fixed FISTA
+    schedule and of the gradient-restart variant (same code, FP64
+    reductions). Both variants are timed to that F*."""
     import numpy as np
     import torch
 
     from paper_1905_13408_gb300 import spg
     n_ref = 1500
-    s = spg.SPG(dict(shape=vol.b.shape, **hyper), data_dtype=args.dtype, hist_capacity=n_ref + 16,
-                tile=args.tile, zchunk=args.zchunk, stream=stream.cuda_stream, storage=args.storage)
-    s.set_data(0, *dev_inputs(vol, args.dtype))
-    s.reweight()
-    s.iterate(n_ref)
-    h = s.history(0)
-    fstar = float(h[:, 4].min())
-    rel = (h[:, 4] - fstar) / abs(fstar)
-    hit = np.nonzero(rel <= 1e-3)[0]
-    k_gap = int(h[hit[0], 0]) if len(hit) else None
-    result = {"F_star": fstar, "F_star_iterations": n_ref, "iterations_to_gap": k_gap}
-    if k_gap is not None:
-        # timed re-run: reweight + k_gap fused iterations from x_0 = 0 (history checked every 10)
-        zero = torch.zeros(vol.b.shape, dtype=torch.float32, device="cuda")
-        s.set_x(0, zero)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+    hists, solvers = {}, {}
+    for restart in (False, True):
+        s = spg.SPG(dict(shape=vol.b.shape, **hyper), data_dtype=args.dtype, hist_capacity=n_ref + 16,
+                    tile=args.tile, zchunk=args.zchunk, stream=stream.cuda_stream, storage=args.storage,
+                    restart=restart)
+        s.set_data(0, *dev_inputs(vol, args.dtype))
         s.reweight()
-        done = 0
-        while done < k_gap:
-            c = min(10, k_gap - done)
-            s.iterate(c)
-            done += c
-        e1.record(stream)
-        torch.cuda.synchronize()
-        result["time_to_gap_ms"] = e0.elapsed_time(e1)
-        result["note"] = "round-1 subproblem (x_0 = 0, weights 1); paper's 512^3 figure: 'medium accurate' in 10 s, hardware unnamed"
-    s.close()
-    return result
+        s.iterate(n_ref)
+        hists[restart] = s.history(0)
+        solvers[restart] = s
+    fstar = min(float(h[:, 4].min()) for h in hists.values())
+    out = {"F_star": fstar, "F_star_iterations": n_ref, "gap": 1e-3,
+           "note": "round-1 subproblem (x_0 = 0, weights 1); the paper's only figure: 'medium accurate' "
+                   "at 512^3 within 10 s on unnamed hardware"}
+    zero = torch.zeros(vol.b.shape, dtype=torch.float32, device="cuda")
+    for restart, h in hists.items():
+        s = solvers[restart]
+        rel = (h[:, 4] - fstar) / abs(fstar)
+        hit = np.nonzero(rel <= 1e-3)[0]
+        k_gap = int(h[hit[0], 0] - h[0, 0]) if len(hit) else None
+        res = {"iterations_to_gap": k_gap}
+        if k_gap is not None:
+            # timed re-run from x_0 = 0: re-weight + k_gap fused iterations (history read every 10)
+            s.set_x(0, zero)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.reweight()
+            done = 0
+            while done < k_gap:
+                c = min(10, k_gap - done)
+                s.iterate(c)
+                done += c
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res["time_to_gap_ms"] = e0.elapsed_time(e1)
+        out["gradient_restart" if restart else "fixed_schedule"] = res
+        s.close()
+    return out
 
 
 def dev_inputs(vol, dtype):

@@ -100,6 +100,9 @@ typedef struct {
     int zchunk;               /* 0 = built-in choice, else planes per work item */
     int ctas_per_sm;          /* 0 = occupancy limit, else a cap */
     spg_iterate_storage iterate_storage;  /* SPG_STORE_DELTA (default) or SPG_STORE_PREV */
+    int restart;              /* 0: fixed FISTA schedule (default); 1: gradient restart of the
+                                 extrapolation (per volume, whenever <y_k - x_{k+1}, x_{k+1} - x_k> > 0,
+                                 O'Donoghue and Candes 2015); decided on the device every iteration */
 } spg_options;
 
 /* Tile codes for spg_options.tile: x extent = 32 * vx, y extent = ty. */
@@ -126,6 +129,26 @@ spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg
  * finite and > 0, b finite: checked on the device, SPG_EINVAL / SPG_ENONFINITE
  * otherwise. Synchronises (it reduces max w in double precision). */
 spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg_dtype src_dtype);
+
+/* Proximal anchor of the implicit-gradient term (Sec. 2.1 Eq. 22, Eq. 31):
+ * adds gamma |x - x_anchor|^2 to the data term of volume `vol`. Because
+ *   1/2 w (x - b)^2 + gamma (x - a)^2 = 1/2 w' (x - b')^2 + const,
+ *   w' = w + 2 gamma,  b' = (w b + 2 gamma a) / w',
+ * the term folds exactly into (b, w): the call replaces the stored b and w of
+ * the volume by b' and w' (computed in float32 on the device, rounded to the
+ * storage dtype). x_anchor is a float32 volume (host or device), typically
+ * the previous maximisation step's solution; gamma >= 0. Objective values
+ * reported afterwards omit the constant. Call after spg_set_data and before
+ * spg_reweight. Synchronises. */
+spg_status spg_set_anchor(spg_ctx *ctx, int vol, float gamma, const float *x_anchor);
+
+/* Parameter scales of Sec. 2.5 for volume `vol`, from the stored b and w:
+ * out = {RMS(w b), mean(w), max(w), min(w)}. In the real-space reading of
+ * the data term, w b is the kernel-regression numerator (the inverse
+ * transform of D y in Eq. 31, up to normalisation), so the paper's rules
+ * read lambda_l1 = c1 RMS(w b) eps, lambda_tv = c2 RMS(w b) eps_tv and
+ * gamma = c3 mean(w). Synchronises. */
+spg_status spg_param_scales(spg_ctx *ctx, int vol, double out[4]);
 
 /* Set / read the current iterate of volume `vol` (float32, nx*ny*nz).
  * The initial iterate is 0. spg_set_x also restarts the momentum
@@ -242,6 +265,19 @@ spg_status spg_objective_noalloc(int nx, int ny, int nz, float lambda_l1, float 
                                  const float *x, const float *b, const float *w, const float *om1,
                                  const float *omtv, double *out, void *stream);
 const char *spg_noalloc_last_error(void);
+
+/* Gold-standard Fourier shell correlation (Sec. 2.3, Eq. 30) of two real
+ * n x n x n maps a and b (float32, host or device, C order):
+ *   fsc[k] = sum_{|k'|=k} Re F(k') G*(k') / sqrt(sum |F|^2 sum |G|^2),
+ * shells k = 0 .. n/2, the shell of frequency index (h, k, l) being the
+ * nearest integer to sqrt(h^2 + k^2 + l^2). counts (optional) receives the
+ * number of coefficients per shell. fsc and counts are host arrays of at least
+ * n/2 + 1 entries (max_shells). Uses cuFFT and allocates its own temporaries;
+ * synchronises `stream`. Errors: SPG_EINVAL, SPG_ENOMEM, SPG_ECUDA with a
+ * message in spg_fsc_last_error(). */
+spg_status spg_fsc(int n, const float *a, const float *b, int max_shells, double *fsc, double *counts,
+                   void *stream);
+const char *spg_fsc_last_error(void);
 
 /* Message for the last failing call on ctx (or a global message if ctx is
  * NULL); never NULL. */

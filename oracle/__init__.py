@@ -42,7 +42,8 @@ class _P(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("lambda_l1", ctypes.c_double), ("lambda_tv", ctypes.c_double),
                 ("mu", ctypes.c_double), ("eps", ctypes.c_double), ("eps_tv", ctypes.c_double),
-                ("momentum", ctypes.c_int)]
+                ("momentum", ctypes.c_int), ("restart", ctypes.c_int), ("gamma", ctypes.c_double),
+                ("anchor", ctypes.c_void_p)]
 
 
 @dataclass
@@ -54,11 +55,20 @@ class Params:
     eps: float = 1e-3
     eps_tv: float = 1e-3
     momentum: str = "fista"  # "fista" or "ista"
+    restart: bool = False    # gradient restart of the extrapolation
+    gamma: float = 0.0       # implicit-gradient term gamma |x - anchor|^2 (Eq. 22)
+    anchor: np.ndarray = None
 
     def c(self):
         nz, ny, nx = self.shape
+        if self.gamma > 0:
+            self._anchor = np.ascontiguousarray(self.anchor, dtype=np.float64)
+            assert self._anchor.shape == tuple(self.shape)
+            ptr = self._anchor.ctypes.data
+        else:
+            ptr = None
         return _P(nx, ny, nz, self.lambda_l1, self.lambda_tv, self.mu, self.eps, self.eps_tv,
-                  0 if self.momentum == "fista" else 1)
+                  0 if self.momentum == "fista" else 1, 1 if self.restart else 0, self.gamma, ptr)
 
 
 _D = ctypes.POINTER(ctypes.c_double)

@@ -47,6 +47,9 @@ typedef struct {
     int nx, ny, nz;
     double lambda_l1, lambda_tv, mu, eps, eps_tv;
     int momentum; /* 0: FISTA extrapolation, 1: plain proximal gradient (beta = 0) */
+    int restart;  /* 1: restart the extrapolation whenever <y_k - x_{k+1}, x_{k+1} - x_k> > 0 */
+    double gamma;          /* weight of the implicit-gradient term gamma |x - anchor|^2 (Eq. 22) */
+    const double *anchor;  /* the previous maximisation step's solution; used when gamma > 0 */
 } orc_params;
 
 #define NVOX(p) ((size_t)(p)->nx * (size_t)(p)->ny * (size_t)(p)->nz)
@@ -138,20 +141,24 @@ void orc_tv_grad(const orc_params *p, const double *x, const double *omtv, doubl
     free(g);
 }
 
-/* Gradient of the smooth part f = data + TV: w (x - b) + lambda_tv D^T(...). */
+/* Gradient of the smooth part f = data + TV (+ the Eq. 22 term):
+ * w (x - b) + lambda_tv D^T(...) + 2 gamma (x - anchor). */
 void orc_grad_f(const orc_params *p, const double *x, const double *b, const double *w,
                 const double *omtv, double *out)
 {
     const size_t n = NVOX(p);
     orc_tv_grad(p, x, omtv, out);
 #pragma omp parallel for schedule(static)
-    for (long long v = 0; v < (long long)n; v++)
+    for (long long v = 0; v < (long long)n; v++) {
         out[v] = w[v] * (x[v] - b[v]) + p->lambda_tv * out[v];
+        if (p->gamma > 0.0) out[v] += 2.0 * p->gamma * (x[v] - p->anchor[v]);
+    }
 }
 
 /* ---------- objective, weights, step size ---------- */
 
-/* out = {data, l1, tv, total} of F at x (Eq. 31 form, Eq. 14 smoothed TV). */
+/* out = {data, l1, tv, total} of F at x (Eq. 31 form, Eq. 14 smoothed TV);
+ * with gamma > 0 the data part includes gamma |x - anchor|^2 (Eq. 22). */
 void orc_objective(const orc_params *p, const double *x, const double *b, const double *w,
                    const double *om1, const double *omtv, double out[4])
 {
@@ -169,6 +176,7 @@ void orc_objective(const orc_params *p, const double *x, const double *b, const 
                 size_t v = AT(p, xx, y, z);
                 double r = x[v] - b[v];
                 sd += 0.5 * w[v] * r * r;
+                if (p->gamma > 0.0) sd += p->gamma * (x[v] - p->anchor[v]) * (x[v] - p->anchor[v]);
                 sl += (om1 ? om1[v] : 1.0) * fabs(x[v]);
                 st += (omtv ? omtv[v] : 1.0) * orc_huber(g[v], g[n + v], g[2 * n + v], p->mu);
             }
@@ -239,14 +247,14 @@ void orc_reweight(const orc_params *p, const double *x, double *om1, double *omt
     free(p2);
 }
 
-/* Lipschitz bound of grad f: max w + |D|^2 lambda_tv max(omtv) / mu, |D|^2 <= 12. */
+/* Lipschitz bound of grad f: max w + |D|^2 lambda_tv max(omtv) / mu (+ 2 gamma), |D|^2 <= 12. */
 double orc_lipschitz(const orc_params *p, const double *w, double max_omtv)
 {
     const size_t n = NVOX(p);
     double m = 0.0;
     for (size_t v = 0; v < n; v++)
         if (w[v] > m) m = w[v];
-    return m + 12.0 * p->lambda_tv * max_omtv / p->mu;
+    return m + 12.0 * p->lambda_tv * max_omtv / p->mu + 2.0 * (p->gamma > 0.0 ? p->gamma : 0.0);
 }
 
 /* FISTA extrapolation weights: t_0 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2,
@@ -280,9 +288,33 @@ void orc_step(const orc_params *p, const double *xk, const double *xkm1, double 
     free(g);
 }
 
+/* <y - x_next, x_next - x> with y = x + beta (x - xprev), summed per z-plane
+ * and then over planes in order (the gradient restart test of O'Donoghue and
+ * Candes, 2015: restart when the step moves against the extrapolation). */
+static double restart_dot(const orc_params *p, const double *x, const double *xprev, const double *xnext,
+                          double beta)
+{
+    double *pz = (double *)calloc((size_t)p->nz, sizeof(double));
+    const size_t plane = (size_t)p->nx * p->ny;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < p->nz; z++) {
+        double s = 0.0;
+        for (size_t v = (size_t)z * plane; v < (size_t)(z + 1) * plane; v++) {
+            double y = x[v] + beta * (x[v] - xprev[v]);
+            s += (y - xnext[v]) * (xnext[v] - x[v]);
+        }
+        pz[z] = s;
+    }
+    double s = 0.0;
+    for (int z = 0; z < p->nz; z++) s += pz[z];
+    free(pz);
+    return s;
+}
+
 /* Reweighted solve: `rounds` rounds of `iters` steps from the given x (in/out).
  * Round r re-weights from the current x, sets tau = 1/L and restarts the
- * momentum (x_{-1} = x_0, t = 1).
+ * momentum (x_{-1} = x_0, t = 1). With p->restart the extrapolation index
+ * also returns to 0 after any step whose restart_dot is positive.
  * hist (optional): rounds*iters*4 doubles, F(x_k) before step k of round r.
  * rstats (optional): rounds*6 doubles = {max omtv, nnz, sum om1, sum omtv, L, tau}.
  * om1_out/omtv_out (optional): the weights of the last round. */
@@ -308,9 +340,14 @@ int orc_solve(const orc_params *p, const double *b, const double *w, int rounds,
             rstats[r * 6 + 5] = tau;
         }
         memcpy(xprev, x, n * sizeof(double));
+        int km = 0; /* index into the extrapolation table */
         for (int k = 0; k < iters; k++) {
             if (hist) orc_objective(p, x, b, w, om1, omtv, hist + ((size_t)r * iters + k) * 4);
-            orc_step(p, x, xprev, beta[k], tau, b, w, om1, omtv, xnext);
+            orc_step(p, x, xprev, beta[km], tau, b, w, om1, omtv, xnext);
+            if (p->restart && restart_dot(p, x, xprev, xnext, beta[km]) > 0.0)
+                km = 0;
+            else
+                km++;
             memcpy(xprev, x, n * sizeof(double));
             memcpy(x, xnext, n * sizeof(double));
         }

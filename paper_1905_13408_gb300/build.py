@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libspg.so")
-SOURCES = ["spg_step_f32.cu", "spg_step_bf16.cu", "spg_step.cu", "spg_aux.cu", "spg_api.cu", "spg_noalloc.cu"]
+SOURCES = ["spg_step_f32.cu", "spg_step_bf16.cu", "spg_step.cu", "spg_aux.cu", "spg_api.cu", "spg_noalloc.cu",
+           "spg_fsc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -68,7 +69,7 @@ def build(force=False, verbose=False):
         for _, log in results:
             sys.stderr.write(log)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH + ["-Xcompiler", "-fPIC"]
+    cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH + ["-Xcompiler", "-fPIC", "-ldl"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")

@@ -264,18 +264,22 @@ spg_status build_plan(spg_ctx *ctx, const StepVariant &v, int zchunk_opt)
     ctx->items_d = nullptr;
     ctx->partials_d = nullptr;
     CK(dalloc(&ctx->items_d, items.size() * sizeof(WorkItem)), "alloc items");
-    CK(dalloc(&ctx->partials_d, items.size() * 3 * sizeof(double)), "alloc partials");
+    CK(dalloc(&ctx->partials_d, items.size() * 4 * sizeof(double)), "alloc partials");
     CK(cudaMemcpyAsync(ctx->items_d, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
                        ctx->stream),
        "upload items");
     CK(cudaMemcpyAsync(ctx->tmaps_d, maps.data(), maps.size() * sizeof(TmapSet), cudaMemcpyHostToDevice, ctx->stream),
        "upload tensor maps");
-    // item ranges changed: refresh descriptors (tau is device-owned, keep it)
+    // item ranges changed: refresh descriptors (tau and the extrapolation index are device-owned)
     std::vector<VolDesc> dev(ctx->nvol);
     CK(cudaMemcpyAsync(dev.data(), ctx->vols_d, ctx->nvol * sizeof(VolDesc), cudaMemcpyDeviceToHost, ctx->stream),
        "read descriptors");
     CK(cudaStreamSynchronize(ctx->stream), "sync");
-    for (int j = 0; j < ctx->nvol; j++) ctx->vols_h[j].tau = dev[j].tau;
+    for (int j = 0; j < ctx->nvol; j++) {
+        ctx->vols_h[j].tau = dev[j].tau;
+        ctx->vols_h[j].kmom = dev[j].kmom;
+        ctx->vols_h[j].beta_last = dev[j].beta_last;
+    }
     CK(cudaMemcpyAsync(ctx->vols_d, ctx->vols_h.data(), ctx->nvol * sizeof(VolDesc), cudaMemcpyHostToDevice,
                        ctx->stream),
        "upload descriptors");
@@ -309,6 +313,7 @@ StepParams step_params(const spg_ctx *c)
     p.nvol = c->nvol;
     p.hist_cap = c->hist_cap;
     p.hist_every = c->hist_every;
+    p.restart = c->opt.restart ? 1 : 0;
     p.timeout_ns = kTimeoutNs;
     return p;
 }
@@ -541,7 +546,7 @@ spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg
     if ((e = dalloc(&ctx->st_d, sizeof(DevState))) != cudaSuccess) return bail(e, "alloc state");
     if ((e = dalloc(&ctx->hist_d, (size_t)ctx->hist_cap * nvol * 5 * sizeof(double))) != cudaSuccess)
         return bail(e, "alloc history");
-    if ((e = dalloc(&ctx->plane_part_d, (size_t)plane * 4 * sizeof(double))) != cudaSuccess)
+    if ((e = dalloc(&ctx->plane_part_d, (size_t)plane * AUX_SEG * 4 * sizeof(double))) != cudaSuccess)
         return bail(e, "alloc partials");
     if ((e = dalloc(&ctx->vol_out_d, (size_t)nvol * 8 * sizeof(double))) != cudaSuccess) return bail(e, "alloc");
     if ((e = dalloc(&ctx->maxw_d, (size_t)nvol * sizeof(double))) != cudaSuccess) return bail(e, "alloc");
@@ -637,6 +642,41 @@ spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg
     return SPG_OK;
 }
 
+spg_status spg_set_anchor(spg_ctx *ctx, int vol, float gamma, const float *x_anchor)
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || !x_anchor || !(gamma >= 0.f) || !std::isfinite(gamma))
+        return fail(ctx, SPG_EINVAL, "spg_set_anchor: bad arguments");
+    if (!ctx->data_set[vol]) return fail(ctx, SPG_ENOTREADY, "spg_set_anchor: call spg_set_data first");
+    const VolDesc &d = ctx->vols_h[vol];
+    // stage the anchor in the l1-weight buffer (re-set by the next spg_reweight)
+    spg_status s = copy_volume_in(ctx, ctx->OM1, 4, d, x_anchor);
+    if (s != SPG_OK) return s;
+    CK(launch_anchor(aux_params(ctx), vol, d.nz, ctx->B, ctx->W, ctx->bf16(), ctx->OM1, gamma, ctx->maxw_d,
+                     ctx->stream),
+       "anchor");
+    ctx->launches += 1;
+    ctx->reweighted = false;
+    return device_status(ctx);
+}
+
+spg_status spg_param_scales(spg_ctx *ctx, int vol, double out[4])
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_param_scales: bad arguments");
+    if (!ctx->data_set[vol]) return fail(ctx, SPG_ENOTREADY, "spg_param_scales: call spg_set_data first");
+    const VolDesc &d = ctx->vols_h[vol];
+    CK(launch_scales(aux_params(ctx), vol, d.nz, ctx->B, ctx->W, ctx->bf16(), ctx->stream), "scales");
+    ctx->launches += 1;
+    double o[8];
+    CK(cudaMemcpyAsync(o, ctx->vol_out_d + (size_t)vol * 8, sizeof(o), cudaMemcpyDeviceToHost, ctx->stream),
+       "read scales");
+    spg_status s = device_status(ctx);
+    if (s != SPG_OK) return s;
+    for (int q = 0; q < 4; q++) out[q] = o[q];
+    return SPG_OK;
+}
+
 spg_status spg_set_x(spg_ctx *ctx, int vol, const float *x)
 {
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
@@ -645,6 +685,13 @@ spg_status spg_set_x(spg_ctx *ctx, int vol, const float *x)
     const int c = ctx->cur();
     spg_status s;
     if ((s = copy_volume_in(ctx, ctx->X[c], 4, d, x)) != SPG_OK) return s;
+    {
+        // the extrapolation restarts from this iterate
+        const int zero = 0;
+        CK(cudaMemcpyAsync(&ctx->vols_d[vol].kmom, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream),
+           "reset extrapolation");
+        CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    }
     if (ctx->xd()) {
         CK(cudaMemsetAsync(ctx->X[ctx->aux_of(c)] + d.off, 0, (size_t)d.pitch * d.ny * d.nz * 4, ctx->stream),
            "reset increment");
@@ -778,14 +825,16 @@ spg_status spg_get_state(spg_ctx *ctx, void *blob, size_t *size)
 {
     if (!ctx || !size) return fail(ctx, SPG_EINVAL, "spg_get_state: bad arguments");
     size_t need = sizeof(StateHeader);
-    for (const auto &d : ctx->vols_h) need += 4 * (size_t)d.nx * d.ny * d.nz * 4 + sizeof(float) + 6 * sizeof(double);
+    for (const auto &d : ctx->vols_h)
+        need += 4 * (size_t)d.nx * d.ny * d.nz * 4 + 2 * sizeof(float) + sizeof(int32_t) + sizeof(int32_t) +
+                6 * sizeof(double);
     if (!blob) {
         *size = need;
         return SPG_OK;
     }
     if (*size < need) return fail(ctx, SPG_EINVAL, "spg_get_state: buffer too small");
     char *p = static_cast<char *>(blob);
-    StateHeader h{kStateMagic, 2, ctx->nvol, ctx->k_round, ctx->reweighted ? 1 : 0, ctx->k_total,
+    StateHeader h{kStateMagic, 3, ctx->nvol, ctx->k_round, ctx->reweighted ? 1 : 0, ctx->k_total,
                   (int32_t)ctx->opt.data_dtype, (int32_t)ctx->opt.momentum, (int32_t)ctx->opt.iterate_storage, 0};
     std::memcpy(p, &h, sizeof(h));
     p += sizeof(h);
@@ -808,6 +857,11 @@ spg_status spg_get_state(spg_ctx *ctx, void *blob, size_t *size)
         CK(cudaStreamSynchronize(ctx->stream), "synchronise");
         std::memcpy(p, &dev[j].tau, sizeof(float));
         p += sizeof(float);
+        std::memcpy(p, &dev[j].beta_last, sizeof(float));
+        p += sizeof(float);
+        const int32_t km[2] = {dev[j].kmom, 0};
+        std::memcpy(p, km, sizeof(km));
+        p += sizeof(km);
         CK(cudaMemcpyAsync(p, ctx->rstats_d + (size_t)j * 6, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
            "read stats");
         p += 6 * sizeof(double);
@@ -825,7 +879,7 @@ spg_status spg_set_state(spg_ctx *ctx, const void *blob, size_t size)
     StateHeader h;
     std::memcpy(&h, p, sizeof(h));
     p += sizeof(h);
-    if (h.magic != kStateMagic || h.version != 2 || h.nvol != ctx->nvol || h.dtype != (int)ctx->opt.data_dtype ||
+    if (h.magic != kStateMagic || h.version != 3 || h.nvol != ctx->nvol || h.dtype != (int)ctx->opt.data_dtype ||
         h.momentum != (int)ctx->opt.momentum || h.storage != (int)ctx->opt.iterate_storage)
         return fail(ctx, SPG_EINVAL, "spg_set_state: blob does not match this context");
     CK(cudaStreamSynchronize(ctx->stream), "synchronise");
@@ -848,6 +902,12 @@ spg_status spg_set_state(spg_ctx *ctx, const void *blob, size_t size)
         std::memcpy(&dev[j].tau, p, sizeof(float));
         ctx->vols_h[j].tau = dev[j].tau;
         p += sizeof(float);
+        std::memcpy(&dev[j].beta_last, p, sizeof(float));
+        p += sizeof(float);
+        int32_t km[2];
+        std::memcpy(km, p, sizeof(km));
+        dev[j].kmom = km[0];
+        p += sizeof(km);
         CK(cudaMemcpyAsync(ctx->rstats_d + (size_t)j * 6, p, 6 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
            "write stats");
         CK(cudaStreamSynchronize(ctx->stream), "synchronise");
@@ -917,7 +977,7 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
     CK(sc.get(&m, vb), "alloc");
     CK(sc.get(&accb, vb), "alloc");
     CK(sc.get(&accw, vb), "alloc");
-    CK(sc.get(&pp, (size_t)K * d.nz * 4 * sizeof(double)), "alloc scalar partials");
+    CK(sc.get(&pp, (size_t)K * d.nz * AUX_SEG * 4 * sizeof(double)), "alloc scalar partials");
     const auto beta = beta_table_host(ctx, K);
     auto vol_at = [&](float *base, int i) { return base + (size_t)i * ctx->total; };
 
@@ -983,7 +1043,7 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
             a.gprev = k >= 1 ? ga[iprev] : ga[icur];
             a.gb = accb;
             a.gw = accw;
-            a.plane_part = pp + (size_t)k * d.nz * 4;
+            a.plane_part = pp + (size_t)k * d.nz * AUX_SEG * 4;
             CK(launch_adjoint_mask(a, ctx->stream), "adjoint mask");
             CK(launch_adjoint_apply(a, ctx->stream), "adjoint apply");
             ctx->launches += 2;
@@ -997,14 +1057,15 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
     }
     if ((s = copy_volume_out(ctx, gb, accb, 4, d)) != SPG_OK) return s;
     if ((s = copy_volume_out(ctx, gw, accw, 4, d)) != SPG_OK) return s;
-    std::vector<double> hp((size_t)K * d.nz * 4);
+    const size_t segs = (size_t)d.nz * AUX_SEG;
+    std::vector<double> hp((size_t)K * segs * 4);
     CK(cudaMemcpyAsync(hp.data(), pp, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "read");
     CK(cudaStreamSynchronize(ctx->stream), "synchronise");
     double s1 = 0, s2 = 0;
     for (int k = K - 1; k >= 0; k--)
-        for (int z = 0; z < d.nz; z++) {
-            s1 += hp[((size_t)k * d.nz + z) * 4 + 0];
-            s2 += hp[((size_t)k * d.nz + z) * 4 + 1];
+        for (size_t q = 0; q < segs; q++) {
+            s1 += hp[((size_t)k * segs + q) * 4 + 0];
+            s2 += hp[((size_t)k * segs + q) * 4 + 1];
         }
     g_scalars[0] = s1;
     g_scalars[1] = s2;
@@ -1092,10 +1153,26 @@ spg_status spg_autotune(spg_ctx *ctx, int trial_iters, int info[6])
     std::vector<double> hist0((size_t)ctx->hist_cap * ctx->nvol * 5);
     CK(cudaMemcpyAsync(hist0.data(), ctx->hist_d, hist0.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
        "save history");
+    std::vector<VolDesc> vd0(ctx->nvol);  // device-owned tau and extrapolation index
+    CK(cudaMemcpyAsync(vd0.data(), ctx->vols_d, ctx->nvol * sizeof(VolDesc), cudaMemcpyDeviceToHost, ctx->stream),
+       "save descriptors");
     CK(cudaStreamSynchronize(ctx->stream), "synchronise");
     const long long kt0 = ctx->k_total;
     const int kr0 = ctx->k_round;
     auto restore = [&]() -> spg_status {
+        std::vector<VolDesc> cur(ctx->nvol);
+        CK(cudaMemcpyAsync(cur.data(), ctx->vols_d, ctx->nvol * sizeof(VolDesc), cudaMemcpyDeviceToHost,
+                           ctx->stream),
+           "read descriptors");
+        CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+        for (int j = 0; j < ctx->nvol; j++) {
+            cur[j].tau = vd0[j].tau;
+            cur[j].kmom = vd0[j].kmom;
+            cur[j].beta_last = vd0[j].beta_last;
+        }
+        CK(cudaMemcpyAsync(ctx->vols_d, cur.data(), ctx->nvol * sizeof(VolDesc), cudaMemcpyHostToDevice,
+                           ctx->stream),
+           "restore descriptors");
         CK(cudaMemcpyAsync(ctx->X[c0], sx, vb, cudaMemcpyDeviceToDevice, ctx->stream), "restore");
         CK(cudaMemcpyAsync(ctx->X[ctx->aux_of(c0)], sa, vb, cudaMemcpyDeviceToDevice, ctx->stream), "restore");
         CK(cudaMemcpyAsync(ctx->st_d, &st0, sizeof(st0), cudaMemcpyHostToDevice, ctx->stream), "restore state");

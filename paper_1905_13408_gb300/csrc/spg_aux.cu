@@ -17,6 +17,14 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int AUX_THREADS = 256;
 
+// Each z-plane is split into AUX_SEG row segments, one CTA each; partial sums
+// are kept per segment (index plane * AUX_SEG + segment).
+__device__ __forceinline__ void seg_rows(int ny, int seg, int &r0, int &r1)
+{
+    r0 = (int)((long long)ny * seg / AUX_SEG);
+    r1 = (int)((long long)ny * (seg + 1) / AUX_SEG);
+}
+
 struct KSum {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float v)
@@ -97,11 +105,13 @@ __global__ void validate_kernel(AuxParams a, int vol, const void *b, const void 
     __shared__ double scratch[32 * 4];
     __shared__ int flag;
     const VolDesc V = a.vols[vol];
-    const int z = blockIdx.x;
+    const int z = blockIdx.x / AUX_SEG;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
     double mx = 0.0, mn = INFINITY;
     double bad_w = 0, bad_b = 0;
-    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
-        const int x = t % V.nx, y = t / V.nx;
+    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
+        const int x = t % V.nx, y = r0 + t / V.nx;
         const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
         const float wv = ld_data(w, bf16, i), bv = ld_data(b, bf16, i);
         if (!(wv > 0.f) || !isfinite(wv)) bad_w += 1;
@@ -116,7 +126,7 @@ __global__ void validate_kernel(AuxParams a, int vol, const void *b, const void 
     double c[2] = {bad_w, bad_b};
     block_sum<2>(c, scratch);
     if (threadIdx.x == 0) {
-        double *pp = a.plane_part + (long long)z * 4;
+        double *pp = a.plane_part + (long long)blockIdx.x * 4;
         pp[0] = mx;
         pp[1] = -nmn;
         pp[2] = c[0];
@@ -125,7 +135,7 @@ __global__ void validate_kernel(AuxParams a, int vol, const void *b, const void 
     if (!last_block(&a.st->ticket_aux, &flag)) return;
     if (threadIdx.x == 0) {
         double m = 0, n = INFINITY, bw = 0, bb = 0;
-        for (int q = 0; q < V.nz; q++) {
+        for (int q = 0; q < V.nz * AUX_SEG; q++) {
             const double *pp = a.plane_part + (long long)q * 4;
             m = fmax(m, __ldcg(pp + 0));
             n = fmin(n, __ldcg(pp + 1));
@@ -138,6 +148,103 @@ __global__ void validate_kernel(AuxParams a, int vol, const void *b, const void 
         o[2] = bw;
         o[3] = bb;
         maxw_out[vol] = m;
+        a.st->ticket_aux = 0;
+        __threadfence();
+    }
+}
+
+// ---------------- implicit-gradient anchor (Eq. 22 / Eq. 31) ----------------
+__device__ __forceinline__ void st_data(void *p, bool bf16, long long i, float v)
+{
+    if (bf16) {
+        __nv_bfloat16 h = __float2bfloat16_rn(v);
+        reinterpret_cast<uint16_t *>(p)[i] = *reinterpret_cast<uint16_t *>(&h);
+    } else {
+        reinterpret_cast<float *>(p)[i] = v;
+    }
+}
+
+// w' = w + 2 gamma, b' = (w b + 2 gamma a) / w'; then max w' per volume.
+__global__ void anchor_kernel(AuxParams a, int vol, void *b, void *w, bool bf16, const float *anchor, float gamma,
+                              double *maxw_out)
+{
+    __shared__ double scratch[32 * 4];
+    __shared__ int flag;
+    const VolDesc V = a.vols[vol];
+    const int z = blockIdx.x / AUX_SEG;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
+    double mx = 0.0;
+    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
+        const int x = t % V.nx, y = r0 + t / V.nx;
+        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+        const float wv = ld_data(w, bf16, i), bv = ld_data(b, bf16, i);
+        const float w2 = wv + 2.0f * gamma;
+        const float b2 = (wv * bv + 2.0f * gamma * anchor[i]) / w2;
+        st_data(w, bf16, i, w2);
+        st_data(b, bf16, i, b2);
+        mx = fmax(mx, (double)ld_data(w, bf16, i));
+    }
+    mx = block_max(mx, scratch);
+    if (threadIdx.x == 0) a.plane_part[(long long)blockIdx.x * 4] = mx;
+    if (!last_block(&a.st->ticket_aux, &flag)) return;
+    if (threadIdx.x == 0) {
+        double m = 0;
+        for (int q = 0; q < V.nz * AUX_SEG; q++) m = fmax(m, __ldcg(a.plane_part + (long long)q * 4));
+        maxw_out[vol] = m;
+        a.st->ticket_aux = 0;
+        __threadfence();
+    }
+}
+
+// Sec. 2.5 scales: sum (w b)^2, sum w, max w, min w of one volume.
+__global__ void scales_kernel(AuxParams a, int vol, const void *b, const void *w, bool bf16)
+{
+    __shared__ double scratch[32 * 4];
+    __shared__ int flag;
+    const VolDesc V = a.vols[vol];
+    const int z = blockIdx.x / AUX_SEG;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
+    KSum s2, sw;
+    double mx = 0.0, mn = INFINITY;
+    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
+        const int x = t % V.nx, y = r0 + t / V.nx;
+        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+        const float wv = ld_data(w, bf16, i), bv = ld_data(b, bf16, i);
+        const float n = wv * bv;
+        s2.add(n * n);
+        sw.add(wv);
+        mx = fmax(mx, (double)wv);
+        mn = fmin(mn, (double)wv);
+    }
+    mx = block_max(mx, scratch);
+    const double nmn = block_max(-mn, scratch);
+    double v[2] = {s2.value(), sw.value()};
+    block_sum<2>(v, scratch);
+    if (threadIdx.x == 0) {
+        double *pp = a.plane_part + (long long)blockIdx.x * 4;
+        pp[0] = v[0];
+        pp[1] = v[1];
+        pp[2] = mx;
+        pp[3] = -nmn;
+    }
+    if (!last_block(&a.st->ticket_aux, &flag)) return;
+    if (threadIdx.x == 0) {
+        double q2 = 0, qw = 0, m = 0, n = INFINITY;
+        for (int q = 0; q < V.nz * AUX_SEG; q++) {
+            const double *pp = a.plane_part + (long long)q * 4;
+            q2 += __ldcg(pp + 0);
+            qw += __ldcg(pp + 1);
+            m = fmax(m, __ldcg(pp + 2));
+            n = fmin(n, __ldcg(pp + 3));
+        }
+        const double cnt = (double)V.nx * V.ny * V.nz;
+        double *o = a.vol_out + (long long)vol * 8;
+        o[0] = sqrt(q2 / cnt);
+        o[1] = qw / cnt;
+        o[2] = m;
+        o[3] = n;
         a.st->ticket_aux = 0;
         __threadfence();
     }
@@ -218,16 +325,18 @@ __global__ void reweight_kernel(AuxParams a, const float *xcur, float *om1, floa
 {
     __shared__ double scratch[32 * 4];
     __shared__ int flag;
-    const int plane = blockIdx.x;
+    const int plane = blockIdx.x / AUX_SEG;
     const int vol = a.plane_vol[plane];
     const VolDesc V = a.vols[vol];
     const int z = plane - V.plane_begin;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
     const Field F{xcur, nullptr, 0.f};
     double mx = 0.0;
     KSum c1, c2;
     float nnz = 0.f;
-    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
-        const int x = t % V.nx, y = t / V.nx;
+    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
+        const int x = t % V.nx, y = r0 + t / V.nx;
         const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
         float g[3];
         grad_at(V, F, x, y, z, g);
@@ -246,7 +355,7 @@ __global__ void reweight_kernel(AuxParams a, const float *xcur, float *om1, floa
     double s[3] = {(double)nnz, c1.value(), c2.value()};
     block_sum<3>(s, scratch);
     if (threadIdx.x == 0) {
-        double *pp = a.plane_part + (long long)plane * 4;
+        double *pp = a.plane_part + (long long)blockIdx.x * 4;
         pp[0] = mx;
         pp[1] = s[0];
         pp[2] = s[1];
@@ -258,7 +367,7 @@ __global__ void reweight_kernel(AuxParams a, const float *xcur, float *om1, floa
         const VolDesc W = a.vols[v];
         double m = 0, n = 0, s1 = 0, s2 = 0;
         if (lane == 0) {
-            for (int q = W.plane_begin; q < W.plane_begin + W.nz; q++) {
+            for (int q = W.plane_begin * AUX_SEG; q < (W.plane_begin + W.nz) * AUX_SEG; q++) {
                 const double *pp = a.plane_part + (long long)q * 4;
                 m = fmax(m, __ldcg(pp + 0));
                 n += __ldcg(pp + 1);
@@ -275,6 +384,8 @@ __global__ void reweight_kernel(AuxParams a, const float *xcur, float *om1, floa
             o[4] = L;
             o[5] = tau;
             vols_rw[v].tau = (float)tau;
+            vols_rw[v].kmom = 0;  // extrapolation restarts with the round
+            vols_rw[v].beta_last = 0.f;
         }
     }
     __syncthreads();
@@ -291,15 +402,17 @@ __global__ void objective_kernel(AuxParams a, const float *xcur, const void *b, 
 {
     __shared__ double scratch[32 * 4];
     __shared__ int flag;
-    const int plane = blockIdx.x;
+    const int plane = blockIdx.x / AUX_SEG;
     const int vol = a.plane_vol[plane];
     const VolDesc V = a.vols[vol];
     const int z = plane - V.plane_begin;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
     const Field F{xcur, nullptr, 0.f};
     KSum kd, kl, kt;
     const float mu = V.mu;
-    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
-        const int x = t % V.nx, y = t / V.nx;
+    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
+        const int x = t % V.nx, y = r0 + t / V.nx;
         const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
         float g[3];
         grad_at(V, F, x, y, z, g);
@@ -314,7 +427,7 @@ __global__ void objective_kernel(AuxParams a, const float *xcur, const void *b, 
     double s[3] = {kd.value(), kl.value(), kt.value()};
     block_sum<3>(s, scratch);
     if (threadIdx.x == 0) {
-        double *pp = a.plane_part + (long long)plane * 4;
+        double *pp = a.plane_part + (long long)blockIdx.x * 4;
         pp[0] = s[0];
         pp[1] = s[1];
         pp[2] = s[2];
@@ -326,7 +439,7 @@ __global__ void objective_kernel(AuxParams a, const float *xcur, const void *b, 
         if (lane != 0) continue;
         const VolDesc W = a.vols[v];
         double d = 0, l = 0, t = 0;
-        for (int q = W.plane_begin; q < W.plane_begin + W.nz; q++) {
+        for (int q = W.plane_begin * AUX_SEG; q < (W.plane_begin + W.nz) * AUX_SEG; q++) {
             const double *pp = a.plane_part + (long long)q * 4;
             d += __ldcg(pp + 0);
             l += __ldcg(pp + 1);
@@ -354,18 +467,20 @@ __global__ void certificate_kernel(AuxParams a, const float *xplus, const float 
 {
     __shared__ double scratch[32 * 4];
     __shared__ int flag;
-    const int plane = blockIdx.x;
+    const int plane = blockIdx.x / AUX_SEG;
     const int vol = a.plane_vol[plane];
     const VolDesc V = a.vols[vol];
     const int z = plane - V.plane_begin;
-    const int kr = a.st->k_round;
-    const float beta = kr >= 1 ? beta_tab[kr - 1] : 0.f;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
+    (void)beta_tab;
+    const float beta = V.beta_last;  // extrapolation weight of the step that produced x+
     const Field Fy{xk, xkm1, beta, dk};
     const Field Fx{xplus, nullptr, 0.f};
     (void)b;
     KSum ks;
-    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
-        const int x = t % V.nx, y = t / V.nx;
+    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
+        const int x = t % V.nx, y = r0 + t / V.nx;
         const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
         const float dy = (xk[i] - xplus[i]) + beta * Fy.d(i);
         const float dv = div_at(V, Fx, omtv, x, y, z) - div_at(V, Fy, omtv, x, y, z);
@@ -374,14 +489,14 @@ __global__ void certificate_kernel(AuxParams a, const float *xplus, const float 
     }
     double s[1] = {ks.value()};
     block_sum<1>(s, scratch);
-    if (threadIdx.x == 0) a.plane_part[(long long)plane * 4] = s[0];
+    if (threadIdx.x == 0) a.plane_part[(long long)blockIdx.x * 4] = s[0];
     if (!last_block(&a.st->ticket_aux, &flag)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int v = warp; v < a.nvol; v += blockDim.x / 32) {
         if (lane != 0) continue;
         const VolDesc W = a.vols[v];
         double acc = 0;
-        for (int q = W.plane_begin; q < W.plane_begin + W.nz; q++) acc += __ldcg(a.plane_part + (long long)q * 4);
+        for (int q = W.plane_begin * AUX_SEG; q < (W.plane_begin + W.nz) * AUX_SEG; q++) acc += __ldcg(a.plane_part + (long long)q * 4);
         a.vol_out[(long long)v * 8 + 4] = acc;
     }
     __syncthreads();
@@ -397,10 +512,12 @@ __global__ void plain_step_kernel(const VolDesc *vols, const float *xk, const fl
                                   float *xout)
 {
     const VolDesc V = vols[0];
-    const int z = blockIdx.x;
+    const int z = blockIdx.x / AUX_SEG;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
     const Field F{xk, xkm1, beta};
-    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
-        const int x = t % V.nx, y = t / V.nx;
+    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
+        const int x = t % V.nx, y = r0 + t / V.nx;
         const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
         const float d = xk[i] - xkm1[i];
         const float g = ld_data(w, bf16, i) * ((xk[i] - ld_data(b, bf16, i)) + beta * d) +
@@ -419,11 +536,13 @@ __global__ void adjoint_mask_kernel(AdjParams a)
 {
     __shared__ double scratch[32 * 4];
     const VolDesc V = a.vols[0];
-    const int z = blockIdx.x;
+    const int z = blockIdx.x / AUX_SEG;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
     const Field F{a.xk, a.xkm1, a.beta};
     KSum k1, k2;
-    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
-        const int x = t % V.nx, y = t / V.nx;
+    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
+        const int x = t % V.nx, y = r0 + t / V.nx;
         const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
         const float d = a.xk[i] - a.xkm1[i];
         const float bv = ld_data(a.b, a.bf16, i), wv = ld_data(a.w, a.bf16, i);
@@ -444,8 +563,8 @@ __global__ void adjoint_mask_kernel(AdjParams a)
     double s[2] = {k1.value(), k2.value()};
     block_sum<2>(s, scratch);
     if (threadIdx.x == 0) {
-        a.plane_part[(long long)z * 4 + 0] = s[0];
-        a.plane_part[(long long)z * 4 + 1] = s[1];
+        a.plane_part[(long long)blockIdx.x * 4 + 0] = s[0];
+        a.plane_part[(long long)blockIdx.x * 4 + 1] = s[1];
     }
 }
 
@@ -487,10 +606,12 @@ __device__ __forceinline__ void hv_at(const VolDesc &V, const Field &F, const fl
 __global__ void adjoint_apply_kernel(AdjParams a)
 {
     const VolDesc V = a.vols[0];
-    const int z = blockIdx.x;
+    const int z = blockIdx.x / AUX_SEG;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
     const Field F{a.xk, a.xkm1, a.beta};
-    for (int t = threadIdx.x; t < V.nx * V.ny; t += blockDim.x) {
-        const int x = t % V.nx, y = t / V.nx;
+    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
+        const int x = t % V.nx, y = r0 + t / V.nx;
         const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
         float hc[3], hx[3], hy[3], hz[3];
         hv_at(V, F, a.m, a.omtv, x, y, z, hc);
@@ -510,7 +631,21 @@ __global__ void adjoint_apply_kernel(AdjParams a)
 cudaError_t launch_validate(const AuxParams &a, int vol, int nz, const void *b, const void *w, bool bf16,
                             double *maxw_out, cudaStream_t s)
 {
-    validate_kernel<<<nz, AUX_THREADS, 0, s>>>(a, vol, b, w, bf16, maxw_out);
+    validate_kernel<<<nz * AUX_SEG, AUX_THREADS, 0, s>>>(a, vol, b, w, bf16, maxw_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_anchor(const AuxParams &a, int vol, int nz, void *b, void *w, bool bf16, const float *anchor,
+                          float gamma, double *maxw_out, cudaStream_t s)
+{
+    anchor_kernel<<<nz * AUX_SEG, AUX_THREADS, 0, s>>>(a, vol, b, w, bf16, anchor, gamma, maxw_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scales(const AuxParams &a, int vol, int nz, const void *b, const void *w, bool bf16,
+                          cudaStream_t s)
+{
+    scales_kernel<<<nz * AUX_SEG, AUX_THREADS, 0, s>>>(a, vol, b, w, bf16);
     return cudaGetLastError();
 }
 
@@ -529,21 +664,21 @@ cudaError_t launch_convert_to_f32(const uint16_t *src, float *dst, long long n, 
 cudaError_t launch_reweight(const AuxParams &a, const float *const *xbuf, float *om1, float *omtv,
                             const double *maxw, double *rstats, VolDesc *vols_rw, cudaStream_t s)
 {
-    reweight_kernel<<<a.nplanes, AUX_THREADS, 0, s>>>(a, xbuf[0], om1, omtv, maxw, rstats, vols_rw);
+    reweight_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a, xbuf[0], om1, omtv, maxw, rstats, vols_rw);
     return cudaGetLastError();
 }
 
 cudaError_t launch_objective(const AuxParams &a, const float *const *xbuf, const void *b, const void *w,
                              bool bf16, const float *om1, const float *omtv, cudaStream_t s)
 {
-    objective_kernel<<<a.nplanes, AUX_THREADS, 0, s>>>(a, xbuf[0], b, w, bf16, om1, omtv);
+    objective_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a, xbuf[0], b, w, bf16, om1, omtv);
     return cudaGetLastError();
 }
 
 cudaError_t launch_certificate(const AuxParams &a, const float *const *xbuf, const float *beta, const void *b,
                                const void *w, bool bf16, const float *omtv, cudaStream_t s)
 {
-    certificate_kernel<<<a.nplanes, AUX_THREADS, 0, s>>>(a, xbuf[0], xbuf[1], xbuf[2], xbuf[3], beta, b, w, bf16,
+    certificate_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a, xbuf[0], xbuf[1], xbuf[2], xbuf[3], beta, b, w, bf16,
                                                          omtv);
     return cudaGetLastError();
 }
@@ -552,19 +687,19 @@ cudaError_t launch_plain_step(const VolDesc *vols, int nplanes, const float *xk,
                               const void *b, const void *w, bool bf16, const float *om1, const float *omtv,
                               float *xout, cudaStream_t s)
 {
-    plain_step_kernel<<<nplanes, AUX_THREADS, 0, s>>>(vols, xk, xkm1, beta, b, w, bf16, om1, omtv, xout);
+    plain_step_kernel<<<nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(vols, xk, xkm1, beta, b, w, bf16, om1, omtv, xout);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_mask(const AdjParams &a, cudaStream_t s)
 {
-    adjoint_mask_kernel<<<a.nplanes, AUX_THREADS, 0, s>>>(a);
+    adjoint_mask_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_apply(const AdjParams &a, cudaStream_t s)
 {
-    adjoint_apply_kernel<<<a.nplanes, AUX_THREADS, 0, s>>>(a);
+    adjoint_apply_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 

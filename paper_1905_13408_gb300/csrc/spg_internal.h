@@ -29,6 +29,8 @@ struct VolDesc {
     float tau;               // 1/L of the current round (written by the re-weighting kernel)
     int item_begin, item_end;    // work items of the fused step that belong to this volume
     int plane_begin;             // index of the volume's first z-plane among all planes
+    int kmom;                    // index of the next step's extrapolation weight in the beta table
+    float beta_last;             // extrapolation weight used by the last step
     int pad0;
 };
 
@@ -67,9 +69,10 @@ struct StepParams {
     float *xbuf[4];
     const float *beta;       // extrapolation table beta_k (float32)
     DevState *st;
-    double *partials;        // [nitems][3] objective partial sums of the last recorded step
+    double *partials;        // [nitems][4] objective sums (data, l1, tv) and restart dot of the last step
     double *hist;            // ring [hist_cap][nvol][5]
     int nitems, nvol, hist_cap, hist_every;
+    int restart;             // gradient restart of the extrapolation, per volume
     long long timeout_ns;    // bound on any single barrier wait
 };
 
@@ -86,14 +89,15 @@ cudaError_t step_configure(const StepVariant &v, int *ctas_per_sm);
 cudaError_t step_launch(const StepVariant &v, int grid, const StepParams &p, cudaStream_t s);
 bool step_variant_supported(const StepVariant &v);
 
-// Auxiliary kernels (spg_aux.cu). Every one runs one CTA per z-plane of
-// every volume and reduces per-plane partials in a fixed order.
+// Auxiliary kernels (spg_aux.cu). Every one runs AUX_SEG CTAs per z-plane of
+// every volume (row segments) and reduces per-segment partials in a fixed order.
+constexpr int AUX_SEG = 8;
 struct AuxParams {
     const VolDesc *vols;
     const int *plane_vol;    // volume of each global plane
     int nplanes, nvol;
     DevState *st;
-    double *plane_part;      // [nplanes][4]
+    double *plane_part;      // [nplanes * AUX_SEG][4]
     double *vol_out;         // [nvol][8]
 };
 
@@ -123,7 +127,7 @@ struct AdjParams {
     const float *gnext;
     float *m;                // scratch volume: masked cotangent of z
     float *gcur, *gprev, *gb, *gw;
-    double *plane_part;      // [nplanes][4]
+    double *plane_part;      // [nplanes * AUX_SEG][4]
 };
 cudaError_t launch_adjoint_mask(const AdjParams &a, cudaStream_t s);
 cudaError_t launch_adjoint_apply(const AdjParams &a, cudaStream_t s);
@@ -131,5 +135,11 @@ cudaError_t launch_plain_step(const VolDesc *vols, int nplanes, const float *xk,
                               float beta, const void *b, const void *w, bool bf16, const float *om1,
                               const float *omtv, float *xout, cudaStream_t s);
 cudaError_t launch_timeout_probe(DevState *st, long long timeout_ns, cudaStream_t s);
+// Fold gamma |x - a|^2 into (b, w) of volume `vol` (a: float32 volume in the pitched layout).
+cudaError_t launch_anchor(const AuxParams &a, int vol, int nz, void *b, void *w, bool bf16, const float *anchor,
+                          float gamma, double *maxw_out, cudaStream_t s);
+// RMS(w b), mean w, max w, min w of volume `vol` into vol_out[vol][0..3].
+cudaError_t launch_scales(const AuxParams &a, int vol, int nz, const void *b, const void *w, bool bf16,
+                          cudaStream_t s);
 
 }  // namespace spg

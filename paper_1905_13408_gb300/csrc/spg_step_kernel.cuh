@@ -190,8 +190,8 @@ struct Cfg {
     static constexpr int STAGE = OFF_O1 + al(O1_BYTES);
     static constexpr int OFF_PY = S * STAGE;                  // 3 x (TY+1) x TX floats
     static constexpr int OFF_HX = OFF_PY + al(3 * (TY + 1) * TX * 4);  // 3 x 32 floats
-    static constexpr int OFF_RED = OFF_HX + 3 * 32 * 4;       // 32 x 3 doubles
-    static constexpr int OFF_BAR = OFF_RED + 32 * 3 * 8;      // S mbarriers
+    static constexpr int OFF_RED = OFF_HX + 3 * 32 * 4;       // 32 x 4 doubles
+    static constexpr int OFF_BAR = OFF_RED + 32 * 4 * 8;      // S mbarriers
     static constexpr int OFF_ST = OFF_BAR + al(S * 8);        // state snapshot
     static constexpr int TOTAL = OFF_ST + 128 + 128;          // + alignment slack
     static constexpr int THREADS = 32 * (TY + 1);
@@ -227,7 +227,7 @@ __device__ __forceinline__ void issue_stage(unsigned char *sm, uint64_t *bars, c
 struct StateSnap {
     int cur, k_round, rec, last;
     long long k_total;
-    float beta, pad;
+    float pad0, pad1;
 };
 
 // Shared-memory carve-up of one CTA.
@@ -250,9 +250,9 @@ struct Pipe {
 // One work item: plane-by-plane march over [z0, z1) of one x-y tile.
 // REC adds the three sums of F(x_k) (data, l1, TV) for the item.
 // Returns true when a barrier wait gave up (the CTA then stops).
-template <int VX, int TY, int S, bool BF16, bool XD, bool REC>
+template <int VX, int TY, int S, bool BF16, bool XD, bool REC, bool DOT>
 __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pipe &pp_, const WorkItem &W, int it,
-                                         int ia, int ib, float beta, float *xout_base, float *dout_base)
+                                         int ia, int ib, float *xout_base, float *dout_base)
 {
     using C = Cfg<VX, TY, S, BF16>;
     constexpr int TX = C::TX, XW = C::XW, OW = C::OW;
@@ -262,6 +262,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
     const VolDesc V = P.vols[W.vol];
     const TmapSet *tm = P.tmaps + W.vol;
     const int nsteps = (W.z1 - W.z0) + 2;
+    const float beta = P.beta[V.kmom];  // per volume: restarts reset a volume's index
     const float tau = V.tau, lam_tv = V.lambda_tv, tl1 = V.tau * V.lambda_l1;
     const float inv_mu = 1.0f / V.mu, half_inv_mu = 0.5f / V.mu, half_mu = 0.5f * V.mu;
     const float mu2 = V.mu * V.mu;
@@ -285,7 +286,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
         dz[i] = 0.f;
         pp[0][i] = pp[1][i] = pp[2][i] = 0.f;
     }
-    KSum kd, kl, kt;
+    KSum kd, kl, kt, kr;  // objective sums and (DOT) the restart test <y - x+, x+ - x>
 
     const int gy = W.y0 + r;
     const int gx0 = W.x0 + VX * lane;
@@ -415,7 +416,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
             float pxn = __shfl_down_sync(FULL, pp[0][0], 1);
             if (lane == 31) pxn = sh.hx_ring[((j - 1) % 3) * 32 + r];
             float out[VX], inc[VX];
-            float dsum = 0.f, lsum = 0.f;
+            float dsum = 0.f, lsum = 0.f, rsum = 0.f;
 #pragma unroll
             for (int i = 0; i < VX; i++) {
                 const float pxr = (i < VX - 1) ? pp[0][(i + 1) % VX] : pxn;
@@ -427,6 +428,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
                 const float t = tl1 * oo[i];
                 inc[i] = fabsf(zz) < t ? -xz[i] : delta - copysignf(t, zz);
                 out[i] = xz[i] + inc[i];
+                if constexpr (DOT) rsum = fmaf(fmaf(beta, dz[i], -inc[i]), inc[i], rsum);  // (y - x+).(x+ - x)
                 if constexpr (REC) {
                     dsum = fmaf(0.5f * ww[i] * res, res, dsum);
                     lsum = fmaf(oo[i], fabsf(xz[i]), lsum);
@@ -436,6 +438,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
                 kd.add(dsum);
                 kl.add(lsum);
             }
+            if constexpr (DOT) kr.add(rsum);
             if (gy_in && gx0 < V.pitch) {
                 const long long o = V.off + ((long long)zo * V.ny + gy) * V.pitch + gx0;
                 st_vec<VX>(xout_base + o, out);
@@ -452,33 +455,22 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
         }
     }
 
-    if constexpr (REC) {
-        if (!aborted) {
-            // block reduction of the item's three sums, fixed order
-            double v0 = kd.value(), v1 = kl.value(), v2 = kt.value();
+    if (!aborted && (REC || DOT)) {
+        // block reduction of the item's sums, fixed order
+        double v[4] = {kd.value(), kl.value(), kt.value(), kr.value()};
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                v0 += __shfl_down_sync(FULL, v0, o);
-                v1 += __shfl_down_sync(FULL, v1, o);
-                v2 += __shfl_down_sync(FULL, v2, o);
-            }
-            if (lane == 0) {
-                sh.red[warp * 3 + 0] = v0;
-                sh.red[warp * 3 + 1] = v1;
-                sh.red[warp * 3 + 2] = v2;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double a0 = 0, a1 = 0, a2 = 0;
-                for (int q = 0; q < TY + 1; q++) {
-                    a0 += sh.red[q * 3 + 0];
-                    a1 += sh.red[q * 3 + 1];
-                    a2 += sh.red[q * 3 + 2];
-                }
-                P.partials[(long long)it * 3 + 0] = a0;
-                P.partials[(long long)it * 3 + 1] = a1;
-                P.partials[(long long)it * 3 + 2] = a2;
-            }
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 4; q++) v[q] += __shfl_down_sync(FULL, v[q], o);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 4; q++) sh.red[warp * 4 + q] = v[q];
+        __syncthreads();
+        if (tid == 0) {
+            double a[4] = {0, 0, 0, 0};
+            for (int w = 0; w < TY + 1; w++)
+                for (int q = 0; q < 4; q++) a[q] += sh.red[w * 4 + q];
+            for (int q = 0; q < 4; q++) P.partials[(long long)it * 4 + q] = a[q];
         }
     }
     __syncthreads();  // every stage consumed before the next item's prologue
@@ -508,7 +500,6 @@ __global__ void __launch_bounds__(32 * (TY + 1), MINB)
         s.k_round = st->k_round;
         s.k_total = st->k_total;
         s.rec = (P.hist_every > 0 && (s.k_total % P.hist_every) == 0) ? 1 : 0;
-        s.beta = P.beta[s.k_round];
         s.last = 0;
         *sh.snap = s;
         for (int i = 0; i < S; i++) mbar_init(&sh.bars[i], 1);
@@ -519,7 +510,6 @@ __global__ void __launch_bounds__(32 * (TY + 1), MINB)
     const int cur = sh.snap->cur;
     const int nxt = XD ? (cur ^ 1) : (cur + 1) % 3;
     const int ia = cur, ib = XD ? 2 + cur : (cur + 2) % 3;
-    const float beta = sh.snap->beta;
     const bool rec = sh.snap->rec != 0;
     // select without indexing the parameter array (keeps the parameters out of local memory)
     auto pick = [&](int i) { return i == 0 ? P.xbuf[0] : (i == 1 ? P.xbuf[1] : (i == 2 ? P.xbuf[2] : P.xbuf[3])); };
@@ -539,8 +529,13 @@ __global__ void __launch_bounds__(32 * (TY + 1), MINB)
     bool aborted = false;
     for (int it = blockIdx.x; it < P.nitems && !aborted; it += gridDim.x) {
         const WorkItem W = P.items[it];
-        aborted = rec ? run_item<VX, TY, S, BF16, XD, true>(P, sh, pipe, W, it, ia, ib, beta, xout_base, dout_base)
-                      : run_item<VX, TY, S, BF16, XD, false>(P, sh, pipe, W, it, ia, ib, beta, xout_base, dout_base);
+        if (P.restart)
+            aborted = rec ? run_item<VX, TY, S, BF16, XD, true, true>(P, sh, pipe, W, it, ia, ib, xout_base, dout_base)
+                          : run_item<VX, TY, S, BF16, XD, false, true>(P, sh, pipe, W, it, ia, ib, xout_base, dout_base);
+        else
+            aborted = rec ? run_item<VX, TY, S, BF16, XD, true, false>(P, sh, pipe, W, it, ia, ib, xout_base, dout_base)
+                          : run_item<VX, TY, S, BF16, XD, false, false>(P, sh, pipe, W, it, ia, ib, xout_base,
+                                                                        dout_base);
     }
 
     if (aborted && warp == TY && lane == 0) {
@@ -562,32 +557,37 @@ __global__ void __launch_bounds__(32 * (TY + 1), MINB)
     __syncthreads();
     if (!sh.snap->last) return;
     __threadfence();
-    if (rec) {
+    {
+        // per volume: objective history (recorded steps), restart test, and
+        // the extrapolation index of the next step
         const int hslot = P.st->hist_count % P.hist_cap;
+        const bool sums = rec || P.restart != 0;
+        VolDesc *vols_rw = const_cast<VolDesc *>(P.vols);
         for (int v = warp; v < P.nvol; v += TY + 1) {
             const VolDesc V = P.vols[v];
-            double a0 = 0, a1 = 0, a2 = 0;
-            for (int q = V.item_begin + lane; q < V.item_end; q += 32) {
-                a0 += __ldcg(P.partials + (long long)q * 3 + 0);
-                a1 += __ldcg(P.partials + (long long)q * 3 + 1);
-                a2 += __ldcg(P.partials + (long long)q * 3 + 2);
-            }
+            double a[4] = {0, 0, 0, 0};
+            if (sums) {
+                for (int q = V.item_begin + lane; q < V.item_end; q += 32)
+                    for (int c = 0; c < 4; c++) a[c] += __ldcg(P.partials + (long long)q * 4 + c);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a0 += __shfl_down_sync(FULL, a0, o);
-                a1 += __shfl_down_sync(FULL, a1, o);
-                a2 += __shfl_down_sync(FULL, a2, o);
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int c = 0; c < 4; c++) a[c] += __shfl_down_sync(FULL, a[c], o);
             }
             if (lane == 0) {
-                double *h = P.hist + ((long long)hslot * P.nvol + v) * 5;
-                const double l1 = (double)V.lambda_l1 * a1, tv = (double)V.lambda_tv * a2;
-                const double tot = a0 + l1 + tv;
-                h[0] = (double)sh.snap->k_total;
-                h[1] = a0;
-                h[2] = l1;
-                h[3] = tv;
-                h[4] = tot;
-                if (!isfinite(tot)) atomicCAS(&P.st->err, 0, (int)SPG_ENONFINITE);
+                if (rec) {
+                    double *h = P.hist + ((long long)hslot * P.nvol + v) * 5;
+                    const double l1 = (double)V.lambda_l1 * a[1], tv = (double)V.lambda_tv * a[2];
+                    const double tot = a[0] + l1 + tv;
+                    h[0] = (double)sh.snap->k_total;
+                    h[1] = a[0];
+                    h[2] = l1;
+                    h[3] = tv;
+                    h[4] = tot;
+                    if (!isfinite(tot)) atomicCAS(&P.st->err, 0, (int)SPG_ENONFINITE);
+                }
+                vols_rw[v].beta_last = P.beta[V.kmom];
+                vols_rw[v].kmom = (P.restart != 0 && a[3] > 0.0) ? 0 : V.kmom + 1;
             }
         }
     }

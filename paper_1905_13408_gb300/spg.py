@@ -36,7 +36,8 @@ EXPORTS = ["spg_create", "spg_create_batch", "spg_set_data", "spg_set_x", "spg_g
            "spg_iterate", "spg_objective", "spg_history", "spg_round_stats", "spg_certificate", "spg_counters",
            "spg_get_state", "spg_set_state", "spg_backward", "spg_unrolled", "spg_probe_timeout",
            "spg_autotune", "spg_launch_count", "spg_plan_info", "spg_last_error", "spg_destroy",
-           "spg_objective_noalloc", "spg_noalloc_last_error"]
+           "spg_objective_noalloc", "spg_noalloc_last_error", "spg_set_anchor", "spg_param_scales",
+           "spg_fsc", "spg_fsc_last_error"]
 
 
 class SPGError(RuntimeError):
@@ -54,7 +55,8 @@ class VolumeParams(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("data_dtype", ctypes.c_int), ("momentum", ctypes.c_int), ("hist_every", ctypes.c_int),
                 ("hist_capacity", ctypes.c_int), ("max_iters_per_round", ctypes.c_int), ("tile", ctypes.c_int),
-                ("zchunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("iterate_storage", ctypes.c_int)]
+                ("zchunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("iterate_storage", ctypes.c_int),
+                ("restart", ctypes.c_int)]
 
 
 _lib = None
@@ -100,6 +102,10 @@ def load():
             "spg_objective_noalloc": (I, [I, I, I, ctypes.c_float, ctypes.c_float, ctypes.c_float, V, V, V, V, V,
                                           V, P]),
             "spg_noalloc_last_error": (ctypes.c_char_p, []),
+            "spg_set_anchor": (I, [P, I, ctypes.c_float, V]),
+            "spg_fsc": (I, [I, V, V, I, ctypes.POINTER(D), ctypes.POINTER(D), P]),
+            "spg_fsc_last_error": (ctypes.c_char_p, []),
+            "spg_param_scales": (I, [P, I, ctypes.POINTER(D)]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -158,6 +164,32 @@ def spg_set_data(h, vol, b, w, dtype=SPG_F32):
     pb, kb = _ptr(b, dt)
     pw, kw = _ptr(w, dt)
     _check(load().spg_set_data(h, vol, pb, pw, dtype), h)
+
+
+def spg_set_anchor(h, vol, gamma, x_anchor):
+    pa, ka = _ptr(x_anchor)
+    _check(load().spg_set_anchor(h, vol, float(gamma), pa), h)
+
+
+def spg_param_scales(h, vol=0):
+    out = (ctypes.c_double * 4)()
+    _check(load().spg_param_scales(h, vol, out), h)
+    return dict(zip(["rms_wb", "mean_w", "max_w", "min_w"], out[:]))
+
+
+def spg_fsc(a, b, stream=None):
+    """(fsc, counts) for shells 0 .. n/2 of two n^3 float32 maps (Eq. 30)."""
+    n = int(a.shape[0])
+    pa, ka = _ptr(a)
+    pb, kb = _ptr(b)
+    m = n // 2 + 1
+    fsc = np.zeros(m)
+    cnt = np.zeros(m)
+    st = load().spg_fsc(n, pa, pb, m, fsc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(stream or 0))
+    if st != SPG_OK:
+        raise SPGError(st, load().spg_fsc_last_error().decode())
+    return fsc, cnt
 
 
 def spg_set_x(h, vol, x):
@@ -237,11 +269,13 @@ def parse_state(blob, shapes):
         arr = np.frombuffer(blob, dtype=np.float32, count=4 * n, offset=off).reshape(4, *sh)
         off += 16 * n
         tau = float(np.frombuffer(blob, dtype=np.float32, count=1, offset=off)[0])
-        off += 4
+        beta_last = float(np.frombuffer(blob, dtype=np.float32, count=1, offset=off + 4)[0])
+        kmom = int(np.frombuffer(blob, dtype=np.int32, count=1, offset=off + 8)[0])
+        off += 16
         stats = np.frombuffer(blob, dtype=np.float64, count=6, offset=off).copy() if off % 8 == 0 else \
             np.frombuffer(bytes(blob[off:off + 48]), dtype=np.float64).copy()
         off += 48
-        v = dict(x=arr[0], om1=arr[2], omtv=arr[3], tau=tau, stats=stats)
+        v = dict(x=arr[0], om1=arr[2], omtv=arr[3], tau=tau, stats=stats, beta_last=beta_last, kmom=kmom)
         if storage == SPG_STORE_DELTA:
             v["d"] = arr[1]
             # the difference of two float32 values is exact in float64 here
@@ -313,14 +347,16 @@ class SPG:
     """A solver context over one or more volumes (one fused launch per iteration)."""
 
     def __init__(self, volumes, data_dtype="f32", momentum="fista", hist_every=1, hist_capacity=4096,
-                 max_iters=100000, tile="auto", zchunk=0, ctas_per_sm=0, storage="delta", stream=None):
+                 max_iters=100000, tile="auto", zchunk=0, ctas_per_sm=0, storage="delta", restart=False,
+                 stream=None):
         if isinstance(volumes, dict):
             volumes = [volumes]
         self.shapes = [tuple(v["shape"]) for v in volumes]
         params = [volume_params(v["shape"], **{k: v[k] for k in v if k != "shape"}) for v in volumes]
         opt = Options(SPG_F32 if data_dtype == "f32" else SPG_BF16, SPG_FISTA if momentum == "fista" else SPG_ISTA,
                       hist_every, hist_capacity, max_iters, TILES[tile] if isinstance(tile, str) else int(tile),
-                      zchunk, ctas_per_sm, SPG_STORE_DELTA if storage == "delta" else SPG_STORE_PREV)
+                      zchunk, ctas_per_sm, SPG_STORE_DELTA if storage == "delta" else SPG_STORE_PREV,
+                      1 if restart else 0)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -335,6 +371,12 @@ class SPG:
 
     def set_x(self, vol, x):
         spg_set_x(self.handle, vol, x)
+
+    def set_anchor(self, vol, gamma, x_anchor):
+        spg_set_anchor(self.handle, vol, gamma, x_anchor)
+
+    def param_scales(self, vol=0):
+        return spg_param_scales(self.handle, vol)
 
     def get_x(self, vol=0, out=None):
         import torch

@@ -142,3 +142,15 @@ def random_volume(shape, seed, positive=False, scale=1.0):
     if positive:
         a = np.exp(0.5 * a)
     return a
+
+
+def make_half_maps(shape, blobs, radius, seed, noise_sd=0.3, field_sigma=4.0):
+    """Two data volumes of the same phantom and weight with independent noise,
+    the synthetic stand-in for the gold-standard half-map split (Sec. 2.3):
+    (Volume, Volume), the second drawing its data noise from seed + 500000."""
+    v1 = make_volume(shape, blobs, radius, seed, noise_sd, field_sigma)
+    rng = np.random.default_rng(seed + 500000)
+    noise = rng.standard_normal(tuple(int(s) for s in shape))
+    b2 = v1.phantom.astype(np.float64) + noise_sd * noise / np.sqrt(v1.w.astype(np.float64))
+    v2 = Volume(b=b2.astype(np.float32), w=v1.w.copy(), phantom=v1.phantom.copy())
+    return v1, v2

@@ -162,6 +162,45 @@ def test_vol512_sampled_step():
     assert abs(st[5] - float(tau)) <= 1e-7 * st[5]
 
 
+@pytest.mark.parametrize("storage", ["delta", "prev"])
+def test_gradient_restart_matches_oracle(storage):
+    """Gradient restart (decided on the device from the fused restart test)
+    follows the oracle's restart schedule. A better-conditioned case (mu = 0.05)
+    restarts within the first 30 steps, so 2 rounds x 120 exercise it."""
+    shape = (32, 32, 32)
+    vol = synth.make_volume(shape, blobs=8, radius=10, seed=44)
+    hyper = dict(HYPER, mu=0.05)
+    x, hist, _, _ = gpu_solve(vol.b, vol.w, hyper, 2, 120, restart=True, storage=storage)
+    ref = oracle.solve(vol.b, vol.w, oracle.Params(shape, restart=True, **hyper), 2, 120)
+    err = rel_l2(x, ref.x)
+    print(f"restart {storage} rel-L2 {err:.3e}")
+    assert err <= 1e-5
+    np.testing.assert_allclose(hist[:, 4], ref.hist.reshape(-1, 4)[:, 3], rtol=1e-6)
+    plain = oracle.solve(vol.b, vol.w, oracle.Params(shape, **hyper), 2, 120)
+    gap = np.abs(plain.hist[..., 3] - ref.hist[..., 3]) / np.abs(ref.hist[..., 3])
+    assert gap.max() > 1e-4  # the restarts did change the trajectory
+
+
+def test_anchor_term_matches_oracle():
+    """Implicit-gradient term gamma |x - a|^2 (Eq. 22), folded into (b, w) on
+    the device, against the oracle's direct implementation of the term."""
+    shape = (30, 40, 50)
+    vol = synth.make_volume(shape, blobs=12, radius=7, seed=95)
+    a = (0.3 * np.random.default_rng(96).standard_normal(shape)).astype(np.float32)
+    g = 0.5
+    s = make_solver(shape)
+    s.set_data(0, vol.b, vol.w)
+    sc = s.param_scales(0)
+    np.testing.assert_allclose(sc["rms_wb"], np.sqrt(np.mean((vol.w.astype(np.float64) * vol.b) ** 2)), rtol=1e-6)
+    np.testing.assert_allclose(sc["mean_w"], vol.w.astype(np.float64).mean(), rtol=1e-6)
+    s.set_anchor(0, g, a)
+    s.solve(2, 60)
+    x = s.get_x(0).cpu().numpy()
+    s.close()
+    ref = oracle.solve(vol.b, vol.w, oracle.Params(shape, gamma=g, anchor=a.astype(np.float64), **HYPER), 2, 60)
+    assert rel_l2(x, ref.x) <= 2e-6
+
+
 def test_objective_and_reweight_match_oracle():
     shape = (21, 34, 77)
     vol = synth.make_volume(shape, blobs=20, radius=8, seed=8)

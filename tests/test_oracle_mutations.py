@@ -46,6 +46,8 @@ MUTATIONS = {
     "adjoint drops the (1 + beta) factor": ("a_cur[v] += (1.0 + beta[k]) * ybar;", "a_cur[v] += ybar;"),
     "adjoint Hessian projection with the wrong sign": ("h0 = (q0 - e0 * eq) / s;", "h0 = (q0 + e0 * eq) / s;"),
     "adjoint of w uses b - y": ("gw[v] += -tau * (y[v] - b[v]) * m[v];", "gw[v] += tau * (y[v] - b[v]) * m[v];"),
+    "restart test with the wrong sign": ("if (p->restart && restart_dot(p, x, xprev, xnext, beta[km]) > 0.0)",
+                                         "if (p->restart && restart_dot(p, x, xprev, xnext, beta[km]) < 0.0)"),
     "Lipschitz bound with |D|^2 <= 4": ("return m + 12.0 * p->lambda_tv * max_omtv / p->mu;",
                                          "return m + 4.0 * p->lambda_tv * max_omtv / p->mu;"),
 }
@@ -71,6 +73,7 @@ QUICK = [
     pins.test_4cubed_optimality_lbfgs_kkt,
     pins.test_adjoint_identity_of_one_linear_step,
     pins.test_adjoint_matches_central_differences,
+    pins.test_gradient_restart_converges_faster,
 ]
 
 
