@@ -413,14 +413,22 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=3):
     s.iterate(5)
     s.get_x(0, x_h)
     torch.cuda.synchronize()
+    phases = {"upload_validate": 0.0, "reweight_iterate_objective": 0.0, "download": 0.0}
     t0 = time.perf_counter()
     for _ in range(reps):
-        s.set_data(0, b_h, w_h)
+        ta = time.perf_counter()
+        s.set_data(0, b_h, w_h)  # synchronises (device validation)
+        tb = time.perf_counter()
         s.reweight()
         s.iterate(iters)
-        s.objective(0)
+        s.objective(0)  # synchronises
+        tc = time.perf_counter()
         s.get_x(0, x_h)
         torch.cuda.synchronize()
+        td = time.perf_counter()
+        phases["upload_validate"] += tb - ta
+        phases["reweight_iterate_objective"] += tc - tb
+        phases["download"] += td - tc
     dt = time.perf_counter() - t0
     s.close()
     del zero
@@ -428,7 +436,8 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=3):
     return {"value": nvox * iters * reps / dt / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": int(b_h.numel() * 4 + w_h.numel() * 4),
             "d2h_bytes_per_step": int(x_h.numel() * 4 + 4 * 8),
-            "step": f"upload b,w from pinned host, re-weight, {iters} fused iterations, objective, download x"}
+            "step": f"upload b,w from pinned host, re-weight, {iters} fused iterations, objective, download x",
+            "ms_per_phase": {k: 1e3 * v / reps for k, v in phases.items()}}
 
 
 def run_batch(args):

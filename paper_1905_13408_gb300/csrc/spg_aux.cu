@@ -108,22 +108,24 @@ __global__ void validate_kernel(AuxParams a, int vol, const void *b, const void 
     const int z = blockIdx.x / AUX_SEG;
     int r0, r1;
     seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
-    double mx = 0.0, mn = INFINITY;
-    double bad_w = 0, bad_b = 0;
+    // per-thread work in float32 and integers (max and min are exact in any precision)
+    float fmx = 0.f, fmn = INFINITY;
+    int bad_w = 0, bad_b = 0;
     for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
         const int x = t % V.nx, y = r0 + t / V.nx;
         const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
         const float wv = ld_data(w, bf16, i), bv = ld_data(b, bf16, i);
-        if (!(wv > 0.f) || !isfinite(wv)) bad_w += 1;
-        if (!isfinite(bv)) bad_b += 1;
-        if (isfinite(wv)) {
-            mx = fmax(mx, (double)wv);
-            mn = fmin(mn, (double)wv);
+        const bool wfin = isfinite(wv);
+        bad_w += (!(wv > 0.f) || !wfin) ? 1 : 0;
+        bad_b += isfinite(bv) ? 0 : 1;
+        if (wfin) {
+            fmx = fmaxf(fmx, wv);
+            fmn = fminf(fmn, wv);
         }
     }
-    mx = block_max(mx, scratch);
-    const double nmn = block_max(-mn, scratch);
-    double c[2] = {bad_w, bad_b};
+    double mx = block_max((double)fmx, scratch);
+    const double nmn = block_max(-(double)fmn, scratch);
+    double c[2] = {(double)bad_w, (double)bad_b};
     block_sum<2>(c, scratch);
     if (threadIdx.x == 0) {
         double *pp = a.plane_part + (long long)blockIdx.x * 4;
@@ -133,15 +135,20 @@ __global__ void validate_kernel(AuxParams a, int vol, const void *b, const void 
         pp[3] = c[1];
     }
     if (!last_block(&a.st->ticket_aux, &flag)) return;
-    if (threadIdx.x == 0) {
-        double m = 0, n = INFINITY, bw = 0, bb = 0;
-        for (int q = 0; q < V.nz * AUX_SEG; q++) {
+    {
+        double m = 0, n = INFINITY, c2[2] = {0, 0};
+        for (int q = threadIdx.x; q < V.nz * AUX_SEG; q += blockDim.x) {
             const double *pp = a.plane_part + (long long)q * 4;
             m = fmax(m, __ldcg(pp + 0));
             n = fmin(n, __ldcg(pp + 1));
-            bw += __ldcg(pp + 2);
-            bb += __ldcg(pp + 3);
+            c2[0] += __ldcg(pp + 2);
+            c2[1] += __ldcg(pp + 3);
         }
+        m = block_max(m, scratch);
+        n = -block_max(-n, scratch);
+        block_sum<2>(c2, scratch);
+        const double bw = c2[0], bb = c2[1];
+        if (threadIdx.x != 0) return;
         double *o = a.vol_out + (long long)vol * 8;
         o[0] = m;
         o[1] = n;
@@ -188,9 +195,10 @@ __global__ void anchor_kernel(AuxParams a, int vol, void *b, void *w, bool bf16,
     mx = block_max(mx, scratch);
     if (threadIdx.x == 0) a.plane_part[(long long)blockIdx.x * 4] = mx;
     if (!last_block(&a.st->ticket_aux, &flag)) return;
+    double m = 0;
+    for (int q = threadIdx.x; q < V.nz * AUX_SEG; q += blockDim.x) m = fmax(m, __ldcg(a.plane_part + (long long)q * 4));
+    m = block_max(m, scratch);
     if (threadIdx.x == 0) {
-        double m = 0;
-        for (int q = 0; q < V.nz * AUX_SEG; q++) m = fmax(m, __ldcg(a.plane_part + (long long)q * 4));
         maxw_out[vol] = m;
         a.st->ticket_aux = 0;
         __threadfence();
@@ -230,15 +238,19 @@ __global__ void scales_kernel(AuxParams a, int vol, const void *b, const void *w
         pp[3] = -nmn;
     }
     if (!last_block(&a.st->ticket_aux, &flag)) return;
+    double c2[2] = {0, 0}, m = 0, n = INFINITY;
+    for (int q = threadIdx.x; q < V.nz * AUX_SEG; q += blockDim.x) {
+        const double *pp = a.plane_part + (long long)q * 4;
+        c2[0] += __ldcg(pp + 0);
+        c2[1] += __ldcg(pp + 1);
+        m = fmax(m, __ldcg(pp + 2));
+        n = fmin(n, __ldcg(pp + 3));
+    }
+    block_sum<2>(c2, scratch);
+    m = block_max(m, scratch);
+    n = -block_max(-n, scratch);
     if (threadIdx.x == 0) {
-        double q2 = 0, qw = 0, m = 0, n = INFINITY;
-        for (int q = 0; q < V.nz * AUX_SEG; q++) {
-            const double *pp = a.plane_part + (long long)q * 4;
-            q2 += __ldcg(pp + 0);
-            qw += __ldcg(pp + 1);
-            m = fmax(m, __ldcg(pp + 2));
-            n = fmin(n, __ldcg(pp + 3));
-        }
+        const double q2 = c2[0], qw = c2[1];
         const double cnt = (double)V.nx * V.ny * V.nz;
         double *o = a.vol_out + (long long)vol * 8;
         o[0] = sqrt(q2 / cnt);
@@ -332,7 +344,7 @@ __global__ void reweight_kernel(AuxParams a, const float *xcur, float *om1, floa
     int r0, r1;
     seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
     const Field F{xcur, nullptr, 0.f};
-    double mx = 0.0;
+    float fmx = 0.f;
     KSum c1, c2;
     float nnz = 0.f;
     for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
@@ -346,12 +358,12 @@ __global__ void reweight_kernel(AuxParams a, const float *xcur, float *om1, floa
         const float ot = V.eps_tv / (gn + V.eps_tv);
         om1[i] = o1;
         omtv[i] = ot;
-        mx = fmax(mx, (double)ot);
+        fmx = fmaxf(fmx, ot);
         nnz += xv != 0.f ? 1.f : 0.f;
         c1.add(o1);
         c2.add(ot);
     }
-    mx = block_max(mx, scratch);
+    const double mx = block_max((double)fmx, scratch);
     double s[3] = {(double)nnz, c1.value(), c2.value()};
     block_sum<3>(s, scratch);
     if (threadIdx.x == 0) {
@@ -362,18 +374,20 @@ __global__ void reweight_kernel(AuxParams a, const float *xcur, float *om1, floa
         pp[3] = s[2];
     }
     if (!last_block(&a.st->ticket_aux, &flag)) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int v = warp; v < a.nvol; v += blockDim.x / 32) {
+    for (int v = 0; v < a.nvol; v++) {
         const VolDesc W = a.vols[v];
-        double m = 0, n = 0, s1 = 0, s2 = 0;
-        if (lane == 0) {
-            for (int q = W.plane_begin * AUX_SEG; q < (W.plane_begin + W.nz) * AUX_SEG; q++) {
-                const double *pp = a.plane_part + (long long)q * 4;
-                m = fmax(m, __ldcg(pp + 0));
-                n += __ldcg(pp + 1);
-                s1 += __ldcg(pp + 2);
-                s2 += __ldcg(pp + 3);
-            }
+        double m = 0, c3[3] = {0, 0, 0};
+        for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG; q += blockDim.x) {
+            const double *pp = a.plane_part + (long long)q * 4;
+            m = fmax(m, __ldcg(pp + 0));
+            c3[0] += __ldcg(pp + 1);
+            c3[1] += __ldcg(pp + 2);
+            c3[2] += __ldcg(pp + 3);
+        }
+        m = block_max(m, scratch);
+        block_sum<3>(c3, scratch);
+        const double n = c3[0], s1 = c3[1], s2 = c3[2];
+        if (threadIdx.x == 0) {
             const double L = maxw[v] + 12.0 * (double)W.lambda_tv * m / (double)W.mu;
             const double tau = 1.0 / L;
             double *o = rstats + (long long)v * 6;
@@ -417,7 +431,7 @@ __global__ void objective_kernel(AuxParams a, const float *xcur, const void *b, 
         float g[3];
         grad_at(V, F, x, y, z, g);
         const float q = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-        const float h = q <= mu * mu ? q * (0.5f / mu) : sqrtf(q) - 0.5f * mu;
+        const float h = q <= mu * mu ? q * (0.5f / mu) : q * rsqrtf(q) - 0.5f * mu;
         const float xv = xcur[i];
         const float r = xv - ld_data(b, bf16, i);
         kd.add(0.5f * ld_data(w, bf16, i) * r * r);
@@ -434,17 +448,18 @@ __global__ void objective_kernel(AuxParams a, const float *xcur, const void *b, 
         pp[3] = 0;
     }
     if (!last_block(&a.st->ticket_aux, &flag)) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int v = warp; v < a.nvol; v += blockDim.x / 32) {
-        if (lane != 0) continue;
+    for (int v = 0; v < a.nvol; v++) {
         const VolDesc W = a.vols[v];
-        double d = 0, l = 0, t = 0;
-        for (int q = W.plane_begin * AUX_SEG; q < (W.plane_begin + W.nz) * AUX_SEG; q++) {
+        double c3[3] = {0, 0, 0};
+        for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG; q += blockDim.x) {
             const double *pp = a.plane_part + (long long)q * 4;
-            d += __ldcg(pp + 0);
-            l += __ldcg(pp + 1);
-            t += __ldcg(pp + 2);
+            c3[0] += __ldcg(pp + 0);
+            c3[1] += __ldcg(pp + 1);
+            c3[2] += __ldcg(pp + 2);
         }
+        block_sum<3>(c3, scratch);
+        if (threadIdx.x != 0) continue;
+        const double d = c3[0], l = c3[1], t = c3[2];
         double *o = a.vol_out + (long long)v * 8;
         o[0] = d;
         o[1] = (double)W.lambda_l1 * l;
@@ -491,13 +506,13 @@ __global__ void certificate_kernel(AuxParams a, const float *xplus, const float 
     block_sum<1>(s, scratch);
     if (threadIdx.x == 0) a.plane_part[(long long)blockIdx.x * 4] = s[0];
     if (!last_block(&a.st->ticket_aux, &flag)) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int v = warp; v < a.nvol; v += blockDim.x / 32) {
-        if (lane != 0) continue;
+    for (int v = 0; v < a.nvol; v++) {
         const VolDesc W = a.vols[v];
-        double acc = 0;
-        for (int q = W.plane_begin * AUX_SEG; q < (W.plane_begin + W.nz) * AUX_SEG; q++) acc += __ldcg(a.plane_part + (long long)q * 4);
-        a.vol_out[(long long)v * 8 + 4] = acc;
+        double acc[1] = {0};
+        for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG; q += blockDim.x)
+            acc[0] += __ldcg(a.plane_part + (long long)q * 4);
+        block_sum<1>(acc, scratch);
+        if (threadIdx.x == 0) a.vol_out[(long long)v * 8 + 4] = acc[0];
     }
     __syncthreads();
     if (threadIdx.x == 0) {

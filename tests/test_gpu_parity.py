@@ -460,3 +460,45 @@ def test_autotune_keeps_the_solve():
     s.close()
     ref = oracle.solve(vol.b, vol.w, oparams(shape), 1, 20)
     assert rel_l2(x, ref.x) <= 1e-6
+
+
+def test_beyond_int32_voxel_count():
+    """1300^3 = 2.2e9 voxels (more than 2^31; about 90 GB on the device): two
+    iterations, then the second step is checked at sampled voxels (faces,
+    edges, corners, interior) against the oracle run on each voxel's clipped
+    3x3x3 neighbourhood, which holds every input of that voxel's update
+    (Eq. 12, 16, 17 reach one voxel in each direction)."""
+    n = 1300
+    shape = (n, n, n)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    b = torch.rand(shape, device="cuda", generator=g) - 0.3
+    w = torch.rand(shape, device="cuda", generator=g) + 0.5
+    hyper = dict(HYPER, mu=0.05)
+    s = make_solver(shape, hyper)
+    s.set_data(0, b, w)
+    s.reweight()
+    s.iterate(1)
+    x1 = s.get_x(0)  # x_0 = 0, so d_1 = x_1 and x_{k-1} of the second step is 0
+    st = s.round_stats(0)
+    s.iterate(1)
+    x2 = s.get_x(0)
+    s.close()
+    tau = np.float32(st[5])
+    beta = float(np.float32(oracle.beta_table(2)[1]))
+    rng = np.random.default_rng(8)
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 5), (n - 1, 0, n // 2), (n // 2, n // 2, 0)]
+    pts += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(40)]
+    for (z, y, x) in pts:
+        z0, z1 = max(z - 1, 0), min(z + 2, n)
+        y0, y1 = max(y - 1, 0), min(y + 2, n)
+        x0, x1_ = max(x - 1, 0), min(x + 2, n)
+        sl = (slice(z0, z1), slice(y0, y1), slice(x0, x1_))
+        cube = [t[sl].double().cpu().numpy() for t in (x1, b, w)]
+        xk, bb, ww = cube
+        xkm1 = np.zeros_like(xk)  # x_0 = 0
+        p = oracle.Params(xk.shape, **hyper)
+        # round-1 weights are 1 (x_0 = 0)
+        idx = np.ravel_multi_index((z - z0, y - y0, x - x0), xk.shape)
+        want = oracle.step_sampled(xk, xkm1, beta, float(tau), bb, ww, None, None, p, np.array([idx]))[0]
+        got = float(x2[z, y, x])
+        assert abs(got - want) <= 2e-6 * max(1.0, abs(want)), (z, y, x, got, want)
