@@ -130,6 +130,21 @@ spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg
  * otherwise. Synchronises (it reduces max w in double precision). */
 spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg_dtype src_dtype);
 
+/* Fourier-domain data term (Sec. 2.5, Eq. 31): replace the data term of a
+ * single-volume context by 1/2 |y - D A x|^2, A the unitary 3-D DFT
+ * (A x = FFT(x) / sqrt(nx ny nz)) and D = diag sqrt(N). y_half (complex64,
+ * interleaved re/im) and N_half (float32, N >= 0) hold the real-to-complex
+ * half spectrum [nz][ny][nx/2+1] of a Hermitian y and a centro-symmetric N;
+ * host or device pointers, copied. Each iteration then forms the extrapolated
+ * point, transforms it (cuFFT, loaded at run time), scales the spectrum by
+ * N and transforms back to get A^H N A y - A^H D y for the fused step;
+ * L = max N + 12 lambda_tv max(omtv) / mu. Needs SPG_F32 data storage and
+ * SPG_STORE_DELTA; certificate, adjoint and anchor are not available in this
+ * mode. The objective history records the l1 and TV terms only (its data
+ * column is 0); spg_objective returns all terms. spg_set_data switches back
+ * to the real-space data term. Synchronises. */
+spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const float *N_half);
+
 /* Proximal anchor of the implicit-gradient term (Sec. 2.1 Eq. 22, Eq. 31):
  * adds gamma |x - x_anchor|^2 to the data term of volume `vol`. Because
  *   1/2 w (x - b)^2 + gamma (x - a)^2 = 1/2 w' (x - b')^2 + const,

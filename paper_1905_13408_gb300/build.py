@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libspg.so")
 SOURCES = ["spg_step_f32.cu", "spg_step_bf16.cu", "spg_step.cu", "spg_aux.cu", "spg_api.cu", "spg_noalloc.cu",
-           "spg_fsc.cu"]
+           "spg_fsc.cu", "spg_cufft.cu", "spg_fourier.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -43,6 +43,7 @@ def _stale():
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, s) for s in SOURCES]
     deps += [os.path.join(CSRC, "spg_internal.h"), os.path.join(CSRC, "spg_step_kernel.cuh"),
+             os.path.join(CSRC, "spg_cufft.h"),
              os.path.join(INCLUDE, "spg.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps)
 

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "spg.h"
+#include "spg_cufft.h"
 #include "spg_internal.h"
 
 using namespace spg;
@@ -84,6 +85,18 @@ struct spg_ctx {
     std::vector<char> data_set;
     int hist_every = 1, hist_cap = 4096, max_iters = 100000;
 
+    // Fourier-domain data term (single volume)
+    bool fourier = false;
+    float *Ybuf = nullptr;   // extrapolated point y_k (pitched)
+    float2 *Fh = nullptr;    // spectrum scratch
+    float2 *Yh = nullptr;    // data spectrum y
+    float *Nh = nullptr;     // weights N
+    float *Nmax = nullptr;
+    double *fpart = nullptr; // reduction partials of the Fourier data value
+    cufftHandle pr2c = 0, pc2r = 0;
+    bool plans = false;
+    long long nhalf = 0;
+
     cudaGraphExec_t gexec = nullptr;
     long long launches = 0;
     std::string err = "no error";
@@ -131,6 +144,13 @@ cudaError_t dalloc(T **p, size_t bytes)
 void free_all(spg_ctx *c)
 {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->plans) {
+        spg::cufft_api().destroy(c->pr2c);
+        spg::cufft_api().destroy(c->pc2r);
+    }
+    void *fs[] = {c->Ybuf, c->Fh, c->Yh, c->Nh, c->Nmax, c->fpart};
+    for (void *p : fs)
+        if (p) cudaFree(p);
     void *ps[] = {c->vols_d, c->items_d, c->tmaps_d, c->plane_vol_d, c->X[0], c->X[1], c->X[2], c->X[3], c->B, c->W,
                   c->OM1, c->OMTV, c->beta_d, c->st_d, c->partials_d, c->hist_d, c->plane_part_d,
                   c->vol_out_d, c->maxw_d, c->rstats_d};
@@ -314,6 +334,7 @@ StepParams step_params(const spg_ctx *c)
     p.hist_cap = c->hist_cap;
     p.hist_every = c->hist_every;
     p.restart = c->opt.restart ? 1 : 0;
+    p.fourier = c->fourier ? 1 : 0;
     p.timeout_ns = kTimeoutNs;
     return p;
 }
@@ -374,20 +395,46 @@ spg_status copy_volume_out(spg_ctx *ctx, void *dst, const void *src_base, size_t
     return SPG_OK;
 }
 
+// One iteration: the fused step, preceded for the Fourier-domain data term by
+// y_k, its spectrum, the N scaling and the inverse transform into b (= G).
+cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
+{
+    if (ctx->fourier) {
+        const VolDesc &d = ctx->vols_h[0];
+        const double V = (double)d.nx * d.ny * d.nz;
+        cudaError_t e = launch_form_y(ctx->st_d, ctx->vols_d, ctx->beta_d, ctx->X, ctx->Ybuf, ctx->total, ctx->stream);
+        if (e != cudaSuccess) return e;
+        const spg::CufftApi &cf = spg::cufft_api();
+        if (cf.exec_r2c(ctx->pr2c, ctx->Ybuf, reinterpret_cast<cufftComplex *>(ctx->Fh)) != CUFFT_SUCCESS)
+            return cudaErrorUnknown;
+        e = launch_spec_scale(ctx->Fh, ctx->Nh, ctx->nhalf, (float)(1.0 / V), ctx->stream);
+        if (e != cudaSuccess) return e;
+        if (cf.exec_c2r(ctx->pc2r, reinterpret_cast<cufftComplex *>(ctx->Fh), static_cast<float *>(ctx->B)) !=
+            CUFFT_SUCCESS)
+            return cudaErrorUnknown;
+        ctx->launches += 2;
+    }
+    return step_launch(ctx->var, ctx->grid, p, ctx->stream);
+}
+
 spg_status launch_steps(spg_ctx *ctx, int k)
 {
     const StepParams p = step_params(ctx);
+    const long long per_iter = ctx->fourier ? 3 : 1;  // kernels of this library per iteration
     if (k >= kGraphLen && !ctx->gexec) {
+        const long long counted = ctx->launches;  // capturing launches nothing
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         for (int i = 0; i < kGraphLen; i++) {
-            cudaError_t e = step_launch(ctx->var, ctx->grid, p, ctx->stream);
+            cudaError_t e = issue_iteration(ctx, p);
             if (e != cudaSuccess) {
                 cudaStreamEndCapture(ctx->stream, &g);
                 if (g) cudaGraphDestroy(g);
+                ctx->launches = counted;
                 return cuda_fail(ctx, e, "capture fused step");
             }
         }
+        ctx->launches = counted;
         CK(cudaStreamEndCapture(ctx->stream, &g), "end capture");
         cudaError_t e = cudaGraphInstantiate(&ctx->gexec, g, 0);
         cudaGraphDestroy(g);
@@ -395,12 +442,13 @@ spg_status launch_steps(spg_ctx *ctx, int k)
     }
     while (k >= kGraphLen && ctx->gexec) {
         CK(cudaGraphLaunch(ctx->gexec, ctx->stream), "graph launch");
-        ctx->launches += kGraphLen;
+        ctx->launches += kGraphLen * per_iter;
         k -= kGraphLen;
     }
     for (int i = 0; i < k; i++) {
-        CK(step_launch(ctx->var, ctx->grid, p, ctx->stream), "fused step launch");
-        ctx->launches += 1;
+        const long long counted = ctx->launches;
+        CK(issue_iteration(ctx, p), "fused step launch");
+        ctx->launches = counted + per_iter;
     }
     return SPG_OK;
 }
@@ -602,6 +650,13 @@ spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !b || !w) return fail(ctx, SPG_EINVAL, "spg_set_data: bad arguments");
     if (src != SPG_F32 && src != SPG_BF16) return fail(ctx, SPG_EINVAL, "spg_set_data: bad dtype");
+    if (ctx->fourier) {
+        ctx->fourier = false;  // back to the real-space data term
+        if (ctx->gexec) {
+            cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+        }
+    }
     const VolDesc &d = ctx->vols_h[vol];
     const long long n = (long long)d.pitch * d.ny * d.nz;
     const bool store_bf16 = ctx->bf16();
@@ -642,12 +697,79 @@ spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg
     return SPG_OK;
 }
 
+spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const float *N_half)
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol != 0 || ctx->nvol != 1 || !y_half || !N_half)
+        return fail(ctx, SPG_EINVAL, "spg_set_data_fourier: single-volume contexts, vol = 0, non-null arrays");
+    if (ctx->bf16() || !ctx->xd())
+        return fail(ctx, SPG_EINVAL, "spg_set_data_fourier: needs SPG_F32 storage and SPG_STORE_DELTA");
+    const spg::CufftApi &cf = spg::cufft_api();
+    if (!cf.ok) return fail(ctx, SPG_ECUDA, "spg_set_data_fourier: cuFFT library could not be loaded");
+    const VolDesc &d = ctx->vols_h[0];
+    const int nxh = d.nx / 2 + 1;
+    ctx->nhalf = (long long)d.nz * d.ny * nxh;
+    if (!ctx->Ybuf) {
+        CK(dalloc(&ctx->Ybuf, (size_t)ctx->total * sizeof(float)), "alloc");
+        CK(dalloc(&ctx->Fh, (size_t)ctx->nhalf * sizeof(float2)), "alloc");
+        CK(dalloc(&ctx->Yh, (size_t)ctx->nhalf * sizeof(float2)), "alloc");
+        CK(dalloc(&ctx->Nh, (size_t)ctx->nhalf * sizeof(float)), "alloc");
+        CK(dalloc(&ctx->Nmax, sizeof(float)), "alloc");
+        CK(dalloc(&ctx->fpart, 1025 * sizeof(double)), "alloc");
+        CK(cudaMemsetAsync(ctx->Ybuf, 0, (size_t)ctx->total * sizeof(float), ctx->stream), "memset");
+    }
+    if (!ctx->plans) {
+        int n[3] = {d.nz, d.ny, d.nx};
+        int real_embed[3] = {d.nz, d.ny, d.pitch};
+        int cplx_embed[3] = {d.nz, d.ny, nxh};
+        const int rdist = d.nz * d.ny * d.pitch, cdist = (int)ctx->nhalf;
+        if (cf.plan_many(&ctx->pr2c, 3, n, real_embed, 1, rdist, cplx_embed, 1, cdist, CUFFT_R2C, 1) != CUFFT_SUCCESS)
+            return fail(ctx, SPG_ECUDA, "spg_set_data_fourier: cufft plan");
+        if (cf.plan_many(&ctx->pc2r, 3, n, cplx_embed, 1, cdist, real_embed, 1, rdist, CUFFT_C2R, 1) != CUFFT_SUCCESS) {
+            cf.destroy(ctx->pr2c);
+            return fail(ctx, SPG_ECUDA, "spg_set_data_fourier: cufft plan");
+        }
+        cf.set_stream(ctx->pr2c, ctx->stream);
+        cf.set_stream(ctx->pc2r, ctx->stream);
+        ctx->plans = true;
+    }
+    CK(cudaMemcpyAsync(ctx->Yh, y_half, (size_t)ctx->nhalf * sizeof(float2), cudaMemcpyDefault, ctx->stream),
+       "copy y");
+    CK(cudaMemcpyAsync(ctx->Nh, N_half, (size_t)ctx->nhalf * sizeof(float), cudaMemcpyDefault, ctx->stream),
+       "copy N");
+    // c = A^H D y = IFFT(sqrt(N) y) / sqrt(V) into the w buffer; G (b buffer) starts at 0
+    const double V = (double)d.nx * d.ny * d.nz;
+    CK(launch_spec_prep(ctx->Fh, ctx->Yh, ctx->Nh, ctx->nhalf, (float)(1.0 / std::sqrt(V)), ctx->stream), "prep");
+    if (cf.exec_c2r(ctx->pc2r, reinterpret_cast<cufftComplex *>(ctx->Fh), static_cast<float *>(ctx->W)) !=
+        CUFFT_SUCCESS)
+        return fail(ctx, SPG_ECUDA, "spg_set_data_fourier: inverse transform");
+    CK(cudaMemsetAsync(ctx->B, 0, (size_t)ctx->total * sizeof(float), ctx->stream), "memset");
+    CK(launch_spec_max(ctx->Nh, ctx->nhalf, ctx->Nmax, ctx->stream), "max N");
+    ctx->launches += 2;
+    float nmax = 0.f;
+    CK(cudaMemcpyAsync(&nmax, ctx->Nmax, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream), "read max N");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    if (!(nmax >= 0.f) || !std::isfinite(nmax)) return fail(ctx, SPG_EINVAL, "spg_set_data_fourier: bad N");
+    const double m = nmax;
+    CK(cudaMemcpyAsync(ctx->maxw_d, &m, sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "write max N");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);  // the iteration body changes
+        ctx->gexec = nullptr;
+    }
+    ctx->fourier = true;
+    ctx->data_set[0] = 1;
+    ctx->reweighted = false;
+    return SPG_OK;
+}
+
 spg_status spg_set_anchor(spg_ctx *ctx, int vol, float gamma, const float *x_anchor)
 {
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !x_anchor || !(gamma >= 0.f) || !std::isfinite(gamma))
         return fail(ctx, SPG_EINVAL, "spg_set_anchor: bad arguments");
     if (!ctx->data_set[vol]) return fail(ctx, SPG_ENOTREADY, "spg_set_anchor: call spg_set_data first");
+    if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_set_anchor: not available with the Fourier-domain data term");
     const VolDesc &d = ctx->vols_h[vol];
     // stage the anchor in the l1-weight buffer (re-set by the next spg_reweight)
     spg_status s = copy_volume_in(ctx, ctx->OM1, 4, d, x_anchor);
@@ -742,12 +864,33 @@ spg_status spg_objective(spg_ctx *ctx, int vol, double out[4])
     if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_objective: bad arguments");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_objective: weights not set (call spg_reweight)");
     const float *xb[1] = {ctx->X[ctx->cur()]};
-    CK(launch_objective(aux_params(ctx), xb, ctx->B, ctx->W, ctx->bf16(), ctx->OM1, ctx->OMTV, ctx->stream),
+    CK(launch_objective(aux_params(ctx), xb, ctx->fourier ? nullptr : ctx->B, ctx->fourier ? nullptr : ctx->W,
+                        ctx->bf16(), ctx->OM1, ctx->OMTV, ctx->stream),
        "objective");
     ctx->launches += 1;
     double o[8];
     CK(cudaMemcpyAsync(o, ctx->vol_out_d + (size_t)vol * 8, sizeof(o), cudaMemcpyDeviceToHost, ctx->stream),
        "read objective");
+    if (ctx->fourier) {
+        // data term 1/2 |y - D A x|^2 from the spectrum of x
+        const VolDesc &d = ctx->vols_h[0];
+        const double V = (double)d.nx * d.ny * d.nz;
+        CK(cudaMemcpyAsync(ctx->Ybuf, ctx->X[ctx->cur()], (size_t)ctx->total * sizeof(float), cudaMemcpyDeviceToDevice,
+                           ctx->stream),
+           "copy x");
+        if (spg::cufft_api().exec_r2c(ctx->pr2c, ctx->Ybuf, reinterpret_cast<cufftComplex *>(ctx->Fh)) !=
+            CUFFT_SUCCESS)
+            return fail(ctx, SPG_ECUDA, "spg_objective: transform");
+        CK(launch_spec_data_value(ctx->Fh, ctx->Yh, ctx->Nh, d.nz, d.ny, d.nx, (float)(1.0 / std::sqrt(V)),
+                                  ctx->fpart, ctx->fpart + 1024, ctx->stream),
+           "data value");
+        ctx->launches += 2;
+        double dv = 0;
+        CK(cudaMemcpyAsync(&dv, ctx->fpart + 1024, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "read");
+        CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+        o[0] = dv;
+        o[3] = o[0] + o[1] + o[2];
+    }
     spg_status s = device_status(ctx);
     if (s != SPG_OK) return s;
     for (int q = 0; q < 4; q++) out[q] = o[q];
@@ -794,6 +937,7 @@ spg_status spg_certificate(spg_ctx *ctx, int vol, double *out)
     if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_certificate: bad arguments");
     if (!ctx->reweighted || ctx->k_round < 1)
         return fail(ctx, SPG_ENOTREADY, "spg_certificate: needs one iteration in the current round");
+    if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_certificate: not available with the Fourier-domain data term");
     const int c = ctx->cur();
     // x_{k+1} = X[c]; x_k and its pair are one rotation back
     const int k = (c + ctx->nbuf() - 1) % ctx->nbuf();
@@ -936,6 +1080,7 @@ spg_status spg_unrolled(spg_ctx *ctx, int K, float *xK)
 {
     if (!ctx || !xK || K < 0) return fail(ctx, SPG_EINVAL, "spg_unrolled: bad arguments");
     if (ctx->nvol != 1) return fail(ctx, SPG_EINVAL, "spg_unrolled: single-volume contexts only");
+    if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_unrolled: not available with the Fourier-domain data term");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_unrolled: call spg_reweight first");
     const VolDesc &d = ctx->vols_h[0];
     const size_t vb = (size_t)ctx->total * 4;
@@ -963,6 +1108,7 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
 {
     if (!ctx || !gx || !gb || !gw || !g_scalars || K < 1) return fail(ctx, SPG_EINVAL, "spg_backward: bad arguments");
     if (ctx->nvol != 1) return fail(ctx, SPG_EINVAL, "spg_backward: single-volume contexts only");
+    if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_backward: not available with the Fourier-domain data term");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_backward: call spg_reweight first");
     const int C = ckpt_every > 0 ? ckpt_every : 10;
     const VolDesc &d = ctx->vols_h[0];

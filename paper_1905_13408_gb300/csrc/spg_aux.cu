@@ -433,8 +433,10 @@ __global__ void objective_kernel(AuxParams a, const float *xcur, const void *b, 
         const float q = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
         const float h = q <= mu * mu ? q * (0.5f / mu) : q * rsqrtf(q) - 0.5f * mu;
         const float xv = xcur[i];
-        const float r = xv - ld_data(b, bf16, i);
-        kd.add(0.5f * ld_data(w, bf16, i) * r * r);
+        if (w) {  // no real-space data term when the Fourier-domain term is in use
+            const float r = xv - ld_data(b, bf16, i);
+            kd.add(0.5f * ld_data(w, bf16, i) * r * r);
+        }
         kl.add(om1[i] * fabsf(xv));
         kt.add(omtv[i] * h);
     }

@@ -1,0 +1,132 @@
+// Kernels of the Fourier-domain data term (Sec. 2.5, Eq. 31):
+//   1/2 |y - D A x|^2, A the unitary DFT, D = diag sqrt(N),
+// whose gradient A^H N A x - A^H D y is formed each iteration at the
+// extrapolated point y_k by a real-to-complex transform, a spectrum scaling
+// and a complex-to-real transform (cuFFT), then consumed by the fused step.
+// Spectra use the real-to-complex half layout [nz][ny][nx/2+1].
+#include "spg_internal.h"
+
+namespace spg {
+namespace {
+
+// y_k = x_k + beta d_k, with x_k = X[cur], d_k = X[2 + cur] (increment storage).
+__global__ void form_y_kernel(const DevState *st, const VolDesc *vols, const float *beta, float *x0, float *x1,
+                              float *d0, float *d1, float *y, long long n)
+{
+    const int cur = st->cur;
+    const float b = beta[vols[0].kmom];
+    const float *x = cur == 0 ? x0 : x1;
+    const float *d = cur == 0 ? d0 : d1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = fmaf(b, d[i], x[i]);
+}
+
+__global__ void spec_scale_kernel(float2 *F, const float *N, long long n, float scale)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float m = N[i] * scale;
+        float2 f = F[i];
+        f.x *= m;
+        f.y *= m;
+        F[i] = f;
+    }
+}
+
+__global__ void spec_prep_kernel(float2 *F, const float2 *Y, const float *N, long long n, float scale)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float m = sqrtf(N[i]) * scale;
+        const float2 y = Y[i];
+        F[i] = make_float2(y.x * m, y.y * m);
+    }
+}
+
+__global__ void spec_max_kernel(const float *N, long long n, unsigned int *out)
+{
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, N[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    // non-negative floats order like their bit patterns
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// Half-spectrum sum of 1/2 |Y - sqrt(N) F scale|^2, coefficients 0 < h < nx/2 counted twice.
+__global__ void spec_value_kernel(const float2 *F, const float2 *Y, const float *N, int nz, int ny, int nx,
+                                  float scale, double *partials)
+{
+    __shared__ double red[32];
+    const int nxh = nx / 2 + 1;
+    const long long n = (long long)nz * ny * nxh;
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int h = (int)(i % nxh);
+        const double wgt = (h == 0 || (nx % 2 == 0 && h == nx / 2)) ? 1.0 : 2.0;
+        const double m = sqrt((double)N[i]) * scale;
+        const double rx = (double)Y[i].x - m * F[i].x, ry = (double)Y[i].y - m * F[i].y;
+        acc += wgt * 0.5 * (rx * rx + ry * ry);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); w++) s += red[w];
+        partials[blockIdx.x] = s;
+    }
+}
+
+__global__ void sum_partials_kernel(const double *partials, int n, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; i++) s += partials[i];
+        *out = s;
+    }
+}
+
+int grid_for(long long n)
+{
+    long long g = (n + 255) / 256;
+    return (int)(g < 4864 ? (g > 0 ? g : 1) : 4864);
+}
+
+}  // namespace
+
+cudaError_t launch_form_y(const DevState *st, const VolDesc *vols, const float *beta, float *const *xbuf, float *y,
+                          long long n, cudaStream_t s)
+{
+    form_y_kernel<<<grid_for(n), 256, 0, s>>>(st, vols, beta, xbuf[0], xbuf[1], xbuf[2], xbuf[3], y, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_scale(float2 *F, const float *N, long long n, float scale, cudaStream_t s)
+{
+    spec_scale_kernel<<<grid_for(n), 256, 0, s>>>(F, N, n, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_prep(float2 *F, const float2 *Y, const float *N, long long n, float scale, cudaStream_t s)
+{
+    spec_prep_kernel<<<grid_for(n), 256, 0, s>>>(F, Y, N, n, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_max(const float *N, long long n, float *out, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    spec_max_kernel<<<grid_for(n), 256, 0, s>>>(N, n, reinterpret_cast<unsigned int *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_data_value(const float2 *F, const float2 *Y, const float *N, int nz, int ny, int nx,
+                                   float scale, double *partials, double *out, cudaStream_t s)
+{
+    const int g = 1024;
+    spec_value_kernel<<<g, 256, 0, s>>>(F, Y, N, nz, ny, nx, scale, partials);
+    sum_partials_kernel<<<1, 32, 0, s>>>(partials, g, out);
+    return cudaGetLastError();
+}
+
+}  // namespace spg

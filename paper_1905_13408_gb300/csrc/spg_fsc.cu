@@ -5,14 +5,13 @@
 // 0 < h < n/2 stand for themselves and their conjugates (weight 2).
 #include <cuda_runtime.h>
 #include <cufft.h>
-#include <dlfcn.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 #include <vector>
 
 #include "spg.h"
+#include "spg_cufft.h"
 
 namespace {
 
@@ -98,41 +97,12 @@ struct Buf {
     }
 };
 
-// cuFFT is resolved at the first call, so the solver library itself does not
-// depend on it being loadable.
-struct Cufft {
-    cufftResult (*plan3d)(cufftHandle *, int, int, int, cufftType) = nullptr;
-    cufftResult (*set_stream)(cufftHandle, cudaStream_t) = nullptr;
-    cufftResult (*exec_r2c)(cufftHandle, cufftReal *, cufftComplex *) = nullptr;
-    cufftResult (*destroy)(cufftHandle) = nullptr;
-    bool ok = false;
-};
-
-const Cufft &cufft()
-{
-    static Cufft c;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        const char *names[] = {"libcufft.so.12", "libcufft.so", "/usr/local/cuda/lib64/libcufft.so.12"};
-        void *h = nullptr;
-        for (const char *n : names)
-            if ((h = dlopen(n, RTLD_NOW | RTLD_LOCAL))) break;
-        if (!h) return;
-        c.plan3d = reinterpret_cast<decltype(c.plan3d)>(dlsym(h, "cufftPlan3d"));
-        c.set_stream = reinterpret_cast<decltype(c.set_stream)>(dlsym(h, "cufftSetStream"));
-        c.exec_r2c = reinterpret_cast<decltype(c.exec_r2c)>(dlsym(h, "cufftExecR2C"));
-        c.destroy = reinterpret_cast<decltype(c.destroy)>(dlsym(h, "cufftDestroy"));
-        c.ok = c.plan3d && c.set_stream && c.exec_r2c && c.destroy;
-    });
-    return c;
-}
-
 struct Plan {
     cufftHandle h = 0;
     bool made = false;
     ~Plan()
     {
-        if (made) cufft().destroy(h);
+        if (made) spg::cufft_api().destroy(h);
     }
 };
 
@@ -178,7 +148,7 @@ extern "C" spg_status spg_fsc(int n, const float *a, const float *b, int max_she
     FSC_CK(cudaMemcpyAsync(rb.p, b, vox * sizeof(float), cudaMemcpyDefault, s));
     const size_t smem = (size_t)nshell * 3 * sizeof(double);
     if (smem > 48 * 1024) return fsc_fail(SPG_EINVAL, "spg_fsc: too many shells (n <= 2046)");
-    const Cufft &cf = cufft();
+    const spg::CufftApi &cf = spg::cufft_api();
     if (!cf.ok) return fsc_fail(SPG_ECUDA, "spg_fsc: cuFFT library could not be loaded");
     Plan plan;
     if (cf.plan3d(&plan.h, n, n, n, CUFFT_R2C) != CUFFT_SUCCESS) return fsc_fail(SPG_ECUDA, "spg_fsc: cufft plan");

@@ -73,6 +73,7 @@ struct StepParams {
     double *hist;            // ring [hist_cap][nvol][5]
     int nitems, nvol, hist_cap, hist_every;
     int restart;             // gradient restart of the extrapolation, per volume
+    int fourier;             // data gradient = b - w (G - c of the Fourier-domain term), single volume
     long long timeout_ns;    // bound on any single barrier wait
 };
 
@@ -135,6 +136,22 @@ cudaError_t launch_plain_step(const VolDesc *vols, int nplanes, const float *xk,
                               float beta, const void *b, const void *w, bool bf16, const float *om1,
                               const float *omtv, float *xout, cudaStream_t s);
 cudaError_t launch_timeout_probe(DevState *st, long long timeout_ns, cudaStream_t s);
+// Fourier-domain data term (spg_fourier.cu), single float32 volume with increment storage.
+// y = x_k + beta d_k over the whole pitched volume (cur and beta read on the device).
+cudaError_t launch_form_y(const DevState *st, const VolDesc *vols, const float *beta, float *const *xbuf,
+                          float *y, long long n, cudaStream_t s);
+// F *= N * scale over n half-spectrum coefficients.
+cudaError_t launch_spec_scale(float2 *F, const float *N, long long n, float scale, cudaStream_t s);
+// F = Y * sqrt(N) * scale.
+cudaError_t launch_spec_prep(float2 *F, const float2 *Y, const float *N, long long n, float scale,
+                             cudaStream_t s);
+// max of n non-negative floats into *out (device float, initialised here).
+cudaError_t launch_spec_max(const float *N, long long n, float *out, cudaStream_t s);
+// out = 1/2 sum_full |Y - sqrt(N) F scale|^2 over the half spectrum (nz, ny, nxh; nx for the weights);
+// partials: at least 1024 doubles.
+cudaError_t launch_spec_data_value(const float2 *F, const float2 *Y, const float *N, int nz, int ny, int nx,
+                                   float scale, double *partials, double *out, cudaStream_t s);
+
 // Fold gamma |x - a|^2 into (b, w) of volume `vol` (a: float32 volume in the pitched layout).
 cudaError_t launch_anchor(const AuxParams &a, int vol, int nz, void *b, void *w, bool bf16, const float *anchor,
                           float gamma, double *maxw_out, cudaStream_t s);

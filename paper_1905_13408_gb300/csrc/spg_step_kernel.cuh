@@ -250,7 +250,7 @@ struct Pipe {
 // One work item: plane-by-plane march over [z0, z1) of one x-y tile.
 // REC adds the three sums of F(x_k) (data, l1, TV) for the item.
 // Returns true when a barrier wait gave up (the CTA then stops).
-template <int VX, int TY, int S, bool BF16, bool XD, bool REC, bool DOT>
+template <int VX, int TY, int S, bool BF16, bool XD, bool REC, bool DOT, bool FOURIER>
 __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pipe &pp_, const WorkItem &W, int it,
                                          int ia, int ib, float *xout_base, float *dout_base)
 {
@@ -422,7 +422,10 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
                 const float pxr = (i < VX - 1) ? pp[0][(i + 1) % VX] : pxn;
                 const float div = (pp[0][i] - pxr) + (pp[1][i] - pyd[i]) + (pp[2][i] - pc[2][i]);
                 const float res = xz[i] - bb[i];
-                const float g = fmaf(lam_tv, div, ww[i] * fmaf(beta, dz[i], res));
+                // data gradient: w (y - b) (Eq. 28 form) or, for the Fourier-domain term of
+                // Eq. 31, G - c with G = A^H N A y in the b tile and c = A^H D y in the w tile
+                const float gdat = FOURIER ? bb[i] - ww[i] : ww[i] * fmaf(beta, dz[i], res);
+                const float g = fmaf(lam_tv, div, gdat);
                 const float delta = fmaf(beta, dz[i], -tau * g);
                 const float zz = xz[i] + delta;
                 const float t = tl1 * oo[i];
@@ -430,7 +433,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
                 out[i] = xz[i] + inc[i];
                 if constexpr (DOT) rsum = fmaf(fmaf(beta, dz[i], -inc[i]), inc[i], rsum);  // (y - x+).(x+ - x)
                 if constexpr (REC) {
-                    dsum = fmaf(0.5f * ww[i] * res, res, dsum);
+                    if constexpr (!FOURIER) dsum = fmaf(0.5f * ww[i] * res, res, dsum);
                     lsum = fmaf(oo[i], fabsf(xz[i]), lsum);
                 }
             }
@@ -529,13 +532,29 @@ __global__ void __launch_bounds__(32 * (TY + 1), MINB)
     bool aborted = false;
     for (int it = blockIdx.x; it < P.nitems && !aborted; it += gridDim.x) {
         const WorkItem W = P.items[it];
-        if (P.restart)
-            aborted = rec ? run_item<VX, TY, S, BF16, XD, true, true>(P, sh, pipe, W, it, ia, ib, xout_base, dout_base)
-                          : run_item<VX, TY, S, BF16, XD, false, true>(P, sh, pipe, W, it, ia, ib, xout_base, dout_base);
-        else
-            aborted = rec ? run_item<VX, TY, S, BF16, XD, true, false>(P, sh, pipe, W, it, ia, ib, xout_base, dout_base)
-                          : run_item<VX, TY, S, BF16, XD, false, false>(P, sh, pipe, W, it, ia, ib, xout_base,
-                                                                        dout_base);
+        bool done = false;
+        if constexpr (!BF16 && XD) {
+            // Fourier-domain data term (float32 storage, increment storage only)
+            if (P.fourier) {
+                aborted = rec ? run_item<VX, TY, S, BF16, XD, true, false, true>(P, sh, pipe, W, it, ia, ib,
+                                                                                 xout_base, dout_base)
+                              : run_item<VX, TY, S, BF16, XD, false, false, true>(P, sh, pipe, W, it, ia, ib,
+                                                                                  xout_base, dout_base);
+                done = true;
+            }
+        }
+        if (!done) {
+            if (P.restart)
+                aborted = rec ? run_item<VX, TY, S, BF16, XD, true, true, false>(P, sh, pipe, W, it, ia, ib,
+                                                                                 xout_base, dout_base)
+                              : run_item<VX, TY, S, BF16, XD, false, true, false>(P, sh, pipe, W, it, ia, ib,
+                                                                                  xout_base, dout_base);
+            else
+                aborted = rec ? run_item<VX, TY, S, BF16, XD, true, false, false>(P, sh, pipe, W, it, ia, ib,
+                                                                                  xout_base, dout_base)
+                              : run_item<VX, TY, S, BF16, XD, false, false, false>(P, sh, pipe, W, it, ia, ib,
+                                                                                   xout_base, dout_base);
+        }
     }
 
     if (aborted && warp == TY && lane == 0) {

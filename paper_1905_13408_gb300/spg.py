@@ -37,7 +37,7 @@ EXPORTS = ["spg_create", "spg_create_batch", "spg_set_data", "spg_set_x", "spg_g
            "spg_get_state", "spg_set_state", "spg_backward", "spg_unrolled", "spg_probe_timeout",
            "spg_autotune", "spg_launch_count", "spg_plan_info", "spg_last_error", "spg_destroy",
            "spg_objective_noalloc", "spg_noalloc_last_error", "spg_set_anchor", "spg_param_scales",
-           "spg_fsc", "spg_fsc_last_error"]
+           "spg_fsc", "spg_fsc_last_error", "spg_set_data_fourier"]
 
 
 class SPGError(RuntimeError):
@@ -105,6 +105,7 @@ def load():
             "spg_set_anchor": (I, [P, I, ctypes.c_float, V]),
             "spg_fsc": (I, [I, V, V, I, ctypes.POINTER(D), ctypes.POINTER(D), P]),
             "spg_fsc_last_error": (ctypes.c_char_p, []),
+            "spg_set_data_fourier": (I, [P, I, V, V]),
             "spg_param_scales": (I, [P, I, ctypes.POINTER(D)]),
         }
         for name, (res, args) in sigs.items():
@@ -190,6 +191,27 @@ def spg_fsc(a, b, stream=None):
     if st != SPG_OK:
         raise SPGError(st, load().spg_fsc_last_error().decode())
     return fsc, cnt
+
+
+def _ptr_complex64(a):
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        if a.dtype != torch.complex64 or not a.is_contiguous():
+            raise TypeError("expected a contiguous complex64 tensor")
+        return ctypes.c_void_p(a.data_ptr()), a
+    a = np.ascontiguousarray(a, dtype=np.complex64)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+def spg_set_data_fourier(h, vol, y_half, N_half):
+    """Fourier-domain data term (Eq. 31): y_half complex64 and N_half float32,
+    both [nz, ny, nx//2 + 1] (the real-to-complex half spectrum)."""
+    py, ky = _ptr_complex64(y_half)
+    pn, kn = _ptr(N_half)
+    _check(load().spg_set_data_fourier(h, vol, py, pn), h)
 
 
 def spg_set_x(h, vol, x):
@@ -371,6 +393,9 @@ class SPG:
 
     def set_x(self, vol, x):
         spg_set_x(self.handle, vol, x)
+
+    def set_data_fourier(self, vol, y_half, N_half):
+        spg_set_data_fourier(self.handle, vol, y_half, N_half)
 
     def set_anchor(self, vol, gamma, x_anchor):
         spg_set_anchor(self.handle, vol, gamma, x_anchor)

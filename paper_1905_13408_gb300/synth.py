@@ -154,3 +154,45 @@ def make_half_maps(shape, blobs, radius, seed, noise_sd=0.3, field_sigma=4.0):
     b2 = v1.phantom.astype(np.float64) + noise_sd * noise / np.sqrt(v1.w.astype(np.float64))
     v2 = Volume(b=b2.astype(np.float32), w=v1.w.copy(), phantom=v1.phantom.copy())
     return v1, v2
+
+
+@dataclass
+class FourierVolume:
+    y: np.ndarray        # complex128 full spectrum [nz][ny][nx], Hermitian
+    N: np.ndarray        # float64 full spectrum, positive, N(-k) = N(k)
+    phantom: np.ndarray  # float32 [nz][ny][nx]
+
+
+def fourier_weight(shape, scale=4.0, falloff=0.15, floor=0.05):
+    """A positive, centro-symmetric N(k) that falls off with resolution and
+    favours directions near the z axis (uneven angular coverage, Sec. 1)."""
+    kz = np.fft.fftfreq(shape[0])[:, None, None]
+    ky = np.fft.fftfreq(shape[1])[None, :, None]
+    kx = np.fft.fftfreq(shape[2])[None, None, :]
+    k2 = kz * kz + ky * ky + kx * kx
+    cos_z = np.abs(kz) / np.sqrt(np.where(k2 > 0, k2, 1.0))
+    return scale * np.exp(-k2 / (2 * falloff ** 2)) * (0.25 + 0.75 * cos_z) + floor
+
+
+def make_fourier_volume(shape, blobs, radius, seed, noise_sd=0.3):
+    """Fourier-space data of Eq. 31: y = sqrt(N) A(phantom) + noise_sd A(e),
+    A the unitary DFT and e real white noise, so y is Hermitian."""
+    shape = tuple(int(s) for s in shape)
+    rng = np.random.default_rng(seed)
+    centre = np.array([(s - 1) / 2.0 for s in shape])
+    dirs = rng.standard_normal((blobs, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    rad = radius * rng.random(blobs) ** (1.0 / 3.0)
+    centres = centre[None, :] + dirs * rad[:, None]
+    sigmas = rng.uniform(1.5, 3.0, blobs)
+    amps = rng.uniform(0.5, 1.0, blobs)
+    noise = rng.standard_normal(shape)
+    phantom = _phantom(shape, centres, sigmas, amps)
+    N = fourier_weight(shape)
+    y = np.sqrt(N) * np.fft.fftn(phantom, norm="ortho") + noise_sd * np.fft.fftn(noise, norm="ortho")
+    return FourierVolume(y=y, N=N, phantom=phantom.astype(np.float32))
+
+
+def half_spectrum(a):
+    """The real-to-complex half of a full spectrum (last axis 0 .. nx/2)."""
+    return np.ascontiguousarray(a[..., : a.shape[-1] // 2 + 1])

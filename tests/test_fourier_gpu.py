@@ -1,0 +1,79 @@
+"""Fourier-domain data term (Eq. 31) on the GPU against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import fourier
+from paper_1905_13408_gb300 import spg, synth
+
+pytestmark = pytest.mark.gpu
+
+HYPER = dict(synth.DEFAULT_HYPER)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def gpu_fourier_solve(fv, hyper, rounds, iters, **kw):
+    shape = fv.phantom.shape
+    s = spg.SPG(dict(shape=shape, **hyper), **kw)
+    s.set_data_fourier(0, synth.half_spectrum(fv.y).astype(np.complex64),
+                       synth.half_spectrum(fv.N).astype(np.float32))
+    s.solve(rounds, iters)
+    x = s.get_x(0).cpu().numpy()
+    obj = s.objective(0)
+    hist = s.history(0)
+    s.close()
+    return x, obj, hist
+
+
+@pytest.mark.parametrize("shape", [(24, 28, 30), (32, 32, 32), (17, 40, 25)])
+def test_fourier_solve_matches_oracle(shape):
+    fv = synth.make_fourier_volume(shape, blobs=12, radius=6, seed=sum(shape))
+    hyper = dict(HYPER, mu=0.02)
+    x, obj, hist = gpu_fourier_solve(fv, hyper, 2, 40)
+    p = oracle.Params(shape, **hyper)
+    xr, hr, rr = fourier.solve(fv.y, fv.N, p, 2, 40)
+    err = rel_l2(x, xr)
+    print(f"fourier {shape}: rel-L2 {err:.3e}")
+    assert err <= 1e-5
+    # l1 and TV columns of the history (its data column is 0 in this mode)
+    np.testing.assert_allclose(hist[:, 2:4], np.concatenate([hr[0, :, 1:3], hr[1, :, 1:3]]), rtol=1e-5)
+
+
+def test_fourier_objective_value():
+    shape = (20, 22, 24)
+    fv = synth.make_fourier_volume(shape, blobs=8, radius=5, seed=61)
+    hyper = dict(HYPER, mu=0.02)
+    s = spg.SPG(dict(shape=shape, **hyper))
+    s.set_data_fourier(0, synth.half_spectrum(fv.y).astype(np.complex64), synth.half_spectrum(fv.N).astype(np.float32))
+    rng = np.random.default_rng(62)
+    x0 = (0.3 * rng.standard_normal(shape)).astype(np.float32)
+    s.set_x(0, x0)
+    s.reweight()
+    obj = s.objective(0)
+    s.close()
+    p = oracle.Params(shape, **hyper)
+    om1, omtv, _ = oracle.reweight(x0, p)
+    want = fourier.objective(x0.astype(np.float64), fv.y, fv.N, om1, omtv, p)
+    np.testing.assert_allclose(obj, want, rtol=1e-5)
+
+
+def test_constant_weight_matches_real_space_solve():
+    """N = w0 and y = sqrt(w0) A b: the Fourier-form solve equals the
+    real-space solve with w = w0 (different code paths on the GPU)."""
+    shape = (32, 32, 32)
+    vol = synth.make_volume(shape, blobs=10, radius=8, seed=63)
+    w0 = 2.0
+    fv = synth.FourierVolume(y=np.sqrt(w0) * np.fft.fftn(vol.b.astype(np.float64), norm="ortho"),
+                             N=np.full(shape, w0), phantom=vol.phantom)
+    hyper = dict(HYPER, mu=0.02)
+    xf, _, _ = gpu_fourier_solve(fv, hyper, 2, 50)
+    s = spg.SPG(dict(shape=shape, **hyper))
+    s.set_data(0, vol.b, np.full(shape, w0, np.float32))
+    s.solve(2, 50)
+    xr = s.get_x(0).cpu().numpy()
+    s.close()
+    assert rel_l2(xf, xr.astype(np.float64)) <= 1e-5

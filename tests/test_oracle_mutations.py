@@ -48,8 +48,10 @@ MUTATIONS = {
     "adjoint of w uses b - y": ("gw[v] += -tau * (y[v] - b[v]) * m[v];", "gw[v] += tau * (y[v] - b[v]) * m[v];"),
     "restart test with the wrong sign": ("if (p->restart && restart_dot(p, x, xprev, xnext, beta[km]) > 0.0)",
                                          "if (p->restart && restart_dot(p, x, xprev, xnext, beta[km]) < 0.0)"),
-    "Lipschitz bound with |D|^2 <= 4": ("return m + 12.0 * p->lambda_tv * max_omtv / p->mu;",
-                                         "return m + 4.0 * p->lambda_tv * max_omtv / p->mu;"),
+    "Lipschitz bound with |D|^2 <= 4": ("return m + 12.0 * p->lambda_tv * max_omtv / p->mu",
+                                         "return m + 4.0 * p->lambda_tv * max_omtv / p->mu"),
+    "gamma term without its factor 2 in the gradient": ("out[v] += 2.0 * p->gamma * (x[v] - p->anchor[v]);",
+                                                        "out[v] += p->gamma * (x[v] - p->anchor[v]);"),
 }
 
 QUICK = [
@@ -74,6 +76,7 @@ QUICK = [
     pins.test_adjoint_identity_of_one_linear_step,
     pins.test_adjoint_matches_central_differences,
     pins.test_gradient_restart_converges_faster,
+    pins.test_gamma_term_folds_into_data_and_weight,
 ]
 
 
