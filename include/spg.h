@@ -145,6 +145,33 @@ spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg
  * to the real-space data term. Synchronises. */
 spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const float *N_half);
 
+/* Kernel-regression back-projection (Sec. 2.2, Eq. 24-28) of m projection
+ * images into the (y, N) of the Fourier-domain data term, for
+ * spg_set_data_fourier. Image i's coefficient X at 2-D frequency index
+ * (kx, ky) (fftfreq order, |k| <= n/2 - 2) lands at p = R_i (kx, ky, 0)
+ * (Eq. 24) and adds K CTF X to num(n) and K CTF^2 to N(n) for the grid points
+ * n near p: kernel 0 is the Gaussian K = exp(-|p - n|^2 / h) on the 27 points
+ * round(p) + {-1,0,1}^3 (the paper uses h = 2); kernel 1 the trilinear
+ * weights on the 8 cell corners. Each of the m entries is one image-pose
+ * pair weighted by its posterior probability P(phi | X_i, V_0) (Eq. 26-28):
+ * an image with several candidate poses appears once per pose.
+ *   rot:  m row-major 3x3 rotations (float32); columns 0, 1 map the image axes
+ *   X:    m x n x n image spectra (complex64 interleaved, [ky][kx]), whose
+ *         real-space origin is the image centre
+ *   ctf:  m x n x n contrast transfer values (float32)
+ *   pw:   m posterior weights (float32, meant to be >= 0; not checked), or
+ *         NULL for weight 1 each
+ * Outputs (half spectrum [n][n][n/2+1], host or device): y_half (complex64)
+ * and N_half (float32) with N' = V N and y = (-1)^(kx+ky+kz) num / sqrt(N)
+ * (0 where N = 0), V = n^3: the data term 1/2 |y - sqrt(N') A x|^2 of a
+ * volume whose origin is voxel 0. n even. Accumulates in double precision
+ * with atomics (the summation order, and so the last bits, can vary between
+ * runs); allocates its own scratch; synchronises `stream`. Message in
+ * spg_backproject_last_error(). */
+spg_status spg_backproject(int n, int m, const float *rot, const void *X, const float *ctf, const float *pw,
+                           int kernel, float h, void *y_half, float *N_half, void *stream);
+const char *spg_backproject_last_error(void);
+
 /* Proximal anchor of the implicit-gradient term (Sec. 2.1 Eq. 22, Eq. 31):
  * adds gamma |x - x_anchor|^2 to the data term of volume `vol`. Because
  *   1/2 w (x - b)^2 + gamma (x - a)^2 = 1/2 w' (x - b')^2 + const,

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libspg.so")
 SOURCES = ["spg_step_f32.cu", "spg_step_bf16.cu", "spg_step.cu", "spg_aux.cu", "spg_api.cu", "spg_noalloc.cu",
-           "spg_fsc.cu", "spg_cufft.cu", "spg_fourier.cu"]
+           "spg_fsc.cu", "spg_cufft.cu", "spg_fourier.cu", "spg_grid.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -91,6 +91,7 @@ struct spg_ctx {
     float2 *Fh = nullptr;    // spectrum scratch
     float2 *Yh = nullptr;    // data spectrum y
     float *Nh = nullptr;     // weights N
+    float2 *Ch = nullptr;    // data spectrum sqrt(N) y / sqrt(V) subtracted in the spectrum pass
     float *Nmax = nullptr;
     double *fpart = nullptr; // reduction partials of the Fourier data value
     cufftHandle pr2c = 0, pc2r = 0;
@@ -148,7 +149,7 @@ void free_all(spg_ctx *c)
         spg::cufft_api().destroy(c->pr2c);
         spg::cufft_api().destroy(c->pc2r);
     }
-    void *fs[] = {c->Ybuf, c->Fh, c->Yh, c->Nh, c->Nmax, c->fpart};
+    void *fs[] = {c->Ybuf, c->Fh, c->Yh, c->Nh, c->Ch, c->Nmax, c->fpart};
     for (void *p : fs)
         if (p) cudaFree(p);
     void *ps[] = {c->vols_d, c->items_d, c->tmaps_d, c->plane_vol_d, c->X[0], c->X[1], c->X[2], c->X[3], c->B, c->W,
@@ -396,7 +397,8 @@ spg_status copy_volume_out(spg_ctx *ctx, void *dst, const void *src_base, size_t
 }
 
 // One iteration: the fused step, preceded for the Fourier-domain data term by
-// y_k, its spectrum, the N scaling and the inverse transform into b (= G).
+// y_k, its spectrum, the residual spectrum N A y_k - D y and the inverse
+// transform into b (= the data gradient).
 cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
 {
     if (ctx->fourier) {
@@ -407,7 +409,7 @@ cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
         const spg::CufftApi &cf = spg::cufft_api();
         if (cf.exec_r2c(ctx->pr2c, ctx->Ybuf, reinterpret_cast<cufftComplex *>(ctx->Fh)) != CUFFT_SUCCESS)
             return cudaErrorUnknown;
-        e = launch_spec_scale(ctx->Fh, ctx->Nh, ctx->nhalf, (float)(1.0 / V), ctx->stream);
+        e = launch_spec_scale(ctx->Fh, ctx->Nh, ctx->Ch, ctx->nhalf, (float)(1.0 / V), ctx->stream);
         if (e != cudaSuccess) return e;
         if (cf.exec_c2r(ctx->pc2r, reinterpret_cast<cufftComplex *>(ctx->Fh), static_cast<float *>(ctx->B)) !=
             CUFFT_SUCCESS)
@@ -714,6 +716,7 @@ spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const
         CK(dalloc(&ctx->Fh, (size_t)ctx->nhalf * sizeof(float2)), "alloc");
         CK(dalloc(&ctx->Yh, (size_t)ctx->nhalf * sizeof(float2)), "alloc");
         CK(dalloc(&ctx->Nh, (size_t)ctx->nhalf * sizeof(float)), "alloc");
+        CK(dalloc(&ctx->Ch, (size_t)ctx->nhalf * sizeof(float2)), "alloc");
         CK(dalloc(&ctx->Nmax, sizeof(float)), "alloc");
         CK(dalloc(&ctx->fpart, 1025 * sizeof(double)), "alloc");
         CK(cudaMemsetAsync(ctx->Ybuf, 0, (size_t)ctx->total * sizeof(float), ctx->stream), "memset");
@@ -737,15 +740,12 @@ spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const
        "copy y");
     CK(cudaMemcpyAsync(ctx->Nh, N_half, (size_t)ctx->nhalf * sizeof(float), cudaMemcpyDefault, ctx->stream),
        "copy N");
-    // c = A^H D y = IFFT(sqrt(N) y) / sqrt(V) into the w buffer; G (b buffer) starts at 0
+    // data spectrum sqrt(N) y / sqrt(V), subtracted from N F / V each iteration; b starts at 0
     const double V = (double)d.nx * d.ny * d.nz;
-    CK(launch_spec_prep(ctx->Fh, ctx->Yh, ctx->Nh, ctx->nhalf, (float)(1.0 / std::sqrt(V)), ctx->stream), "prep");
-    if (cf.exec_c2r(ctx->pc2r, reinterpret_cast<cufftComplex *>(ctx->Fh), static_cast<float *>(ctx->W)) !=
-        CUFFT_SUCCESS)
-        return fail(ctx, SPG_ECUDA, "spg_set_data_fourier: inverse transform");
+    CK(launch_spec_prep(ctx->Ch, ctx->Yh, ctx->Nh, ctx->nhalf, (float)(1.0 / std::sqrt(V)), ctx->stream), "prep");
     CK(cudaMemsetAsync(ctx->B, 0, (size_t)ctx->total * sizeof(float), ctx->stream), "memset");
     CK(launch_spec_max(ctx->Nh, ctx->nhalf, ctx->Nmax, ctx->stream), "max N");
-    ctx->launches += 2;
+    ctx->launches += 2;  // prep and max
     float nmax = 0.f;
     CK(cudaMemcpyAsync(&nmax, ctx->Nmax, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream), "read max N");
     CK(cudaStreamSynchronize(ctx->stream), "synchronise");

@@ -1,8 +1,13 @@
 // Kernels of the Fourier-domain data term (Sec. 2.5, Eq. 31):
 //   1/2 |y - D A x|^2, A the unitary DFT, D = diag sqrt(N),
-// whose gradient A^H N A x - A^H D y is formed each iteration at the
-// extrapolated point y_k by a real-to-complex transform, a spectrum scaling
-// and a complex-to-real transform (cuFFT), then consumed by the fused step.
+// whose gradient A^H (N A x - D y) is formed each iteration at the
+// extrapolated point y_k by a real-to-complex transform, a spectrum pass that
+// scales by N and subtracts the data spectrum, and a complex-to-real
+// transform (cuFFT), then consumed by the fused step. Subtracting before the
+// inverse transform keeps FP32 rounding relative to the residual rather than
+// to A^H N A y_k, which for the strongly uneven N of gridded data (many orders
+// of magnitude between low and high frequencies) is the difference between
+// errors of 1e-7 and 1e-5 after a hundred iterations.
 // Spectra use the real-to-complex half layout [nz][ny][nx/2+1].
 #include "spg_internal.h"
 
@@ -21,13 +26,16 @@ __global__ void form_y_kernel(const DevState *st, const VolDesc *vols, const flo
         y[i] = fmaf(b, d[i], x[i]);
 }
 
-__global__ void spec_scale_kernel(float2 *F, const float *N, long long n, float scale)
+// F <- N F scale - C: the unnormalised spectrum of the residual (scale = 1/V,
+// C = sqrt(N) y / sqrt(V)), so the inverse transform gives A^H (N A y_k - D y).
+__global__ void spec_scale_kernel(float2 *F, const float *N, const float2 *C, long long n, float scale)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float m = N[i] * scale;
+        const float2 c = C[i];
         float2 f = F[i];
-        f.x *= m;
-        f.y *= m;
+        f.x = fmaf(f.x, m, -c.x);
+        f.y = fmaf(f.y, m, -c.y);
         F[i] = f;
     }
 }
@@ -100,9 +108,9 @@ cudaError_t launch_form_y(const DevState *st, const VolDesc *vols, const float *
     return cudaGetLastError();
 }
 
-cudaError_t launch_spec_scale(float2 *F, const float *N, long long n, float scale, cudaStream_t s)
+cudaError_t launch_spec_scale(float2 *F, const float *N, const float2 *C, long long n, float scale, cudaStream_t s)
 {
-    spec_scale_kernel<<<grid_for(n), 256, 0, s>>>(F, N, n, scale);
+    spec_scale_kernel<<<grid_for(n), 256, 0, s>>>(F, N, C, n, scale);
     return cudaGetLastError();
 }
 

@@ -73,7 +73,7 @@ struct StepParams {
     double *hist;            // ring [hist_cap][nvol][5]
     int nitems, nvol, hist_cap, hist_every;
     int restart;             // gradient restart of the extrapolation, per volume
-    int fourier;             // data gradient = b - w (G - c of the Fourier-domain term), single volume
+    int fourier;             // data gradient = b (A^H (N A y - D y) of the Fourier-domain term), no w tile
     long long timeout_ns;    // bound on any single barrier wait
 };
 
@@ -140,8 +140,8 @@ cudaError_t launch_timeout_probe(DevState *st, long long timeout_ns, cudaStream_
 // y = x_k + beta d_k over the whole pitched volume (cur and beta read on the device).
 cudaError_t launch_form_y(const DevState *st, const VolDesc *vols, const float *beta, float *const *xbuf,
                           float *y, long long n, cudaStream_t s);
-// F *= N * scale over n half-spectrum coefficients.
-cudaError_t launch_spec_scale(float2 *F, const float *N, long long n, float scale, cudaStream_t s);
+// F <- N F scale - C over n half-spectrum coefficients.
+cudaError_t launch_spec_scale(float2 *F, const float *N, const float2 *C, long long n, float scale, cudaStream_t s);
 // F = Y * sqrt(N) * scale.
 cudaError_t launch_spec_prep(float2 *F, const float2 *Y, const float *N, long long n, float scale,
                              cudaStream_t s);

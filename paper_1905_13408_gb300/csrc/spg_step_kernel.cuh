@@ -203,7 +203,7 @@ struct Cfg {
 // plane z = z0-1+j of x_k (buffer ia) and of x_{k-1} or d_k (buffer ib), both
 // with halo, and of omtv, and plane z-1 of b, w and om1. Steps 0 and 1 skip
 // what they do not consume.
-template <class C, int S>
+template <class C, int S, bool LOADW>
 __device__ __forceinline__ void issue_stage(unsigned char *sm, uint64_t *bars, const TmapSet *tm,
                                             const WorkItem &W, int ia, int ib, long long gstep, int j)
 {
@@ -212,14 +212,14 @@ __device__ __forceinline__ void issue_stage(unsigned char *sm, uint64_t *bars, c
     const int z = W.z0 - 1 + j;
     const bool need_om = j >= 1, need_bwo = j >= 2;
     const uint32_t bytes = 2 * C::XT_BYTES + (need_om ? C::OM_BYTES : 0) +
-                           (need_bwo ? 2 * C::BW_BYTES + C::O1_BYTES : 0);
+                           (need_bwo ? (LOADW ? 2 : 1) * C::BW_BYTES + C::O1_BYTES : 0);
     mbar_arrive_expect_tx(&bars[s], bytes);
     tma_load_3d(base + C::OFF_XK, &tm->x[ia], W.x0 - 4, W.y0 - 1, z, &bars[s]);
     tma_load_3d(base + C::OFF_XM, &tm->x[ib], W.x0 - 4, W.y0 - 1, z, &bars[s]);
     if (need_om) tma_load_3d(base + C::OFF_OM, &tm->omtv, W.x0, W.y0, z, &bars[s]);
     if (need_bwo) {
         tma_load_3d(base + C::OFF_B, &tm->b, W.x0, W.y0, z - 1, &bars[s]);
-        tma_load_3d(base + C::OFF_W, &tm->w, W.x0, W.y0, z - 1, &bars[s]);
+        if (LOADW) tma_load_3d(base + C::OFF_W, &tm->w, W.x0, W.y0, z - 1, &bars[s]);
         tma_load_3d(base + C::OFF_O1, &tm->om1, W.x0, W.y0, z - 1, &bars[s]);
     }
 }
@@ -272,7 +272,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
     const bool producer = (warp == TY) && (lane == 0);
     if (producer) {
         const int pro = nsteps < S ? nsteps : S;
-        for (int j = 0; j < pro; j++) issue_stage<C, S>(sh.sm, sh.bars, tm, W, ia, ib, g0, j);
+        for (int j = 0; j < pro; j++) issue_stage<C, S, !FOURIER>(sh.sm, sh.bars, tm, W, ia, ib, g0, j);
         pp_.issued_upto = g0 + pro;
     }
 
@@ -401,7 +401,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
         }
         // refill the stage consumed in step j-1
         if (producer && j >= 1 && j - 1 + S < nsteps) {
-            issue_stage<C, S>(sh.sm, sh.bars, tm, W, ia, ib, g0, j - 1 + S);
+            issue_stage<C, S, !FOURIER>(sh.sm, sh.bars, tm, W, ia, ib, g0, j - 1 + S);
             pp_.issued_upto = g0 + j + S;
         }
 
@@ -410,7 +410,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
             const int zo = z - 1;
             float bb[VX], ww[VX], oo[VX], pyd[VX];
             ld_data<VX, BF16>(base + C::OFF_B, r * TX + VX * lane, bb);
-            ld_data<VX, BF16>(base + C::OFF_W, r * TX + VX * lane, ww);
+            if constexpr (!FOURIER) ld_data<VX, BF16>(base + C::OFF_W, r * TX + VX * lane, ww);
             ld_vec<VX>(reinterpret_cast<const float *>(base + C::OFF_O1) + r * TX + VX * lane, oo);
             ld_vec<VX>(sh.py_ring + (((j - 1) % 3) * (TY + 1) + r + 1) * TX + VX * lane, pyd);
             float pxn = __shfl_down_sync(FULL, pp[0][0], 1);
@@ -423,8 +423,8 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
                 const float div = (pp[0][i] - pxr) + (pp[1][i] - pyd[i]) + (pp[2][i] - pc[2][i]);
                 const float res = xz[i] - bb[i];
                 // data gradient: w (y - b) (Eq. 28 form) or, for the Fourier-domain term of
-                // Eq. 31, G - c with G = A^H N A y in the b tile and c = A^H D y in the w tile
-                const float gdat = FOURIER ? bb[i] - ww[i] : ww[i] * fmaf(beta, dz[i], res);
+                // Eq. 31, A^H (N A y - D y) formed by the transforms in the b tile (no w tile)
+                const float gdat = FOURIER ? bb[i] : ww[i] * fmaf(beta, dz[i], res);
                 const float g = fmaf(lam_tv, div, gdat);
                 const float delta = fmaf(beta, dz[i], -tau * g);
                 const float zz = xz[i] + delta;

@@ -37,7 +37,8 @@ EXPORTS = ["spg_create", "spg_create_batch", "spg_set_data", "spg_set_x", "spg_g
            "spg_get_state", "spg_set_state", "spg_backward", "spg_unrolled", "spg_probe_timeout",
            "spg_autotune", "spg_launch_count", "spg_plan_info", "spg_last_error", "spg_destroy",
            "spg_objective_noalloc", "spg_noalloc_last_error", "spg_set_anchor", "spg_param_scales",
-           "spg_fsc", "spg_fsc_last_error", "spg_set_data_fourier"]
+           "spg_fsc", "spg_fsc_last_error", "spg_set_data_fourier", "spg_backproject",
+           "spg_backproject_last_error"]
 
 
 class SPGError(RuntimeError):
@@ -106,6 +107,8 @@ def load():
             "spg_fsc": (I, [I, V, V, I, ctypes.POINTER(D), ctypes.POINTER(D), P]),
             "spg_fsc_last_error": (ctypes.c_char_p, []),
             "spg_set_data_fourier": (I, [P, I, V, V]),
+            "spg_backproject": (I, [I, I, V, V, V, V, I, ctypes.c_float, V, V, P]),
+            "spg_backproject_last_error": (ctypes.c_char_p, []),
             "spg_param_scales": (I, [P, I, ctypes.POINTER(D)]),
         }
         for name, (res, args) in sigs.items():
@@ -212,6 +215,31 @@ def spg_set_data_fourier(h, vol, y_half, N_half):
     py, ky = _ptr_complex64(y_half)
     pn, kn = _ptr(N_half)
     _check(load().spg_set_data_fourier(h, vol, py, pn), h)
+
+
+def spg_backproject(rot, X, ctf, pw=None, kernel="gauss", h=2.0, stream=None):
+    """(y_half complex64, N_half float32) on the GPU of m n x n images
+    (rot [m, 3, 3], X [m, n, n] complex, ctf [m, n, n], optional posterior
+    weights pw [m]); kernel "gauss" or "trilinear" (Sec. 2.2)."""
+    import torch
+    rot = np.ascontiguousarray(rot, dtype=np.float32)
+    m, n = int(rot.shape[0]), int(X.shape[-1])
+    pX, kX = _ptr_complex64(X)
+    if isinstance(ctf, np.ndarray):
+        ctf = np.ascontiguousarray(ctf, dtype=np.float32)
+    pc, kc = _ptr(ctf)
+    pp = ctypes.c_void_p(0)
+    if pw is not None:
+        pw = np.ascontiguousarray(pw, dtype=np.float32)
+        pp = ctypes.c_void_p(pw.ctypes.data)
+    y = torch.empty((n, n, n // 2 + 1), dtype=torch.complex64, device="cuda")
+    N = torch.empty((n, n, n // 2 + 1), dtype=torch.float32, device="cuda")
+    st = load().spg_backproject(n, m, ctypes.c_void_p(rot.ctypes.data), pX, pc, pp, 0 if kernel == "gauss" else 1,
+                                float(h), ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(N.data_ptr()),
+                                ctypes.c_void_p(stream or 0))
+    if st != SPG_OK:
+        raise SPGError(st, load().spg_backproject_last_error().decode())
+    return y, N
 
 
 def spg_set_x(h, vol, x):

@@ -196,3 +196,64 @@ def make_fourier_volume(shape, blobs, radius, seed, noise_sd=0.3):
 def half_spectrum(a):
     """The real-to-complex half of a full spectrum (last axis 0 .. nx/2)."""
     return np.ascontiguousarray(a[..., : a.shape[-1] // 2 + 1])
+
+
+@dataclass
+class ProjectionData:
+    rot: np.ndarray      # float64 [m][3][3]; column 0 and 1 map the image axes (kx, ky) to 3-D (x, y, z)
+    X: np.ndarray        # complex128 [m][n][n] image spectra [ky][kx], fftfreq order, Hermitian per image
+    ctf: np.ndarray      # float64 [m][n][n] contrast transfer functions (real, centro-symmetric)
+    phantom: np.ndarray  # float32 [n][n][n]
+
+
+def random_rotations(m, rng):
+    """m uniformly distributed rotations (unit quaternions)."""
+    q = rng.standard_normal((m, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    return np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)], -1),
+        np.stack([2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)], -1),
+        np.stack([2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)], -1),
+    ], 1)
+
+
+def make_projection_data(n, blobs, radius, n_images, seed, noise_sd=1.0):
+    """Spectra of n x n projection images of a Gaussian-blob phantom (n even):
+    by the projection-slice relation (Sec. 2, Eq. 1 and Eq. 24) image i
+    samples the phantom's 3-D transform on the central plane R_i (kx, ky, 0);
+    the blobs' transform is analytic, so the samples are exact at off-grid
+    positions. Transforms take the real-space origin at the box centre
+    (voxel n/2 on every axis), as cryo-EM images do, so they vary smoothly
+    between grid points. Each image is multiplied by its own CTF (a
+    defocus-like oscillation) and receives the 2-D transform of real white
+    noise."""
+    assert n % 2 == 0, "projection data need an even box"
+    rng = np.random.default_rng(seed)
+    shape = (n, n, n)
+    centre = np.array([(n - 1) / 2.0] * 3)
+    dirs = rng.standard_normal((blobs, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    rad = radius * rng.random(blobs) ** (1.0 / 3.0)
+    centres = centre[None, :] + dirs * rad[:, None]   # (z, y, x) voxel coordinates
+    sigmas = rng.uniform(1.5, 3.0, blobs)
+    amps = rng.uniform(0.5, 1.0, blobs)
+    phantom = _phantom(shape, centres, sigmas, amps)
+    rot = random_rotations(n_images, rng)
+    defocus = rng.uniform(0.5, 1.5, n_images)
+    f = np.fft.fftfreq(n) * n
+    KY, KX = np.meshgrid(f, f, indexing="ij")
+    cxyz = centres[:, ::-1] - n / 2.0                  # (x, y, z) about the box centre
+    X = np.empty((n_images, n, n), dtype=np.complex128)
+    ctf = np.empty((n_images, n, n))
+    s2 = (KX * KX + KY * KY) / (n * n)
+    for i in range(n_images):
+        q = rot[i][:, 0][None, None, :] * KX[..., None] + rot[i][:, 1][None, None, :] * KY[..., None]
+        qq = (q * q).sum(-1) / (n * n)
+        phase = np.einsum("abk,ck->abc", q, cxyz) / n  # [ky][kx][blob]
+        amp = amps * (2 * np.pi * sigmas ** 2) ** 1.5
+        F = (amp[None, None, :] * np.exp(-2 * np.pi ** 2 * sigmas[None, None, :] ** 2 * qq[..., None])
+             * np.exp(-2j * np.pi * phase)).sum(-1)
+        ctf[i] = np.sin(0.5 + 30.0 * defocus[i] * s2)
+        X[i] = ctf[i] * F + noise_sd * np.fft.fft2(rng.standard_normal((n, n)))
+    return ProjectionData(rot=rot, X=X, ctf=ctf, phantom=phantom.astype(np.float32))
