@@ -145,29 +145,55 @@ spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg
  * to the real-space data term. Synchronises. */
 spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const float *N_half);
 
-/* Kernel-regression back-projection (Sec. 2.2, Eq. 24-28) of m projection
- * images into the (y, N) of the Fourier-domain data term, for
- * spg_set_data_fourier. Image i's coefficient X at 2-D frequency index
- * (kx, ky) (fftfreq order, |k| <= n/2 - 2) lands at p = R_i (kx, ky, 0)
- * (Eq. 24) and adds K CTF X to num(n) and K CTF^2 to N(n) for the grid points
- * n near p: kernel 0 is the Gaussian K = exp(-|p - n|^2 / h) on the 27 points
+/* Kernel-regression back-projection (Sec. 2.2, Eq. 24-28): a streaming
+ * accumulator that grids batches of projection images into the (y, N) of
+ * the Fourier-domain data term, for spg_set_data_fourier.
+ *
+ * Image i's coefficient X at 2-D frequency index (kx, ky) (fftfreq order,
+ * |k| <= n/2 - 2) lands at p = R_i (kx, ky, 0) (Eq. 24) and adds
+ * P K CTF X to num(n) and P K CTF^2 to N(n) for the grid points n near p:
+ * kernel 0 is the Gaussian K = exp(-|p - n|^2 / h) on the 27 points
  * round(p) + {-1,0,1}^3 (the paper uses h = 2); kernel 1 the trilinear
- * weights on the 8 cell corners. Each of the m entries is one image-pose
- * pair weighted by its posterior probability P(phi | X_i, V_0) (Eq. 26-28):
- * an image with several candidate poses appears once per pose.
+ * weights on the 8 cell corners. Each image is one image-pose pair with
+ * posterior probability P = P(phi | X_i, V_0) (Eq. 26-28): an image with
+ * several candidate poses is added once per pose.
+ *
+ * Images are real and CTFs centro-symmetric, so only the half ky >= 0 of
+ * each spectrum (kx >= 0 on ky = 0) is read; the other half enters as its
+ * conjugate. Sums are FP64 (atomics: the last bits can vary between runs).
+ *
+ * spg_grid_create: n even >= 4 (n^3 <= 2^31), kernel 0 or 1, h > 0; the
+ *   accumulator (32 B per half-spectrum point) is owned by the object; all
+ *   work is queued on `stream` (a cudaStream_t, NULL = default stream).
+ * spg_grid_add: m image-pose pairs, asynchronous on the stream:
  *   rot:  m row-major 3x3 rotations (float32); columns 0, 1 map the image axes
  *   X:    m x n x n image spectra (complex64 interleaved, [ky][kx]), whose
  *         real-space origin is the image centre
  *   ctf:  m x n x n contrast transfer values (float32)
  *   pw:   m posterior weights (float32, meant to be >= 0; not checked), or
  *         NULL for weight 1 each
- * Outputs (half spectrum [n][n][n/2+1], host or device): y_half (complex64)
- * and N_half (float32) with N' = V N and y = (-1)^(kx+ky+kz) num / sqrt(N)
- * (0 where N = 0), V = n^3: the data term 1/2 |y - sqrt(N') A x|^2 of a
- * volume whose origin is voxel 0. n even. Accumulates in double precision
- * with atomics (the summation order, and so the last bits, can vary between
- * runs); allocates its own scratch; synchronises `stream`. Message in
- * spg_backproject_last_error(). */
+ *   Device arrays are read in place (they must stay valid until the work
+ *   queued on the stream is done); host arrays are copied to a staging
+ *   buffer first.
+ * spg_grid_finish: writes the half spectra [n][n][n/2+1] (host or device):
+ *   y_half (complex64) and N_half (float32), N' = V N and
+ *   y = (-1)^(kx+ky+kz) num / sqrt(N) (0 where N = 0), V = n^3: the data
+ *   term 1/2 |y - sqrt(N') A x|^2 of a volume whose origin is voxel 0.
+ *   Keeps the sums (more images may be added); synchronises the stream.
+ * spg_grid_reset: zeroes the sums. spg_grid_count: image-pose pairs added.
+ * Messages of failed calls in spg_grid_last_error(g) (g = NULL: of a failed
+ * spg_grid_create). */
+typedef struct spg_grid spg_grid;
+spg_status spg_grid_create(int n, int kernel, float h, void *stream, spg_grid **out);
+spg_status spg_grid_add(spg_grid *g, int m, const float *rot, const void *X, const float *ctf, const float *pw);
+spg_status spg_grid_finish(spg_grid *g, void *y_half, float *N_half);
+spg_status spg_grid_reset(spg_grid *g);
+long long spg_grid_count(const spg_grid *g);
+const char *spg_grid_last_error(const spg_grid *g);
+void spg_grid_destroy(spg_grid *g);
+
+/* One-shot back-projection: create, add the m images, finish, destroy.
+ * Message in spg_backproject_last_error(). */
 spg_status spg_backproject(int n, int m, const float *rot, const void *X, const float *ctf, const float *pw,
                            int kernel, float h, void *y_half, float *N_half, void *stream);
 const char *spg_backproject_last_error(void);

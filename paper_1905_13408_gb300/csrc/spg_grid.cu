@@ -4,15 +4,24 @@
 // position p = R_i (kx, ky, 0) (Eq. 24). Every grid point n of the kernel's
 // support around p receives
 //     num(n) += P K CTF X,    N(n) += P K CTF^2        (Eq. 26-28)
-// with P the posterior weight of the image-pose pair (1 for known poses)
-// with K = exp(-|p - n|^2 / h) on the 27 points round(p) + {-1,0,1}^3 (the
+// with P the posterior weight of the image-pose pair (1 for known poses) and
+// K = exp(-|p - n|^2 / h) on the 27 points round(p) + {-1,0,1}^3 (the
 // Gaussian kernel of Sec. 2.2) or the trilinear weights on the 8 corners of
-// p's cell (the interpolation kernel the paper attributes to Relion). One
-// thread per image coefficient scatters with double-precision atomics into
-// full-spectrum accumulators; a second pass writes the half spectrum of the
-// Eq. 31 data term: N' = V N and y = (-1)^(kx+ky+kz) num / sqrt(N), the sign
-// moving the transform's origin from the box centre (image convention) to
-// voxel 0 (the solver's convention; n even).
+// p's cell (the interpolation kernel the paper attributes to Relion).
+//
+// Images are real, so X(-k) = conj X(k), and CTFs are centro-symmetric: the
+// coefficient -k lands at -p with the conjugate contribution. Only the half
+// ky > 0 (and kx >= 0 on ky = 0) is read, and each contribution is added at n
+// or, mirrored, at -n, whichever lies in the stored half spectrum
+// [n][n][n/2+1] (both on the planes kx = 0 and kx = n/2). This halves both
+// the atomics and the accumulator against a full-spectrum scatter and gives
+// the same sums. One thread per image coefficient forms its deposits in
+// FP32 and adds them with FP64 atomics into an interleaved accumulator
+// (Re num, Im num, N, unused: one 32-byte sector per grid point). A finishing
+// pass writes the Eq. 31 data term: N' = V N and
+// y = (-1)^(kx+ky+kz) num / sqrt(N), the sign moving the
+// transform's origin from the box centre (image convention) to voxel 0 (the
+// solver's convention; n even).
 #include <cuda_runtime.h>
 
 #include <string>
@@ -23,63 +32,114 @@ namespace {
 
 thread_local std::string g_grid_err = "no error";
 
+constexpr int kThreads = 256;
+constexpr int kMaxBlocks = 152 * 16;
+
 __device__ __forceinline__ int fidx(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
 __device__ __forceinline__ int wrap(int i, int n) { return ((i % n) + n) % n; }
 
-__global__ void scatter_kernel(int n, int m, const float *__restrict__ rot, const float2 *__restrict__ X,
-                               const float *__restrict__ ctf, const float *__restrict__ pw, int kernel, float h,
-                               double *num_re, double *num_im, double *N)
+// Add (re, im, w) at full-spectrum point (x, y, z) (any integers), and, unless
+// the sample is its own mate (k = 0), the mate's (re, -im, w) at (-x, -y, -z):
+// each where it falls in the stored half.
+__device__ __forceinline__ void deposit(double *acc, int n, int x, int y, int z, double re, double im, double w,
+                                        bool self_mate)
 {
-    const long long per_image = (long long)n * n;
+    const int nh = n / 2 + 1;
+    const int xw = wrap(x, n);
+    if (xw < nh) {
+        double *a = acc + 4 * (((long long)wrap(z, n) * n + wrap(y, n)) * nh + xw);
+        atomicAdd(a + 0, re);
+        atomicAdd(a + 1, im);
+        atomicAdd(a + 2, w);
+    }
+    if (self_mate) return;
+    const int mx = wrap(-x, n);
+    if (mx < nh) {
+        double *a = acc + 4 * (((long long)wrap(-z, n) * n + wrap(-y, n)) * nh + mx);
+        atomicAdd(a + 0, re);
+        atomicAdd(a + 1, -im);
+        atomicAdd(a + 2, w);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) scatter_kernel(int n, int m, const float *__restrict__ rot,
+                                                           const float2 *__restrict__ X,
+                                                           const float *__restrict__ ctf,
+                                                           const float *__restrict__ pw, int kernel, float h,
+                                                           double *acc)
+{
+    const int rows = n / 2;  // ky = 0 .. n/2 - 1
+    const long long per_image = (long long)rows * n;
     const long long total = per_image * m;
     const float rmax2 = (n * 0.5f - 2.0f) * (n * 0.5f - 2.0f);
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
          q += (long long)gridDim.x * blockDim.x) {
         const int img = (int)(q / per_image);
         const int rem = (int)(q % per_image);
-        const int ky = fidx(rem / n, n), kx = fidx(rem % n, n);
+        const int ky = rem / n, col = rem % n;
+        const int kx = fidx(col, n);
+        if (ky == 0 && kx < 0) continue;  // the mate half of row 0
         if ((float)(kx * kx + ky * ky) > rmax2) continue;
+        const bool self_mate = (kx == 0 && ky == 0);
         const float *R = rot + (long long)img * 9;  // row-major 3x3; columns 0 and 1 span the image plane
         // positions in double so the nearest-point decisions match a double-precision reference
         const double px = __dadd_rn(__dmul_rn(R[0], kx), __dmul_rn(R[1], ky));
         const double py = __dadd_rn(__dmul_rn(R[3], kx), __dmul_rn(R[4], ky));
         const double pz = __dadd_rn(__dmul_rn(R[6], kx), __dmul_rn(R[7], ky));
-        const float2 x = X[q];
-        const float c = ctf[q];
-        const double pc = pw ? (double)pw[img] * c : (double)c;
-        const double cx = pc * x.x, cy = pc * x.y, cc = pc * c;
+        const long long src = (long long)img * n * n + (long long)ky * n + col;
+        const float2 x = X[src];
+        const float c = ctf[src];
+        const float pc = pw ? pw[img] * c : c;
+        const float vre = pc * x.x, vim = pc * x.y, vcc = pc * c;
+        // The kernel weight factorises over the axes (a product of 1-D
+        // Gaussians, or of 1-D hat functions); the factors and the deposits
+        // are FP32 (the FP64 pipe is narrow), only the sums are FP64.
+        float wx[3], wy[3], wz[3];
+        int bx, by, bz;
         if (kernel == 0) {
-            const int bx = __double2int_rn(px), by = __double2int_rn(py), bz = __double2int_rn(pz);
-            for (int dz = -1; dz <= 1; dz++)
-                for (int dy = -1; dy <= 1; dy++)
-                    for (int dx = -1; dx <= 1; dx++) {
-                        const double ex = px - (bx + dx), ey = py - (by + dy), ez = pz - (bz + dz);
-                        const double K = exp(-(ex * ex + ey * ey + ez * ez) / h);
-                        const long long g =
-                            ((long long)wrap(bz + dz, n) * n + wrap(by + dy, n)) * n + wrap(bx + dx, n);
-                        atomicAdd(num_re + g, K * cx);
-                        atomicAdd(num_im + g, K * cy);
-                        atomicAdd(N + g, K * cc);
-                    }
+            bx = __double2int_rn(px);
+            by = __double2int_rn(py);
+            bz = __double2int_rn(pz);
+            const float fx = (float)(px - bx), fy = (float)(py - by), fz = (float)(pz - bz);
+            const float ih = 1.0f / h;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const float ex = fx - (d - 1), ey = fy - (d - 1), ez = fz - (d - 1);
+                wx[d] = expf(-ex * ex * ih);
+                wy[d] = expf(-ey * ey * ih);
+                wz[d] = expf(-ez * ez * ih);
+            }
+            bx -= 1;
+            by -= 1;
+            bz -= 1;
         } else {
-            const int bx = (int)floor(px), by = (int)floor(py), bz = (int)floor(pz);
-            for (int dz = 0; dz <= 1; dz++)
-                for (int dy = 0; dy <= 1; dy++)
-                    for (int dx = 0; dx <= 1; dx++) {
-                        const double K = (1.0 - fabs(px - (bx + dx))) * (1.0 - fabs(py - (by + dy))) *
-                                         (1.0 - fabs(pz - (bz + dz)));
-                        const long long g =
-                            ((long long)wrap(bz + dz, n) * n + wrap(by + dy, n)) * n + wrap(bx + dx, n);
-                        atomicAdd(num_re + g, K * cx);
-                        atomicAdd(num_im + g, K * cy);
-                        atomicAdd(N + g, K * cc);
-                    }
+            const double flx = floor(px), fly = floor(py), flz = floor(pz);
+            bx = (int)flx;
+            by = (int)fly;
+            bz = (int)flz;
+            const float fx = (float)(px - flx), fy = (float)(py - fly), fz = (float)(pz - flz);
+            wx[0] = 1.f - fx;
+            wx[1] = fx;
+            wy[0] = 1.f - fy;
+            wy[1] = fy;
+            wz[0] = 1.f - fz;
+            wz[1] = fz;
+            wx[2] = wy[2] = wz[2] = 0.f;
         }
+        const int span = kernel == 0 ? 3 : 2;
+        for (int dz = 0; dz < span; dz++)
+            for (int dy = 0; dy < span; dy++) {
+                const float kyz = wy[dy] * wz[dz];
+                for (int dx = 0; dx < span; dx++) {
+                    const float K = wx[dx] * kyz;
+                    deposit(acc, n, bx + dx, by + dy, bz + dz, (double)(K * vre), (double)(K * vim),
+                            (double)(K * vcc), self_mate);
+                }
+            }
     }
 }
 
-__global__ void finalize_kernel(int n, const double *num_re, const double *num_im, const double *N, float2 *y_half,
-                                float *N_half)
+__global__ void finish_kernel(int n, const double *__restrict__ acc, float2 *y_half, float *N_half)
 {
     const int nh = n / 2 + 1;
     const long long total = (long long)n * n * nh;
@@ -89,90 +149,213 @@ __global__ void finalize_kernel(int n, const double *num_re, const double *num_i
         const int kx = (int)(q % nh);
         const int ky = (int)((q / nh) % n);
         const int kz = (int)(q / ((long long)nh * n));
-        const long long g = ((long long)kz * n + ky) * n + kx;
-        const double w = N[g];
+        const double *a = acc + 4 * q;
+        const double w = a[2];
         const double sgn = ((kx + ky + kz) & 1) ? -1.0 : 1.0;
         float2 y = make_float2(0.f, 0.f);
         if (w > 0) {
             const double s = sgn / sqrt(w);
-            y = make_float2((float)(num_re[g] * s), (float)(num_im[g] * s));
+            y = make_float2((float)(a[0] * s), (float)(a[1] * s));
         }
         y_half[q] = y;
         N_half[q] = (float)(V * w);
     }
 }
 
-struct Buf {
-    void *p = nullptr;
-    ~Buf()
-    {
-        if (p) cudaFree(p);
-    }
-};
-
-spg_status grid_fail(spg_status s, const std::string &m)
+int blocks_for(long long work)
 {
-    g_grid_err = m;
-    return s;
+    const long long b = (work + kThreads - 1) / kThreads;
+    return (int)(b < kMaxBlocks ? (b > 0 ? b : 1) : kMaxBlocks);
+}
+
+bool on_device(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
+
+struct spg_grid {
+    int n = 0, kernel = 0;
+    float h = 2.f;
+    cudaStream_t stream = nullptr;
+    double *acc = nullptr;  // [n][n][n/2+1][4]
+    void *stage = nullptr;  // device copies of host inputs / outputs
+    size_t stage_bytes = 0;
+    long long images = 0;
+    std::string err = "no error";
+    size_t half() const { return (size_t)n * n * (n / 2 + 1); }
+};
+
+namespace {
+
+spg_status gfail(spg_grid *g, spg_status s, const std::string &m)
+{
+    (g ? g->err : g_grid_err) = m;
+    return s;
+}
+
+spg_status cuda_fail(spg_grid *g, cudaError_t e, const char *what)
+{
+    cudaGetLastError();
+    return gfail(g, e == cudaErrorMemoryAllocation ? SPG_ENOMEM : SPG_ECUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Make sure the staging buffer holds `bytes`; waits for the stream before
+// replacing a buffer that queued work may still read.
+cudaError_t ensure_stage(spg_grid *g, size_t bytes)
+{
+    if (bytes <= g->stage_bytes) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return e;
+    if (g->stage) cudaFree(g->stage);
+    g->stage = nullptr;
+    g->stage_bytes = 0;
+    e = cudaMalloc(&g->stage, bytes);
+    if (e == cudaSuccess) g->stage_bytes = bytes;
+    return e;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" spg_status spg_grid_create(int n, int kernel, float h, void *stream, spg_grid **out)
+{
+    if (!out) return gfail(nullptr, SPG_EINVAL, "spg_grid_create: null output");
+    *out = nullptr;
+    if (n < 4 || n % 2 || (kernel != 0 && kernel != 1) || !(h > 0.f))
+        return gfail(nullptr, SPG_EINVAL, "spg_grid_create: bad arguments (even n >= 4, kernel 0 or 1, h > 0)");
+    if ((long long)n * n * n > (1LL << 31)) return gfail(nullptr, SPG_EINVAL, "spg_grid_create: volume too large");
+    spg_grid *g = new spg_grid;
+    g->n = n;
+    g->kernel = kernel;
+    g->h = h;
+    g->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMalloc(&g->acc, g->half() * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->acc, 0, g->half() * 4 * sizeof(double), g->stream);
+    if (e != cudaSuccess) {
+        spg_status s = cuda_fail(nullptr, e, "spg_grid_create");
+        if (g->acc) cudaFree(g->acc);
+        delete g;
+        return s;
+    }
+    *out = g;
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_grid_add(spg_grid *g, int m, const float *rot, const void *X, const float *ctf,
+                                   const float *pw)
+{
+    if (!g) return gfail(nullptr, SPG_EINVAL, "spg_grid_add: null accumulator");
+    if (m < 1 || !rot || !X || !ctf) return gfail(g, SPG_EINVAL, "spg_grid_add: m >= 1 and non-null arrays");
+    const int n = g->n;
+    const size_t img = (size_t)m * n * n;
+    struct In {
+        const void *src;
+        size_t bytes;
+        const void *dev;
+        bool host;
+    } in[4] = {{rot, (size_t)m * 9 * sizeof(float), nullptr, false},
+               {X, img * sizeof(float2), nullptr, false},
+               {ctf, img * sizeof(float), nullptr, false},
+               {pw, pw ? (size_t)m * sizeof(float) : 0, nullptr, false}};
+    size_t need = 0;
+    for (auto &a : in) {
+        a.host = a.src && !on_device(a.src);
+        if (a.host) need += align256(a.bytes);
+    }
+    cudaError_t e = ensure_stage(g, need);
+    if (e != cudaSuccess) return cuda_fail(g, e, "spg_grid_add: staging buffer");
+    size_t off = 0;
+    for (auto &a : in) {
+        if (!a.host) {
+            a.dev = a.src;
+            continue;
+        }
+        void *dst = static_cast<char *>(g->stage) + off;
+        e = cudaMemcpyAsync(dst, a.src, a.bytes, cudaMemcpyHostToDevice, g->stream);
+        if (e != cudaSuccess) return cuda_fail(g, e, "spg_grid_add: copy");
+        a.dev = dst;
+        off += align256(a.bytes);
+    }
+    const long long work = (long long)m * (n / 2) * n;
+    scatter_kernel<<<blocks_for(work), kThreads, 0, g->stream>>>(
+        n, m, static_cast<const float *>(in[0].dev), static_cast<const float2 *>(in[1].dev),
+        static_cast<const float *>(in[2].dev), static_cast<const float *>(in[3].dev), g->kernel, g->h, g->acc);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(g, e, "spg_grid_add: launch");
+    g->images += m;
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_grid_finish(spg_grid *g, void *y_half, float *N_half)
+{
+    if (!g) return gfail(nullptr, SPG_EINVAL, "spg_grid_finish: null accumulator");
+    if (!y_half || !N_half) return gfail(g, SPG_EINVAL, "spg_grid_finish: null output");
+    const size_t half = g->half();
+    const bool dy = on_device(y_half), dn = on_device(N_half);
+    const size_t ybytes = dy ? 0 : align256(half * sizeof(float2));
+    const size_t need = ybytes + (dn ? 0 : align256(half * sizeof(float)));
+    cudaError_t e = ensure_stage(g, need);
+    if (e != cudaSuccess) return cuda_fail(g, e, "spg_grid_finish: staging buffer");
+    float2 *yo = dy ? static_cast<float2 *>(y_half) : static_cast<float2 *>(g->stage);
+    float *no = dn ? N_half : reinterpret_cast<float *>(static_cast<char *>(g->stage) + ybytes);
+    finish_kernel<<<blocks_for((long long)half), kThreads, 0, g->stream>>>(g->n, g->acc, yo, no);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(g, e, "spg_grid_finish: launch");
+    if (!dy) {
+        e = cudaMemcpyAsync(y_half, yo, half * sizeof(float2), cudaMemcpyDeviceToHost, g->stream);
+        if (e != cudaSuccess) return cuda_fail(g, e, "spg_grid_finish: copy");
+    }
+    if (!dn) {
+        e = cudaMemcpyAsync(N_half, no, half * sizeof(float), cudaMemcpyDeviceToHost, g->stream);
+        if (e != cudaSuccess) return cuda_fail(g, e, "spg_grid_finish: copy");
+    }
+    e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "spg_grid_finish: synchronise");
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_grid_reset(spg_grid *g)
+{
+    if (!g) return gfail(nullptr, SPG_EINVAL, "spg_grid_reset: null accumulator");
+    cudaError_t e = cudaMemsetAsync(g->acc, 0, g->half() * 4 * sizeof(double), g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "spg_grid_reset");
+    g->images = 0;
+    return SPG_OK;
+}
+
+extern "C" long long spg_grid_count(const spg_grid *g) { return g ? g->images : 0; }
+
+extern "C" const char *spg_grid_last_error(const spg_grid *g) { return g ? g->err.c_str() : g_grid_err.c_str(); }
+
+extern "C" void spg_grid_destroy(spg_grid *g)
+{
+    if (!g) return;
+    cudaStreamSynchronize(g->stream);
+    if (g->acc) cudaFree(g->acc);
+    if (g->stage) cudaFree(g->stage);
+    delete g;
+}
 
 extern "C" const char *spg_backproject_last_error(void) { return g_grid_err.c_str(); }
 
 extern "C" spg_status spg_backproject(int n, int m, const float *rot, const void *X, const float *ctf,
                                       const float *pw, int kernel, float h, void *y_half, float *N_half, void *stream)
 {
-    if (n < 4 || n % 2 || m < 1 || !rot || !X || !ctf || !y_half || !N_half || (kernel != 0 && kernel != 1) ||
-        !(h > 0.f))
-        return grid_fail(SPG_EINVAL, "spg_backproject: bad arguments (even n >= 4, m >= 1, kernel 0 or 1, h > 0)");
-    if ((long long)n * n * n > (1LL << 31)) return grid_fail(SPG_EINVAL, "spg_backproject: volume too large");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const size_t vox = (size_t)n * n * n;
-    const size_t img = (size_t)m * n * n;
-    Buf re, im, nn, dR, dX, dC, dP;
-    cudaError_t e;
-#define GRID_CK(call)                                                                              \
-    do {                                                                                           \
-        e = (call);                                                                                \
-        if (e != cudaSuccess) {                                                                    \
-            cudaGetLastError();                                                                    \
-            return grid_fail(e == cudaErrorMemoryAllocation ? SPG_ENOMEM : SPG_ECUDA,              \
-                             std::string("spg_backproject: ") + cudaGetErrorString(e));            \
-        }                                                                                          \
-    } while (0)
-    GRID_CK(cudaMalloc(&re.p, vox * sizeof(double)));
-    GRID_CK(cudaMalloc(&im.p, vox * sizeof(double)));
-    GRID_CK(cudaMalloc(&nn.p, vox * sizeof(double)));
-    GRID_CK(cudaMalloc(&dR.p, (size_t)m * 9 * sizeof(float)));
-    GRID_CK(cudaMalloc(&dX.p, img * sizeof(float2)));
-    GRID_CK(cudaMalloc(&dC.p, img * sizeof(float)));
-    GRID_CK(cudaMemsetAsync(re.p, 0, vox * sizeof(double), s));
-    GRID_CK(cudaMemsetAsync(im.p, 0, vox * sizeof(double), s));
-    GRID_CK(cudaMemsetAsync(nn.p, 0, vox * sizeof(double), s));
-    GRID_CK(cudaMemcpyAsync(dR.p, rot, (size_t)m * 9 * sizeof(float), cudaMemcpyDefault, s));
-    GRID_CK(cudaMemcpyAsync(dX.p, X, img * sizeof(float2), cudaMemcpyDefault, s));
-    GRID_CK(cudaMemcpyAsync(dC.p, ctf, img * sizeof(float), cudaMemcpyDefault, s));
-    if (pw) {
-        GRID_CK(cudaMalloc(&dP.p, (size_t)m * sizeof(float)));
-        GRID_CK(cudaMemcpyAsync(dP.p, pw, (size_t)m * sizeof(float), cudaMemcpyDefault, s));
-    }
-    scatter_kernel<<<4864, 256, 0, s>>>(n, m, static_cast<float *>(dR.p), static_cast<float2 *>(dX.p),
-                                        static_cast<float *>(dC.p), static_cast<float *>(dP.p), kernel, h,
-                                        static_cast<double *>(re.p),
-                                        static_cast<double *>(im.p), static_cast<double *>(nn.p));
-    GRID_CK(cudaGetLastError());
-    const size_t half = (size_t)n * n * (n / 2 + 1);
-    Buf yo, no;
-    GRID_CK(cudaMalloc(&yo.p, half * sizeof(float2)));
-    GRID_CK(cudaMalloc(&no.p, half * sizeof(float)));
-    finalize_kernel<<<4864, 256, 0, s>>>(n, static_cast<double *>(re.p), static_cast<double *>(im.p),
-                                         static_cast<double *>(nn.p), static_cast<float2 *>(yo.p),
-                                         static_cast<float *>(no.p));
-    GRID_CK(cudaGetLastError());
-    GRID_CK(cudaMemcpyAsync(y_half, yo.p, half * sizeof(float2), cudaMemcpyDefault, s));
-    GRID_CK(cudaMemcpyAsync(N_half, no.p, half * sizeof(float), cudaMemcpyDefault, s));
-    GRID_CK(cudaStreamSynchronize(s));
-#undef GRID_CK
-    return SPG_OK;
+    spg_grid *g = nullptr;
+    spg_status s = spg_grid_create(n, kernel, h, stream, &g);
+    if (s != SPG_OK) return s;  // message already in g_grid_err
+    s = spg_grid_add(g, m, rot, X, ctf, pw);
+    if (s == SPG_OK) s = spg_grid_finish(g, y_half, N_half);
+    if (s != SPG_OK) g_grid_err = g->err;
+    spg_grid_destroy(g);
+    return s;
 }

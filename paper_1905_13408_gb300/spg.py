@@ -38,7 +38,8 @@ EXPORTS = ["spg_create", "spg_create_batch", "spg_set_data", "spg_set_x", "spg_g
            "spg_autotune", "spg_launch_count", "spg_plan_info", "spg_last_error", "spg_destroy",
            "spg_objective_noalloc", "spg_noalloc_last_error", "spg_set_anchor", "spg_param_scales",
            "spg_fsc", "spg_fsc_last_error", "spg_set_data_fourier", "spg_backproject",
-           "spg_backproject_last_error"]
+           "spg_backproject_last_error", "spg_grid_create", "spg_grid_add", "spg_grid_finish", "spg_grid_reset",
+           "spg_grid_count", "spg_grid_last_error", "spg_grid_destroy"]
 
 
 class SPGError(RuntimeError):
@@ -109,6 +110,13 @@ def load():
             "spg_set_data_fourier": (I, [P, I, V, V]),
             "spg_backproject": (I, [I, I, V, V, V, V, I, ctypes.c_float, V, V, P]),
             "spg_backproject_last_error": (ctypes.c_char_p, []),
+            "spg_grid_create": (I, [I, I, ctypes.c_float, P, PP]),
+            "spg_grid_add": (I, [P, I, V, V, V, V]),
+            "spg_grid_finish": (I, [P, V, V]),
+            "spg_grid_reset": (I, [P]),
+            "spg_grid_count": (LL, [P]),
+            "spg_grid_last_error": (ctypes.c_char_p, [P]),
+            "spg_grid_destroy": (None, [P]),
             "spg_param_scales": (I, [P, I, ctypes.POINTER(D)]),
         }
         for name, (res, args) in sigs.items():
@@ -217,25 +225,96 @@ def spg_set_data_fourier(h, vol, y_half, N_half):
     _check(load().spg_set_data_fourier(h, vol, py, pn), h)
 
 
+def _grid_inputs(rot, X, ctf, pw):
+    """Marshal (rot, X, ctf, pw) to pointers; numpy arrays become contiguous
+    float32 / complex64 host arrays, torch tensors are passed as they are."""
+    import torch
+    keep = []
+
+    def f32(a):
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float32 or not a.is_contiguous():
+                raise TypeError("expected a contiguous float32 tensor")
+            keep.append(a)
+            return ctypes.c_void_p(a.data_ptr())
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        keep.append(a)
+        return ctypes.c_void_p(a.ctypes.data)
+
+    pX, kX = _ptr_complex64(X)
+    keep.append(kX)
+    ptrs = (f32(rot), pX, f32(ctf), ctypes.c_void_p(0) if pw is None else f32(pw))
+    return ptrs, keep
+
+
+class Grid:
+    """Streaming kernel-regression back-projection (Sec. 2.2, Eq. 24-28):
+    add batches of image-pose pairs, then finish into the (y_half, N_half)
+    of the Fourier-domain data term."""
+
+    def __init__(self, n, kernel="gauss", h=2.0, stream=None):
+        self.n = int(n)
+        out = ctypes.c_void_p()
+        st = load().spg_grid_create(self.n, 0 if kernel == "gauss" else 1, float(h), ctypes.c_void_p(stream or 0),
+                                    ctypes.byref(out))
+        if st != SPG_OK:
+            raise SPGError(st, load().spg_grid_last_error(None).decode())
+        self.handle = out
+        self._keep = []
+
+    def _check(self, st):
+        if st != SPG_OK:
+            raise SPGError(st, load().spg_grid_last_error(self.handle).decode())
+
+    def add(self, rot, X, ctf, pw=None):
+        """rot [m, 3, 3], X [m, n, n] complex, ctf [m, n, n], pw [m] or None
+        (numpy arrays are staged through host memory; CUDA tensors are read
+        in place and kept alive until finish)."""
+        m = int(np.shape(rot)[0])
+        (pr, pX, pc, pp), keep = _grid_inputs(rot, X, ctf, pw)
+        self._check(load().spg_grid_add(self.handle, m, pr, pX, pc, pp))
+        self._keep.extend(keep)
+
+    def finish(self):
+        """(y_half complex64, N_half float32) CUDA tensors [n, n, n/2+1]."""
+        import torch
+        n = self.n
+        y = torch.empty((n, n, n // 2 + 1), dtype=torch.complex64, device="cuda")
+        N = torch.empty((n, n, n // 2 + 1), dtype=torch.float32, device="cuda")
+        self._check(load().spg_grid_finish(self.handle, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(N.data_ptr())))
+        self._keep = []
+        return y, N
+
+    def reset(self):
+        self._check(load().spg_grid_reset(self.handle))
+
+    def count(self):
+        return int(load().spg_grid_count(self.handle))
+
+    def close(self):
+        if self.handle:
+            load().spg_grid_destroy(self.handle)
+            self.handle = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def spg_backproject(rot, X, ctf, pw=None, kernel="gauss", h=2.0, stream=None):
     """(y_half complex64, N_half float32) on the GPU of m n x n images
     (rot [m, 3, 3], X [m, n, n] complex, ctf [m, n, n], optional posterior
     weights pw [m]); kernel "gauss" or "trilinear" (Sec. 2.2)."""
     import torch
-    rot = np.ascontiguousarray(rot, dtype=np.float32)
-    m, n = int(rot.shape[0]), int(X.shape[-1])
-    pX, kX = _ptr_complex64(X)
-    if isinstance(ctf, np.ndarray):
-        ctf = np.ascontiguousarray(ctf, dtype=np.float32)
-    pc, kc = _ptr(ctf)
-    pp = ctypes.c_void_p(0)
-    if pw is not None:
-        pw = np.ascontiguousarray(pw, dtype=np.float32)
-        pp = ctypes.c_void_p(pw.ctypes.data)
+    m, n = int(np.shape(rot)[0]), int(X.shape[-1])
+    (pr, pX, pc, pp), keep = _grid_inputs(rot, X, ctf, pw)
     y = torch.empty((n, n, n // 2 + 1), dtype=torch.complex64, device="cuda")
     N = torch.empty((n, n, n // 2 + 1), dtype=torch.float32, device="cuda")
-    st = load().spg_backproject(n, m, ctypes.c_void_p(rot.ctypes.data), pX, pc, pp, 0 if kernel == "gauss" else 1,
-                                float(h), ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(N.data_ptr()),
+    st = load().spg_backproject(n, m, pr, pX, pc, pp, 0 if kernel == "gauss" else 1, float(h),
+                                ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(N.data_ptr()),
                                 ctypes.c_void_p(stream or 0))
     if st != SPG_OK:
         raise SPGError(st, load().spg_backproject_last_error().decode())

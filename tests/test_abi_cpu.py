@@ -48,3 +48,17 @@ def test_bad_arguments_rejected_before_device_use():
     assert lib.spg_create(ctypes.byref(neg), None, None, ctypes.byref(h)) == spg.SPG_EINVAL
     assert lib.spg_reweight(None) == spg.SPG_EINVAL
     assert lib.spg_iterate(None, 3) == spg.SPG_EINVAL
+
+
+def test_grid_bad_arguments_rejected_before_device_use():
+    lib = spg.load()
+    g = ctypes.c_void_p()
+    assert lib.spg_grid_create(15, 0, 2.0, None, ctypes.byref(g)) == spg.SPG_EINVAL  # odd n
+    assert not g.value
+    assert b"even n" in lib.spg_grid_last_error(None)
+    assert lib.spg_grid_create(16, 2, 2.0, None, ctypes.byref(g)) == spg.SPG_EINVAL  # no kernel 2
+    assert lib.spg_grid_create(16, 0, 0.0, None, ctypes.byref(g)) == spg.SPG_EINVAL  # h = 0
+    assert lib.spg_grid_add(None, 1, None, None, None, None) == spg.SPG_EINVAL
+    assert lib.spg_grid_finish(None, None, None) == spg.SPG_EINVAL
+    assert lib.spg_grid_count(None) == 0
+    lib.spg_grid_destroy(None)

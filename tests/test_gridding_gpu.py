@@ -57,3 +57,27 @@ def test_images_to_regularised_map():
     print(f"pipeline 32^3, 120 images: rel-L2 vs oracle {err:.2e}, correlation with phantom {corr:.3f}")
     assert err <= 1e-5
     assert corr > 0.8
+
+
+def test_streaming_accumulator():
+    """Batches added to one accumulator (host arrays, CUDA tensors, a finish
+    in between) equal the one-shot back-projection; reset empties it."""
+    n, m = 20, 24
+    pd, rot, X, ctf = _inputs(n, m, 83)
+    pw = np.random.default_rng(84).uniform(0.2, 1.0, m).astype(np.float32)
+    y1, N1 = spg.spg_backproject(rot, X, ctf, pw=pw)
+    g = spg.Grid(n)
+    g.add(rot[:10], X[:10], ctf[:10], pw[:10])
+    g.finish()  # the sums stay
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    g.add(d(rot[10:17]), d(X[10:17]), d(ctf[10:17]), d(pw[10:17]))
+    g.add(rot[17:], X[17:], ctf[17:], pw[17:])
+    assert g.count() == m
+    y2, N2 = g.finish()
+    torch.testing.assert_close(N2, N1, rtol=1e-6, atol=1e-6 * float(N1.max()))
+    torch.testing.assert_close(y2, y1, rtol=1e-5, atol=1e-6 * float(y1.abs().max()))
+    g.reset()
+    assert g.count() == 0
+    y3, N3 = g.finish()
+    assert float(N3.abs().max()) == 0.0 and float(y3.abs().max()) == 0.0
+    g.close()
