@@ -164,7 +164,7 @@ def bytes_per_voxel(dtype, storage="delta"):
     return 4 + 4 + data + 4 + 4 + 4 + (4 if storage == "delta" else 0)
 
 
-def cpu_baseline(vol, hyper, nz_slab=64, iters=30):
+def cpu_baseline(vol, hyper, nz_slab=128, iters=100):
     """The FP64 oracle, as it stands, on a z-slab of the workload."""
     import numpy as np
 

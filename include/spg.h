@@ -105,9 +105,12 @@ typedef struct {
                                  O'Donoghue and Candes 2015); decided on the device every iteration */
 } spg_options;
 
-/* Tile codes for spg_options.tile: x extent = 32 * vx, y extent = ty. */
+/* Tile codes for spg_options.tile: x extent = 32 * vx, y extent = ty.
+ * SPG_TILE_128x7_S4 is the 128x7 tile with a 4-deep copy pipeline (3 is the
+ * default depth of that tile). */
 enum { SPG_TILE_AUTO = 0, SPG_TILE_128x8 = 1, SPG_TILE_128x4 = 2, SPG_TILE_64x8 = 3,
-       SPG_TILE_64x4 = 4, SPG_TILE_128x7 = 6, SPG_TILE_128x15 = 7, SPG_TILE_64x7 = 8 };
+       SPG_TILE_64x4 = 4, SPG_TILE_128x7 = 6, SPG_TILE_128x15 = 7, SPG_TILE_64x7 = 8,
+       SPG_TILE_128x7_S4 = 9 };
 
 /* Create a solver for one volume (spg_create) or for nvol independent
  * volumes of possibly different sizes advanced together, one fused launch per

@@ -643,6 +643,7 @@ struct Launcher {
 #define SPG_VARIANTS(X) \
     X(4, 8, 3, 2)       \
     X(4, 7, 3, 2)       \
+    X(4, 7, 4, 2)       \
     X(4, 15, 2, 1)      \
     X(4, 4, 4, 3)       \
     X(2, 8, 4, 2)       \

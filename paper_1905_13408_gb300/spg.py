@@ -26,7 +26,8 @@ SPG_OK, SPG_EINVAL, SPG_ENOMEM, SPG_ECUDA, SPG_ENOTREADY, SPG_ENONFINITE, SPG_ET
 SPG_F32, SPG_BF16 = 0, 1
 SPG_FISTA, SPG_ISTA = 0, 1
 SPG_STORE_DELTA, SPG_STORE_PREV = 0, 1
-TILES = {"auto": 0, "128x8": 1, "128x4": 2, "64x8": 3, "64x4": 4, "128x7": 6, "128x15": 7, "64x7": 8}
+TILES = {"auto": 0, "128x8": 1, "128x4": 2, "64x8": 3, "64x4": 4, "128x7": 6, "128x15": 7, "64x7": 8,
+         "128x7s4": 9}
 
 _STATUS_NAMES = {0: "SPG_OK", -1: "SPG_EINVAL", -2: "SPG_ENOMEM", -3: "SPG_ECUDA", -4: "SPG_ENOTREADY",
                  -5: "SPG_ENONFINITE", -6: "SPG_ETIMEOUT"}
