@@ -381,21 +381,31 @@ bool params_ok(const spg_volume_params &p)
            pos(p.eps) && pos(p.eps_tv) && (long long)p.nx * p.ny < (1LL << 31);
 }
 
+// Unpitched volumes move as one linear copy (row-by-row 2-D copies to or from
+// host memory run several times slower than a linear one).
 spg_status copy_volume_in(spg_ctx *ctx, void *dst_base, size_t es, const VolDesc &d, const void *src)
 {
     char *dst = static_cast<char *>(dst_base) + (size_t)d.off * es;
-    CK(cudaMemcpy2DAsync(dst, (size_t)d.pitch * es, src, (size_t)d.nx * es, (size_t)d.nx * es, (size_t)d.ny * d.nz,
-                         cudaMemcpyDefault, ctx->stream),
-       "copy volume in");
+    if (d.pitch == d.nx)
+        CK(cudaMemcpyAsync(dst, src, (size_t)d.nx * d.ny * d.nz * es, cudaMemcpyDefault, ctx->stream),
+           "copy volume in");
+    else
+        CK(cudaMemcpy2DAsync(dst, (size_t)d.pitch * es, src, (size_t)d.nx * es, (size_t)d.nx * es,
+                             (size_t)d.ny * d.nz, cudaMemcpyDefault, ctx->stream),
+           "copy volume in");
     return SPG_OK;
 }
 
 spg_status copy_volume_out(spg_ctx *ctx, void *dst, const void *src_base, size_t es, const VolDesc &d)
 {
     const char *src = static_cast<const char *>(src_base) + (size_t)d.off * es;
-    CK(cudaMemcpy2DAsync(dst, (size_t)d.nx * es, src, (size_t)d.pitch * es, (size_t)d.nx * es, (size_t)d.ny * d.nz,
-                         cudaMemcpyDefault, ctx->stream),
-       "copy volume out");
+    if (d.pitch == d.nx)
+        CK(cudaMemcpyAsync(dst, src, (size_t)d.nx * d.ny * d.nz * es, cudaMemcpyDefault, ctx->stream),
+           "copy volume out");
+    else
+        CK(cudaMemcpy2DAsync(dst, (size_t)d.nx * es, src, (size_t)d.pitch * es, (size_t)d.nx * es,
+                             (size_t)d.ny * d.nz, cudaMemcpyDefault, ctx->stream),
+           "copy volume out");
     return SPG_OK;
 }
 
