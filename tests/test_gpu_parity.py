@@ -69,7 +69,7 @@ def test_few_steps_odd_shapes(shape):
 
 
 @pytest.mark.parametrize("storage", ["delta", "prev"])
-@pytest.mark.parametrize("tile", ["128x8", "128x4", "64x8", "64x4", "128x7", "128x15", "64x7"])
+@pytest.mark.parametrize("tile", ["128x8", "128x4", "64x8", "64x4", "128x7", "128x7s4", "128x15", "64x7"])
 def test_tile_variants_agree(tile, storage):
     """Every compiled tile variant computes the same iterate (ragged 3-D shape)."""
     shape = (23, 45, 150)
@@ -126,6 +126,22 @@ def test_vol256_previous_iterate_storage(vol256_ref):
     print(f"vol256 prev rel-L2 {err:.3e}")
     assert err <= 2e-5
     np.testing.assert_allclose(hist[:, 4], ref.hist.reshape(-1, 4)[:, 3], rtol=1e-6)
+
+
+def test_vol512_first_iterations_match_oracle():
+    """The benchmark's 512^3 volume, default launch configuration, first 20
+    iterations of round 1 on the whole volume: iterate rel-L2 <= 1e-5 and
+    every recorded objective rel <= 1e-6 against the FP64 oracle (about
+    2.7e9 voxel-iterations of oracle work, ~10 GB of host memory)."""
+    vol, hyper, _, _ = synth.workload("vol512")
+    shape = vol.b.shape
+    x, hist, st, _ = gpu_solve(vol.b, vol.w, hyper, 1, 20)
+    ref = oracle.solve(vol.b, vol.w, oparams(shape, hyper), 1, 20)
+    err = rel_l2(x, ref.x)
+    print(f"512^3, 20 iterations: rel-L2 {err:.2e}")
+    assert err <= 1e-5
+    np.testing.assert_allclose(hist[:, 4], ref.hist[0, :, 3], rtol=1e-6)
+    np.testing.assert_allclose(st[0, 4:], ref.rstats[0, 4:], rtol=1e-6)
 
 
 def test_vol512_sampled_step():
