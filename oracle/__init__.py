@@ -43,7 +43,8 @@ class _P(ctypes.Structure):
                 ("lambda_l1", ctypes.c_double), ("lambda_tv", ctypes.c_double),
                 ("mu", ctypes.c_double), ("eps", ctypes.c_double), ("eps_tv", ctypes.c_double),
                 ("momentum", ctypes.c_int), ("restart", ctypes.c_int), ("gamma", ctypes.c_double),
-                ("anchor", ctypes.c_void_p)]
+                ("anchor", ctypes.c_void_p), ("forward", ctypes.c_int), ("periodic", ctypes.c_int),
+                ("post_div", ctypes.c_int)]
 
 
 @dataclass
@@ -58,6 +59,16 @@ class Params:
     restart: bool = False    # gradient restart of the extrapolation
     gamma: float = 0.0       # implicit-gradient term gamma |x - anchor|^2 (Eq. 22)
     anchor: np.ndarray = None
+    # alternative readings (the adopted ones are the defaults): Eq. 12's
+    # backward differences or forward ones; differences vanishing at the
+    # volume's edge (Neumann) or wrapping around it (periodic); the TV weight
+    # inside the divergence, D^T(omtv grad h), or after it as Eq. 20 prints it
+    difference: str = "backward"   # "backward" | "forward"
+    boundary: str = "neumann"      # "neumann" | "periodic"
+    tv_weight: str = "inside"      # "inside" | "post_div"
+
+    def adopted_readings(self):
+        return (self.difference, self.boundary, self.tv_weight) == ("backward", "neumann", "inside")
 
     def c(self):
         nz, ny, nx = self.shape
@@ -67,8 +78,12 @@ class Params:
             ptr = self._anchor.ctypes.data
         else:
             ptr = None
+        assert self.difference in ("backward", "forward") and self.boundary in ("neumann", "periodic")
+        assert self.tv_weight in ("inside", "post_div")
         return _P(nx, ny, nz, self.lambda_l1, self.lambda_tv, self.mu, self.eps, self.eps_tv,
-                  0 if self.momentum == "fista" else 1, 1 if self.restart else 0, self.gamma, ptr)
+                  0 if self.momentum == "fista" else 1, 1 if self.restart else 0, self.gamma, ptr,
+                  int(self.difference == "forward"), int(self.boundary == "periodic"),
+                  int(self.tv_weight == "post_div"))
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -233,7 +248,10 @@ def step(xk, xkm1, beta, tau, b, w, om1, omtv, p: Params):
 
 
 def step_sampled(xk, xkm1, beta, tau, b, w, om1, omtv, p: Params, idx):
-    """x_{k+1} at flat voxel indices ``idx``, each evaluated around that voxel."""
+    """x_{k+1} at flat voxel indices ``idx``, each evaluated around that voxel
+    (adopted readings only)."""
+    if not p.adopted_readings():
+        raise ValueError("step_sampled implements the adopted readings only")
     xk, xkm1, b, w = (_a(a, p.shape) for a in (xk, xkm1, b, w))
     o1, ot = _opt(om1, p.shape), _opt(omtv, p.shape)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
@@ -293,7 +311,10 @@ def certificate(y, xplus, tau, b, w, omtv, p: Params):
 
 
 def backward(b, w, om1, omtv, tau, iters, x0, gK, p: Params):
-    """(dL/db, dL/dw, (dL/dlambda_l1, dL/dlambda_tv)) through `iters` steps."""
+    """(dL/db, dL/dw, (dL/dlambda_l1, dL/dlambda_tv)) through `iters` steps
+    (adopted readings only)."""
+    if not p.adopted_readings():
+        raise ValueError("backward implements the adopted readings only")
     b, w, x0, gK = (_a(a, p.shape) for a in (b, w, x0, gK))
     o1, ot = _opt(om1, p.shape), _opt(omtv, p.shape)
     gb, gw, gs = np.empty(p.shape), np.empty(p.shape), np.zeros(2)

@@ -37,6 +37,10 @@
  *   x_{k+1} = soft(z, tau lambda_l1 om1)
  *
  * with tau = 1/L, L = max w + 12 lambda_tv max(omtv) / mu.
+ *
+ * Alternative readings of the paper are flags of orc_params (forward
+ * differences, periodic boundary, TV weight after the divergence); the
+ * per-voxel sampled step and the adjoint implement the adopted readings only.
  */
 #include <math.h>
 #include <stdint.h>
@@ -50,6 +54,12 @@ typedef struct {
     int restart;  /* 1: restart the extrapolation whenever <y_k - x_{k+1}, x_{k+1} - x_k> > 0 */
     double gamma;          /* weight of the implicit-gradient term gamma |x - anchor|^2 (Eq. 22) */
     const double *anchor;  /* the previous maximisation step's solution; used when gamma > 0 */
+    /* Alternative readings of the paper (the adopted ones are all 0):
+     * forward:  forward differences x_{v+e_a} - x_v instead of Eq. 12's backward ones;
+     * periodic: differences wrap around the volume instead of vanishing at its edge;
+     * post_div: the TV weight multiplies the divergence, omtv * D^T(grad h_mu(D x))
+     *           (Eq. 20 as printed), instead of D^T(omtv grad h_mu(D x)). */
+    int forward, periodic, post_div;
 } orc_params;
 
 #define NVOX(p) ((size_t)(p)->nx * (size_t)(p)->ny * (size_t)(p)->nz)
@@ -85,44 +95,85 @@ void orc_huber_grad(double z0, double z1, double z2, double mu, double out[3])
 
 /* ---------- linear operators (Eq. 12, Eq. 17) ---------- */
 
-/* g[a*n + v] = (Dx)_{v,a}, a = 0 (x), 1 (y), 2 (z); backward differences,
- * zero on the first plane of each axis (Neumann boundary). */
+/* Coordinate c of axis a (extent na) shifted by d, wrapped modulo na. */
+static int wrapc(int c, int d, int na) { return ((c + d) % na + na) % na; }
+
+/* Whether the difference of axis a at coordinate c exists (it is 0 otherwise):
+ * backward needs the voxel at c - 1, forward the voxel at c + 1; with the
+ * periodic boundary every difference exists. */
+static int has_diff(const orc_params *p, int c, int na)
+{
+    if (p->periodic) return 1;
+    return p->forward ? c + 1 <= na - 1 : c >= 1;
+}
+
+static size_t at_axis(const orc_params *p, int xx, int y, int z, int a, int c)
+{
+    if (a == 0) return AT(p, c, y, z);
+    if (a == 1) return AT(p, xx, c, z);
+    return AT(p, xx, y, c);
+}
+
+/* g[a*n + v] = (Dx)_{v,a}, a = 0 (x), 1 (y), 2 (z). Adopted reading: backward
+ * differences (Eq. 12), zero on the first plane of each axis (Neumann). */
 void orc_grad(const orc_params *p, const double *x, double *g)
 {
     const size_t n = NVOX(p);
+    const int ext[3] = {p->nx, p->ny, p->nz};
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; z++)
         for (int y = 0; y < p->ny; y++)
             for (int xx = 0; xx < p->nx; xx++) {
-                size_t v = AT(p, xx, y, z);
-                g[v]         = xx >= 1 ? x[v] - x[AT(p, xx - 1, y, z)] : 0.0;
-                g[n + v]     = y >= 1 ? x[v] - x[AT(p, xx, y - 1, z)] : 0.0;
-                g[2 * n + v] = z >= 1 ? x[v] - x[AT(p, xx, y, z - 1)] : 0.0;
+                const size_t v = AT(p, xx, y, z);
+                const int co[3] = {xx, y, z};
+                for (int a = 0; a < 3; a++) {
+                    const int c = co[a], na = ext[a];
+                    double d = 0.0;
+                    if (has_diff(p, c, na)) {
+                        if (p->forward)
+                            d = x[at_axis(p, xx, y, z, a, wrapc(c, 1, na))] - x[v];
+                        else
+                            d = x[v] - x[at_axis(p, xx, y, z, a, wrapc(c, -1, na))];
+                    }
+                    g[(size_t)a * n + v] = d;
+                }
             }
 }
 
-/* out = D^T u, the adjoint of orc_grad (Eq. 17 with the same boundary). */
+/* out = D^T u, the adjoint of orc_grad (Eq. 17 for the adopted reading): x_v
+ * enters the difference at v with sign +1 (backward) or -1 (forward), and the
+ * difference at its successor v + e_a (backward, sign -1) or predecessor
+ * v - e_a (forward, sign +1) whenever that difference exists. */
 void orc_div(const orc_params *p, const double *u, double *out)
 {
     const size_t n = NVOX(p);
+    const int ext[3] = {p->nx, p->ny, p->nz};
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; z++)
         for (int y = 0; y < p->ny; y++)
             for (int xx = 0; xx < p->nx; xx++) {
-                size_t v = AT(p, xx, y, z);
+                const size_t v = AT(p, xx, y, z);
+                const int co[3] = {xx, y, z};
                 double s = 0.0;
-                if (xx >= 1) s += u[v];
-                if (xx + 1 <= p->nx - 1) s -= u[AT(p, xx + 1, y, z)];
-                if (y >= 1) s += u[n + v];
-                if (y + 1 <= p->ny - 1) s -= u[n + AT(p, xx, y + 1, z)];
-                if (z >= 1) s += u[2 * n + v];
-                if (z + 1 <= p->nz - 1) s -= u[2 * n + AT(p, xx, y, z + 1)];
+                for (int a = 0; a < 3; a++) {
+                    const double *ua = u + (size_t)a * n;
+                    const int c = co[a], na = ext[a];
+                    if (!p->forward) {
+                        if (has_diff(p, c, na)) s += ua[v];
+                        if (p->periodic || c + 1 <= na - 1) s -= ua[at_axis(p, xx, y, z, a, wrapc(c, 1, na))];
+                    } else {
+                        if (has_diff(p, c, na)) s -= ua[v];
+                        if (p->periodic || c >= 1) s += ua[at_axis(p, xx, y, z, a, wrapc(c, -1, na))];
+                    }
+                }
                 out[v] = s;
             }
 }
 
 /* Gradient of the weighted smoothed TV term (without lambda_tv):
- * D^T(omtv * grad h_mu(D x)), Eq. 15-17 with the Eq. 11 weights inside. */
+ * D^T(omtv * grad h_mu(D x)), Eq. 15-17 with the Eq. 11 weights inside
+ * (with post_div: omtv * D^T(grad h_mu(D x)), which is not the gradient of
+ * any objective unless omtv is constant). */
 void orc_tv_grad(const orc_params *p, const double *x, const double *omtv, double *out)
 {
     const size_t n = NVOX(p);
@@ -132,12 +183,16 @@ void orc_tv_grad(const orc_params *p, const double *x, const double *omtv, doubl
     for (long long v = 0; v < (long long)n; v++) {
         double u[3];
         orc_huber_grad(g[v], g[n + v], g[2 * n + v], p->mu, u);
-        double om = omtv ? omtv[v] : 1.0;
+        double om = (omtv && !p->post_div) ? omtv[v] : 1.0;
         g[v] = om * u[0];
         g[n + v] = om * u[1];
         g[2 * n + v] = om * u[2];
     }
     orc_div(p, g, out);
+    if (p->post_div && omtv) {
+#pragma omp parallel for schedule(static)
+        for (long long v = 0; v < (long long)n; v++) out[v] *= omtv[v];
+    }
     free(g);
 }
 

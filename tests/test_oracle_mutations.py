@@ -14,20 +14,27 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_readings as readings
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "spg_oracle.c")
 
 MUTATIONS = {
-    "D^T without the first-plane gate": ("if (xx >= 1) s += u[v];", "s += u[v];"),
-    "forward instead of backward x-difference": (
-        "g[v]         = xx >= 1 ? x[v] - x[AT(p, xx - 1, y, z)] : 0.0;",
-        "g[v]         = xx + 1 < p->nx ? x[AT(p, xx + 1, y, z)] - x[v] : 0.0;"),
-    "y-difference taken along x": (
-        "g[n + v]     = y >= 1 ? x[v] - x[AT(p, xx, y - 1, z)] : 0.0;",
-        "g[n + v]     = xx >= 1 ? x[v] - x[AT(p, xx - 1, y, z)] : 0.0;"),
-    "first z-plane difference not zeroed": (
-        "g[2 * n + v] = z >= 1 ? x[v] - x[AT(p, xx, y, z - 1)] : 0.0;",
-        "g[2 * n + v] = z >= 1 ? x[v] - x[AT(p, xx, y, z - 1)] : x[v];"),
+    "D^T without the first-plane gate": ("if (has_diff(p, c, na)) s += ua[v];", "s += ua[v];"),
+    "backward difference taken forward": (
+        "d = x[v] - x[at_axis(p, xx, y, z, a, wrapc(c, -1, na))];",
+        "d = x[at_axis(p, xx, y, z, a, wrapc(c, 1, na))] - x[v];"),
+    "y neighbour taken along x": ("if (a == 1) return AT(p, xx, c, z);", "if (a == 1) return AT(p, c, y, z);"),
+    "first-plane difference not zeroed (wraps around)": ("return p->forward ? c + 1 <= na - 1 : c >= 1;",
+                                                         "return p->forward ? c + 1 <= na - 1 : c >= 0;"),
+    "TV weight dropped from the gradient": ("double om = (omtv && !p->post_div) ? omtv[v] : 1.0;",
+                                              "double om = 1.0;"),
+    "periodic D^T without the wrap-around term": (
+        "if (p->periodic || c + 1 <= na - 1) s -= ua[at_axis(p, xx, y, z, a, wrapc(c, 1, na))];",
+        "if (c + 1 <= na - 1) s -= ua[at_axis(p, xx, y, z, a, wrapc(c, 1, na))];"),
+    "forward-difference D^T with the wrong sign": ("if (has_diff(p, c, na)) s -= ua[v];",
+                                                   "if (has_diff(p, c, na)) s += ua[v];"),
+    "post-divergence weight applied twice": ("for (long long v = 0; v < (long long)n; v++) out[v] *= omtv[v];",
+                                             "for (long long v = 0; v < (long long)n; v++) out[v] *= omtv[v] * omtv[v];"),
     "Huber offset mu instead of mu/2": ("return s - 0.5 * mu;", "return s - mu;"),
     "Huber gradient not clipped to the unit ball": ("double d = s > mu ? s : mu;", "double d = mu;"),
     "soft-threshold shrinks by 2t": ("return z > 0.0 ? z - t : z + t;", "return z > 0.0 ? z - 2.0 * t : z + 2.0 * t;"),
@@ -77,6 +84,11 @@ QUICK = [
     pins.test_adjoint_matches_central_differences,
     pins.test_gradient_restart_converges_faster,
     pins.test_gamma_term_folds_into_data_and_weight,
+    lambda o: readings.test_div_is_the_adjoint_of_grad("forward", "neumann", (5, 7, 9)),
+    lambda o: readings.test_div_is_the_adjoint_of_grad("backward", "periodic", (5, 7, 9)),
+    lambda o: readings.test_div_is_the_adjoint_of_grad("forward", "periodic", (5, 7, 9)),
+    lambda o: readings.test_forward_differences_are_reversed_backward_ones(),
+    lambda o: readings.test_tv_weight_inside_is_a_gradient_and_post_div_is_not(),
 ]
 
 
