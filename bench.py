@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-gap", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--difference", default="backward", choices=["backward", "forward"])
+    ap.add_argument("--boundary", default="neumann", choices=["neumann", "periodic"])
+    ap.add_argument("--tv-weight", default="inside", choices=["inside", "post_div"])
     ap.add_argument("--full-schedule", action="store_true",
                     help="with --impl reference: time the oracle on the whole volume for the workload's "
                          "rounds x iterations (one line, no warm-up)")
@@ -341,9 +344,11 @@ def run_spg(args):
     hyper = dict(synth.DEFAULT_HYPER)
     nvox = vol.b.size
 
+    readings = dict(difference=args.difference, boundary=args.boundary, tv_weight=args.tv_weight)
+    adopted = readings == dict(difference="backward", boundary="neumann", tv_weight="inside")
     s = spg.SPG(dict(shape=vol.b.shape, **hyper), data_dtype=args.dtype, tile=args.tile, zchunk=args.zchunk,
                 stream=stream.cuda_stream, max_iters=max(100000, args.steps + args.warmup + 16),
-                hist_every=args.hist_every, storage=args.storage)
+                hist_every=args.hist_every, storage=args.storage, **readings)
     s.set_data(0, *dev_inputs(vol, args.dtype))
     s.reweight()
     s.iterate(args.warmup)
@@ -375,13 +380,16 @@ def run_spg(args):
     peaks, peak_kind = measured_peaks()
     bpv = bytes_per_voxel(args.dtype, args.storage)
     achieved = bpv * nvox / per_launch_s / 1e9
-    traffic = profiled_traffic(args.workload, args.dtype, args.storage)
+    traffic = profiled_traffic(args.workload, args.dtype, args.storage) if adopted else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": bpv * nvox,
-            "kernel": "spg_step_kernel (fused iteration + objective)"}
+            "kernel": "spg_step_kernel (fused iteration + objective)" if adopted
+            else "generic_step_kernel (alternative readings %s)" % readings}
 
     e2e = None
+    if not adopted:
+        args.no_e2e = args.no_gap = args.no_cpu_baseline = True
     if not args.no_e2e:
         e2e = measure_e2e(vol, hyper, args, stream)
     gap = None

@@ -103,7 +103,28 @@ typedef struct {
     int restart;              /* 0: fixed FISTA schedule (default); 1: gradient restart of the
                                  extrapolation (per volume, whenever <y_k - x_{k+1}, x_{k+1} - x_k> > 0,
                                  O'Donoghue and Candes 2015); decided on the device every iteration */
+    int readings;             /* 0: the adopted readings of the paper (the fused path); otherwise an
+                                 OR of SPG_READ_* flags, run by a plain two-pass path (below) */
 } spg_options;
+
+/* Alternative readings of the paper, for spg_options.readings. The adopted
+ * reading (0) takes Eq. 12's backward differences, which vanish where the
+ * neighbour lies outside the volume (the paper names no boundary), and puts
+ * the TV weight inside the divergence, D^T(omtv grad h_mu(D x)), the gradient
+ * of the weighted TV term of Eq. 11. The flags select instead:
+ *   SPG_READ_FORWARD   forward differences x_{v+e_a} - x_v (and their adjoint);
+ *   SPG_READ_PERIODIC  differences that wrap around the volume;
+ *   SPG_READ_POST_DIV  the weight after the divergence, omtv D^T(grad h_mu(D x)),
+ *                      as Eq. 20 prints it (not the gradient of any objective
+ *                      unless omtv is constant).
+ * They apply to the re-weighting (|D x|), the objective (TV term) and the
+ * iteration. A context with readings != 0 iterates with one plain kernel per
+ * step instead of the fused one (it re-evaluates the differences at every
+ * neighbour from global memory: about a ninth of the fused step's speed, a
+ * path for comparing readings, not for production) and needs float32 data
+ * with the real-space data term; restart, the certificate, the adjoint and
+ * autotuning are not available for it. */
+enum { SPG_READ_FORWARD = 1, SPG_READ_PERIODIC = 2, SPG_READ_POST_DIV = 4 };
 
 /* Tile codes for spg_options.tile: x extent = 32 * vx, y extent = ty.
  * SPG_TILE_128x7_S4 is the 128x7 tile with a 4-deep copy pipeline (3 is the

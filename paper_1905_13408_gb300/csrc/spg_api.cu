@@ -429,6 +429,26 @@ cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
             return cudaErrorUnknown;
         ctx->launches += 2;
     }
+    if (ctx->opt.readings) {
+        GenericParams g;
+        g.vols = ctx->vols_d;
+        g.plane_vol = ctx->plane_vol_d;
+        g.nplanes = ctx->nplanes;
+        g.nvol = ctx->nvol;
+        g.st = ctx->st_d;
+        g.plane_part = ctx->plane_part_d;
+        for (int q = 0; q < 4; q++) g.xbuf[q] = ctx->X[q];
+        g.xd = ctx->xd() ? 1 : 0;
+        g.b = static_cast<const float *>(ctx->B);
+        g.w = static_cast<const float *>(ctx->W);
+        g.om1 = ctx->OM1;
+        g.omtv = ctx->OMTV;
+        g.beta = ctx->beta_d;
+        g.hist = ctx->hist_d;
+        g.hist_cap = ctx->hist_cap;
+        g.hist_every = ctx->hist_every;
+        return launch_generic_step(g, ctx->stream);
+    }
     return step_launch(ctx->var, ctx->grid, p, ctx->stream);
 }
 
@@ -540,6 +560,14 @@ spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg
         delete ctx;
         return fail(nullptr, SPG_EINVAL, "spg_create: bad data dtype");
     }
+    if (ctx->opt.readings < 0 || ctx->opt.readings > (SPG_READ_FORWARD | SPG_READ_PERIODIC | SPG_READ_POST_DIV)) {
+        delete ctx;
+        return fail(nullptr, SPG_EINVAL, "spg_create: bad readings flags");
+    }
+    if (ctx->opt.readings && (ctx->opt.data_dtype != SPG_F32 || ctx->opt.restart)) {
+        delete ctx;
+        return fail(nullptr, SPG_EINVAL, "spg_create: alternative readings need float32 data and no restart");
+    }
     ctx->hist_every = ctx->opt.hist_every > 0 ? ctx->opt.hist_every : 1;
     ctx->hist_cap = ctx->opt.hist_capacity > 0 ? ctx->opt.hist_capacity : 4096;
     ctx->max_iters = ctx->opt.max_iters_per_round > 0 ? ctx->opt.max_iters_per_round : 100000;
@@ -574,6 +602,7 @@ spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg
         d.eps_tv = p.eps_tv;
         d.tau = 0.f;
         d.plane_begin = plane;
+        d.readings = ctx->opt.readings;
         ctx->vols_h.push_back(d);
         for (int z = 0; z < p.nz; z++) ctx->plane_vol_h.push_back(j);
         off += round_up((long long)d.pitch * d.ny * d.nz, 64);
@@ -717,6 +746,7 @@ spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol != 0 || ctx->nvol != 1 || !y_half || !N_half)
         return fail(ctx, SPG_EINVAL, "spg_set_data_fourier: single-volume contexts, vol = 0, non-null arrays");
+    if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_set_data_fourier: not available with alternative readings");
     if (ctx->bf16() || !ctx->xd())
         return fail(ctx, SPG_EINVAL, "spg_set_data_fourier: needs SPG_F32 storage and SPG_STORE_DELTA");
     const spg::CufftApi &cf = spg::cufft_api();
@@ -948,6 +978,7 @@ spg_status spg_certificate(spg_ctx *ctx, int vol, double *out)
 {
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_certificate: bad arguments");
+    if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_certificate: not available with alternative readings");
     if (!ctx->reweighted || ctx->k_round < 1)
         return fail(ctx, SPG_ENOTREADY, "spg_certificate: needs one iteration in the current round");
     if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_certificate: not available with the Fourier-domain data term");
@@ -1094,6 +1125,7 @@ spg_status spg_unrolled(spg_ctx *ctx, int K, float *xK)
     if (!ctx || !xK || K < 0) return fail(ctx, SPG_EINVAL, "spg_unrolled: bad arguments");
     if (ctx->nvol != 1) return fail(ctx, SPG_EINVAL, "spg_unrolled: single-volume contexts only");
     if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_unrolled: not available with the Fourier-domain data term");
+    if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_unrolled: not available with alternative readings");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_unrolled: call spg_reweight first");
     const VolDesc &d = ctx->vols_h[0];
     const size_t vb = (size_t)ctx->total * 4;
@@ -1122,6 +1154,7 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
     if (!ctx || !gx || !gb || !gw || !g_scalars || K < 1) return fail(ctx, SPG_EINVAL, "spg_backward: bad arguments");
     if (ctx->nvol != 1) return fail(ctx, SPG_EINVAL, "spg_backward: single-volume contexts only");
     if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_backward: not available with the Fourier-domain data term");
+    if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_backward: not available with alternative readings");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_backward: call spg_reweight first");
     const int C = ckpt_every > 0 ? ckpt_every : 10;
     const VolDesc &d = ctx->vols_h[0];
@@ -1289,6 +1322,7 @@ void cache_store(const std::string &key, int tile, int zchunk)
 spg_status spg_autotune(spg_ctx *ctx, int trial_iters, int info[6])
 {
     if (!ctx || trial_iters < 1) return fail(ctx, SPG_EINVAL, "spg_autotune: bad arguments");
+    if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_autotune: not available with alternative readings");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_autotune: call spg_reweight first");
     const std::string key = tune_key(ctx);
     int tile = 0, zc = 0;

@@ -291,18 +291,43 @@ struct Field {
     }
 };
 
-// D u at (x, y, z) in volume V (Eq. 12, zero first planes).
+// D u at (x, y, z) in volume V. Adopted reading: backward differences that
+// vanish on the first plane of each axis (Eq. 12); the SPG_READ_* flags of
+// the volume select forward differences and/or a periodic boundary.
 __device__ __forceinline__ void grad_at(const VolDesc &V, const Field &F, int x, int y, int z, float g[3])
 {
     const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
     const float xc = F.x(i), dc = F.d(i);
-    g[0] = x >= 1 ? (xc - F.x(i - 1)) + F.beta * (dc - F.d(i - 1)) : 0.f;
-    g[1] = y >= 1 ? (xc - F.x(i - V.pitch)) + F.beta * (dc - F.d(i - V.pitch)) : 0.f;
-    const long long ps = (long long)V.pitch * V.ny;
-    g[2] = z >= 1 ? (xc - F.x(i - ps)) + F.beta * (dc - F.d(i - ps)) : 0.f;
+    if (V.readings == 0) {
+        g[0] = x >= 1 ? (xc - F.x(i - 1)) + F.beta * (dc - F.d(i - 1)) : 0.f;
+        g[1] = y >= 1 ? (xc - F.x(i - V.pitch)) + F.beta * (dc - F.d(i - V.pitch)) : 0.f;
+        const long long ps = (long long)V.pitch * V.ny;
+        g[2] = z >= 1 ? (xc - F.x(i - ps)) + F.beta * (dc - F.d(i - ps)) : 0.f;
+        return;
+    }
+    const bool fwd = (V.readings & SPG_READ_FORWARD) != 0, per = (V.readings & SPG_READ_PERIODIC) != 0;
+    const int co[3] = {x, y, z}, ext[3] = {V.nx, V.ny, V.nz};
+    const long long stp[3] = {1, V.pitch, (long long)V.pitch * V.ny};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int c = co[a], n = ext[a];
+        long long j;
+        if (!fwd) {
+            if (c >= 1) j = i - stp[a];
+            else if (per && n > 1) j = i + (long long)(n - 1) * stp[a];
+            else { g[a] = 0.f; continue; }
+            g[a] = (xc - F.x(j)) + F.beta * (dc - F.d(j));
+        } else {
+            if (c + 1 <= n - 1) j = i + stp[a];
+            else if (per && n > 1) j = i - (long long)(n - 1) * stp[a];
+            else { g[a] = 0.f; continue; }
+            g[a] = (F.x(j) - xc) + F.beta * (F.d(j) - dc);
+        }
+    }
 }
 
-// p = omtv * D u / max(mu, |D u|) at (x, y, z); zero outside the volume.
+// p = omtv * D u / max(mu, |D u|) at (x, y, z) (without omtv under
+// SPG_READ_POST_DIV); zero outside the volume.
 __device__ __forceinline__ void p_at(const VolDesc &V, const Field &F, const float *omtv, int x, int y, int z,
                                      float p[3])
 {
@@ -314,21 +339,40 @@ __device__ __forceinline__ void p_at(const VolDesc &V, const Field &F, const flo
     grad_at(V, F, x, y, z, g);
     const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
     const float s2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-    const float sc = omtv[i] * fminf(1.0f / V.mu, rsqrtf(s2));
+    const float om = (V.readings & SPG_READ_POST_DIV) ? 1.0f : omtv[i];
+    const float sc = om * fminf(1.0f / V.mu, rsqrtf(s2));
     p[0] = g[0] * sc;
     p[1] = g[1] * sc;
     p[2] = g[2] * sc;
 }
 
-// (D^T p)(x, y, z) with p evaluated on the fly (Eq. 17).
+// (D^T p)(x, y, z) with p evaluated on the fly (Eq. 17 for the adopted
+// reading; the adjoint of the selected D otherwise, times omtv under
+// SPG_READ_POST_DIV).
 __device__ __forceinline__ float div_at(const VolDesc &V, const Field &F, const float *omtv, int x, int y, int z)
 {
     float pc[3], px[3], pyv[3], pz[3];
     p_at(V, F, omtv, x, y, z, pc);
-    p_at(V, F, omtv, x + 1, y, z, px);
-    p_at(V, F, omtv, x, y + 1, z, pyv);
-    p_at(V, F, omtv, x, y, z + 1, pz);
-    return (pc[0] - px[0]) + (pc[1] - pyv[1]) + (pc[2] - pz[2]);
+    if (V.readings == 0) {
+        p_at(V, F, omtv, x + 1, y, z, px);
+        p_at(V, F, omtv, x, y + 1, z, pyv);
+        p_at(V, F, omtv, x, y, z + 1, pz);
+        return (pc[0] - px[0]) + (pc[1] - pyv[1]) + (pc[2] - pz[2]);
+    }
+    const bool fwd = (V.readings & SPG_READ_FORWARD) != 0, per = (V.readings & SPG_READ_PERIODIC) != 0;
+    // neighbour along each axis: successor (backward D) or predecessor (forward D),
+    // wrapped under the periodic boundary, else possibly outside (p = 0 there)
+    auto nb = [&](int c, int n) {
+        const int d = fwd ? c - 1 : c + 1;
+        return per ? (d + n) % n : d;
+    };
+    p_at(V, F, omtv, nb(x, V.nx), y, z, px);
+    p_at(V, F, omtv, x, nb(y, V.ny), z, pyv);
+    p_at(V, F, omtv, x, y, nb(z, V.nz), pz);
+    float r = fwd ? (px[0] - pc[0]) + (pyv[1] - pc[1]) + (pz[2] - pc[2])
+                  : (pc[0] - px[0]) + (pc[1] - pyv[1]) + (pc[2] - pz[2]);
+    if (V.readings & SPG_READ_POST_DIV) r *= omtv[V.off + ((long long)z * V.ny + y) * V.pitch + x];
+    return r;
 }
 
 // ---------------- re-weighting (Eq. 11, eps scaling of Sec. 2.5) ----------------
@@ -546,6 +590,121 @@ __global__ void plain_step_kernel(const VolDesc *vols, const float *xk, const fl
     }
 }
 
+// ---------------- one iteration under alternative readings ----------------
+// The fused step's arithmetic for volumes with SPG_READ_* flags, written
+// plainly: one CTA per row segment of a z-plane; D^T(p) re-evaluates p at the
+// voxel and its three neighbours; the objective at x_k is summed when the
+// step records history. The last CTA writes the history entries, advances
+// each volume's extrapolation index and the device state, as the fused
+// kernel does, so the two paths are interchangeable between launches.
+__global__ void generic_step_kernel(GenericParams g)
+{
+    __shared__ double scratch[32 * 4];
+    __shared__ int flag, s_cur, s_rec, s_kr;
+    __shared__ long long s_kt;
+    if (threadIdx.x == 0) {
+        volatile DevState *st = g.st;
+        s_cur = st->cur;
+        s_kr = st->k_round;
+        s_kt = st->k_total;
+        s_rec = (g.hist_every > 0 && (s_kt % g.hist_every) == 0) ? 1 : 0;
+    }
+    __syncthreads();
+    const int cur = s_cur;
+    const bool rec = s_rec != 0;
+    const int nxt = g.xd ? (cur ^ 1) : (cur + 1) % 3;
+    auto pick = [&](int i) { return i == 0 ? g.xbuf[0] : (i == 1 ? g.xbuf[1] : (i == 2 ? g.xbuf[2] : g.xbuf[3])); };
+    const float *xk = pick(cur);
+    const float *aux = pick(g.xd ? 2 + cur : (cur + 2) % 3);
+    float *xout = pick(nxt);
+    float *dout = g.xd ? pick(2 + nxt) : nullptr;
+
+    const int plane = blockIdx.x / AUX_SEG;
+    const int vol = g.plane_vol[plane];
+    const VolDesc V = g.vols[vol];
+    const int z = plane - V.plane_begin;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
+    const float beta = g.beta[V.kmom];
+    const Field F{xk, g.xd ? nullptr : aux, beta, g.xd ? aux : nullptr};
+    const Field X0{xk, nullptr, 0.f};
+    const float tau = V.tau, tl1 = V.tau * V.lambda_l1, mu = V.mu;
+    KSum kd, kl, kt;
+    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
+        const int x = t % V.nx, y = r0 + t / V.nx;
+        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+        const float xc = xk[i], dc = F.d(i), wv = g.w[i], o1 = g.om1[i];
+        const float res = xc - g.b[i];
+        const float gtot = fmaf(V.lambda_tv, div_at(V, F, g.omtv, x, y, z), wv * fmaf(beta, dc, res));
+        const float delta = fmaf(beta, dc, -tau * gtot);
+        const float zz = xc + delta;
+        const float th = tl1 * o1;
+        const float inc = fabsf(zz) < th ? -xc : delta - copysignf(th, zz);
+        xout[i] = xc + inc;
+        if (dout) dout[i] = inc;
+        if (rec) {
+            float gq[3];
+            grad_at(V, X0, x, y, z, gq);
+            const float q = gq[0] * gq[0] + gq[1] * gq[1] + gq[2] * gq[2];
+            const float h = q <= mu * mu ? q * (0.5f / mu) : q * rsqrtf(q) - 0.5f * mu;
+            kd.add(0.5f * wv * res * res);
+            kl.add(o1 * fabsf(xc));
+            kt.add(g.omtv[i] * h);
+        }
+    }
+    if (rec) {
+        double sm[3] = {kd.value(), kl.value(), kt.value()};
+        block_sum<3>(sm, scratch);
+        if (threadIdx.x == 0) {
+            double *pp = g.plane_part + (long long)blockIdx.x * 4;
+            pp[0] = sm[0];
+            pp[1] = sm[1];
+            pp[2] = sm[2];
+        }
+    }
+    if (!last_block(&g.st->ticket, &flag)) return;
+    const int hslot = g.st->hist_count % g.hist_cap;
+    for (int v = 0; v < g.nvol; v++) {
+        const VolDesc W = g.vols[v];
+        if (rec) {
+            double c3[3] = {0, 0, 0};
+            for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG;
+                 q += blockDim.x) {
+                const double *pp = g.plane_part + (long long)q * 4;
+                c3[0] += __ldcg(pp + 0);
+                c3[1] += __ldcg(pp + 1);
+                c3[2] += __ldcg(pp + 2);
+            }
+            block_sum<3>(c3, scratch);
+            if (threadIdx.x == 0) {
+                double *h = g.hist + ((long long)hslot * g.nvol + v) * 5;
+                const double l1 = (double)W.lambda_l1 * c3[1], tv = (double)W.lambda_tv * c3[2];
+                const double tot = c3[0] + l1 + tv;
+                h[0] = (double)s_kt;
+                h[1] = c3[0];
+                h[2] = l1;
+                h[3] = tv;
+                h[4] = tot;
+                if (!isfinite(tot)) atomicCAS(&g.st->err, 0, (int)SPG_ENONFINITE);
+            }
+        }
+        if (threadIdx.x == 0) {
+            g.vols[v].beta_last = g.beta[W.kmom];
+            g.vols[v].kmom = W.kmom + 1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        DevState *st = g.st;
+        if (rec) st->hist_count = st->hist_count + 1;
+        st->cur = nxt;
+        st->k_round = s_kr + 1;
+        st->k_total = s_kt + 1;
+        st->ticket = 0;
+        __threadfence();
+    }
+}
+
 // ---------------- adjoint of one step ----------------
 // Pass 1: m = gnext * [soft-threshold passes], the l1 and TV scalar partials,
 // gb += tau w m, gw += -tau (y - b) m.
@@ -705,6 +864,12 @@ cudaError_t launch_plain_step(const VolDesc *vols, int nplanes, const float *xk,
                               float *xout, cudaStream_t s)
 {
     plain_step_kernel<<<nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(vols, xk, xkm1, beta, b, w, bf16, om1, omtv, xout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_generic_step(const GenericParams &g, cudaStream_t s)
+{
+    generic_step_kernel<<<g.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(g);
     return cudaGetLastError();
 }
 

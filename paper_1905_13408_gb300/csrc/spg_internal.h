@@ -31,7 +31,7 @@ struct VolDesc {
     int plane_begin;             // index of the volume's first z-plane among all planes
     int kmom;                    // index of the next step's extrapolation weight in the beta table
     float beta_last;             // extrapolation weight used by the last step
-    int pad0;
+    int readings;                // SPG_READ_* flags (0: the adopted readings, the fused path)
 };
 
 // One work item of the fused step: an x-y tile [x0, x0+TX) x [y0, y0+TY) of
@@ -136,6 +136,23 @@ cudaError_t launch_plain_step(const VolDesc *vols, int nplanes, const float *xk,
                               float beta, const void *b, const void *w, bool bf16, const float *om1,
                               const float *omtv, float *xout, cudaStream_t s);
 cudaError_t launch_timeout_probe(DevState *st, long long timeout_ns, cudaStream_t s);
+// One iteration under alternative readings (VolDesc.readings != 0): the fused
+// step's arithmetic in a plain kernel over row segments of every plane, with
+// the same device-state protocol (history, extrapolation index, buffers).
+struct GenericParams {
+    VolDesc *vols;
+    const int *plane_vol;
+    int nplanes, nvol;
+    DevState *st;
+    double *plane_part;       // [nplanes * AUX_SEG][4]
+    float *xbuf[4];           // iterate buffers (see StepParams)
+    int xd;                   // increment storage
+    const float *b, *w, *om1, *omtv;
+    const float *beta;
+    double *hist;
+    int hist_cap, hist_every;
+};
+cudaError_t launch_generic_step(const GenericParams &g, cudaStream_t s);
 // Fourier-domain data term (spg_fourier.cu), single float32 volume with increment storage.
 // y = x_k + beta d_k over the whole pitched volume (cur and beta read on the device).
 cudaError_t launch_form_y(const DevState *st, const VolDesc *vols, const float *beta, float *const *xbuf,

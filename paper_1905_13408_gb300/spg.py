@@ -55,11 +55,23 @@ class VolumeParams(ctypes.Structure):
                 ("eps", ctypes.c_float), ("eps_tv", ctypes.c_float)]
 
 
+SPG_READ_FORWARD, SPG_READ_PERIODIC, SPG_READ_POST_DIV = 1, 2, 4
+
+
+def readings_flags(difference="backward", boundary="neumann", tv_weight="inside"):
+    """SPG_READ_* flags of a choice of readings (0: the adopted ones)."""
+    if difference not in ("backward", "forward") or boundary not in ("neumann", "periodic") \
+            or tv_weight not in ("inside", "post_div"):
+        raise ValueError("difference: backward|forward, boundary: neumann|periodic, tv_weight: inside|post_div")
+    return ((SPG_READ_FORWARD if difference == "forward" else 0) | (SPG_READ_PERIODIC if boundary == "periodic" else 0)
+            | (SPG_READ_POST_DIV if tv_weight == "post_div" else 0))
+
+
 class Options(ctypes.Structure):
     _fields_ = [("data_dtype", ctypes.c_int), ("momentum", ctypes.c_int), ("hist_every", ctypes.c_int),
                 ("hist_capacity", ctypes.c_int), ("max_iters_per_round", ctypes.c_int), ("tile", ctypes.c_int),
                 ("zchunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("iterate_storage", ctypes.c_int),
-                ("restart", ctypes.c_int)]
+                ("restart", ctypes.c_int), ("readings", ctypes.c_int)]
 
 
 _lib = None
@@ -478,7 +490,7 @@ class SPG:
 
     def __init__(self, volumes, data_dtype="f32", momentum="fista", hist_every=1, hist_capacity=4096,
                  max_iters=100000, tile="auto", zchunk=0, ctas_per_sm=0, storage="delta", restart=False,
-                 stream=None):
+                 stream=None, difference="backward", boundary="neumann", tv_weight="inside"):
         if isinstance(volumes, dict):
             volumes = [volumes]
         self.shapes = [tuple(v["shape"]) for v in volumes]
@@ -486,7 +498,7 @@ class SPG:
         opt = Options(SPG_F32 if data_dtype == "f32" else SPG_BF16, SPG_FISTA if momentum == "fista" else SPG_ISTA,
                       hist_every, hist_capacity, max_iters, TILES[tile] if isinstance(tile, str) else int(tile),
                       zchunk, ctas_per_sm, SPG_STORE_DELTA if storage == "delta" else SPG_STORE_PREV,
-                      1 if restart else 0)
+                      1 if restart else 0, readings_flags(difference, boundary, tv_weight))
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
