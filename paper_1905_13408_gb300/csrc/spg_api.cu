@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -221,6 +222,23 @@ cudaError_t encode_map(CUtensorMap *m, CUtensorMapDataType dt, void *base, const
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Tensor maps of one volume for variant v: the iterate boxes of the given
+// buffers (null entries are left zero), then omtv, b, w and om1.
+cudaError_t encode_set(const spg_ctx *ctx, const VolDesc &d, const StepVariant &v, float *const xq[4], TmapSet *m)
+{
+    const int TX = 32 * v.vx, TY = v.ty;
+    const CUtensorMapDataType dt_data = v.bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    std::memset(m, 0, sizeof(*m));
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 4 && e == cudaSuccess; q++)
+        if (xq[q]) e = encode_map(&m->x[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, xq[q], d, 4, TX + 8, TY + 2);
+    if (e == cudaSuccess) e = encode_map(&m->omtv, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ctx->OMTV, d, 4, TX + 4, TY + 1);
+    if (e == cudaSuccess) e = encode_map(&m->b, dt_data, ctx->B, d, ctx->data_es(), TX, TY);
+    if (e == cudaSuccess) e = encode_map(&m->w, dt_data, ctx->W, d, ctx->data_es(), TX, TY);
+    if (e == cudaSuccess) e = encode_map(&m->om1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ctx->OM1, d, 4, TX, TY);
+    return e;
+}
+
 // Work plan: tensor maps for the variant's boxes, work items, grid size.
 spg_status build_plan(spg_ctx *ctx, const StepVariant &v, int zchunk_opt)
 {
@@ -270,17 +288,10 @@ spg_status build_plan(spg_ctx *ctx, const StepVariant &v, int zchunk_opt)
 
     // tensor maps
     std::vector<TmapSet> maps(ctx->nvol);
-    const CUtensorMapDataType dt_data = v.bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     for (int j = 0; j < ctx->nvol; j++) {
-        const VolDesc &d = ctx->vols_h[j];
-        TmapSet &m = maps[j];
-        std::memset(&m, 0, sizeof(m));
-        for (int q = 0; q < ctx->nalloc(); q++)
-            CK(encode_map(&m.x[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ctx->X[q], d, 4, TX + 8, TY + 2), "tensor map x");
-        CK(encode_map(&m.omtv, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ctx->OMTV, d, 4, TX + 4, TY + 1), "tensor map omtv");
-        CK(encode_map(&m.b, dt_data, ctx->B, d, ctx->data_es(), TX, TY), "tensor map b");
-        CK(encode_map(&m.w, dt_data, ctx->W, d, ctx->data_es(), TX, TY), "tensor map w");
-        CK(encode_map(&m.om1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ctx->OM1, d, 4, TX, TY), "tensor map om1");
+        float *xq[4] = {nullptr, nullptr, nullptr, nullptr};
+        for (int q = 0; q < ctx->nalloc(); q++) xq[q] = ctx->X[q];
+        CK(encode_set(ctx, ctx->vols_h[j], v, xq, &maps[j]), "tensor maps");
     }
 
     if (ctx->items_d) cudaFree(ctx->items_d);
@@ -529,6 +540,103 @@ std::vector<float> beta_table_host(const spg_ctx *ctx, int K)
     return b;
 }
 
+
+// Forward steps of the unrolled map through the fused kernel, on caller
+// buffers: previous-iterate storage, a private device state and a private
+// copy of the volume descriptor (the context's own state, history and
+// iterate buffers are untouched). Steps are planned first (add), their
+// tensor maps encoded and uploaded once (upload), then launched in order
+// (launch); step k uses the extrapolation weight beta_k.
+struct Sweep {
+    struct Entry {
+        float *xk, *xkm1, *xout;
+        int k;
+    };
+    spg_ctx *ctx;
+    StepVariant v;
+    Scratch sc;
+    DevState *st = nullptr;
+    VolDesc *vol = nullptr;
+    TmapSet *tm = nullptr;
+    std::vector<Entry> plan;
+    std::vector<int> kvals;  // extrapolation indices copied to the device (kept alive)
+    int launched = 0, kmom_dev = 0;
+
+    explicit Sweep(spg_ctx *c) : ctx(c), v(c->var) { v.xd = false; }
+    void add(float *xk, float *xkm1, float *xout, int k) { plan.push_back({xk, xkm1, xout, k}); }
+    cudaError_t upload()
+    {
+        int occ = 0;
+        cudaError_t e = step_configure(v, &occ);
+        if (e == cudaSuccess) e = sc.get(&st, sizeof(DevState));
+        if (e == cudaSuccess) e = sc.get(&vol, sizeof(VolDesc));
+        if (e == cudaSuccess) e = sc.get(&tm, std::max<size_t>(1, plan.size()) * sizeof(TmapSet));
+        if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(DevState), ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(vol, ctx->vols_d, sizeof(VolDesc), cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e != cudaSuccess) return e;
+        std::vector<TmapSet> h(plan.size());
+        for (size_t j = 0; j < plan.size(); j++) {
+            const int cur = (int)(j % 3);
+            float *xq[4] = {nullptr, nullptr, nullptr, nullptr};
+            xq[cur] = plan[j].xk;
+            xq[(cur + 2) % 3] = plan[j].xkm1;
+            if ((e = encode_set(ctx, ctx->vols_h[0], v, xq, &h[j])) != cudaSuccess) return e;
+        }
+        kvals.resize(plan.size());
+        if (!h.empty())
+            e = cudaMemcpyAsync(tm, h.data(), h.size() * sizeof(TmapSet), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // h goes out of scope
+        kmom_dev = -1;  // the copied descriptor's index is the context's: set before the first step
+        return e;
+    }
+    cudaError_t launch()
+    {
+        const Entry &E = plan[launched];
+        cudaError_t e = cudaSuccess;
+        if (kmom_dev != E.k) {
+            kvals[launched] = E.k;
+            e = cudaMemcpyAsync(reinterpret_cast<char *>(vol) + offsetof(VolDesc, kmom), &kvals[launched],
+                                sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+            if (e != cudaSuccess) return e;
+        }
+        const int cur = launched % 3;  // the private state's buffer index advances by one per step
+        StepParams p;
+        p.vols = vol;
+        p.items = ctx->items_d;
+        p.tmaps = tm + launched;
+        p.xbuf[cur] = E.xk;
+        p.xbuf[(cur + 2) % 3] = E.xkm1;
+        p.xbuf[(cur + 1) % 3] = E.xout;
+        p.xbuf[3] = nullptr;
+        p.beta = ctx->beta_d;
+        p.st = st;
+        p.partials = ctx->partials_d;
+        p.hist = ctx->hist_d;
+        p.nitems = ctx->nitems;
+        p.nvol = 1;
+        p.hist_cap = ctx->hist_cap;
+        p.hist_every = 0;  // no objective, no history
+        p.restart = 0;
+        p.fourier = 0;
+        p.timeout_ns = kTimeoutNs;
+        e = step_launch(v, ctx->grid, p, ctx->stream);
+        ctx->launches += 1;
+        launched++;
+        kmom_dev = E.k + 1;
+        return e;
+    }
+    // SPG_ETIMEOUT if a step gave up waiting for its copies (synchronises).
+    spg_status status()
+    {
+        int err = 0;
+        if (cudaMemcpyAsync(&err, reinterpret_cast<char *>(st) + offsetof(DevState, err), sizeof(int),
+                            cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            return SPG_ECUDA;
+        return err ? (spg_status)err : SPG_OK;
+    }
+};
 }  // namespace
 
 extern "C" {
@@ -1127,6 +1235,7 @@ spg_status spg_unrolled(spg_ctx *ctx, int K, float *xK)
     if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_unrolled: not available with the Fourier-domain data term");
     if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_unrolled: not available with alternative readings");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_unrolled: call spg_reweight first");
+    if (K > ctx->max_iters) return fail(ctx, SPG_EINVAL, "spg_unrolled: K above max_iters_per_round");
     const VolDesc &d = ctx->vols_h[0];
     const size_t vb = (size_t)ctx->total * 4;
     Scratch sc;
@@ -1134,16 +1243,17 @@ spg_status spg_unrolled(spg_ctx *ctx, int K, float *xK)
     for (int q = 0; q < 3; q++) CK(sc.get(&buf[q], vb), "alloc");
     CK(cudaMemcpyAsync(buf[0], ctx->X[ctx->cur()], vb, cudaMemcpyDeviceToDevice, ctx->stream), "copy x0");
     CK(cudaMemcpyAsync(buf[2], buf[0], vb, cudaMemcpyDeviceToDevice, ctx->stream), "copy x0");
-    const auto beta = beta_table_host(ctx, K);
+    Sweep sw(ctx);
     int c = 0;
     for (int k = 0; k < K; k++) {
-        CK(launch_plain_step(ctx->vols_d, d.nz, buf[c], buf[(c + 2) % 3], beta[k], ctx->B, ctx->W, ctx->bf16(),
-                             ctx->OM1, ctx->OMTV, buf[(c + 1) % 3], ctx->stream),
-           "plain step");
-        ctx->launches += 1;
+        sw.add(buf[c], buf[(c + 2) % 3], buf[(c + 1) % 3], k);
         c = (c + 1) % 3;
     }
-    spg_status s = copy_volume_out(ctx, xK, buf[c], 4, d);
+    CK(sw.upload(), "plan the unrolled steps");
+    for (int k = 0; k < K; k++) CK(sw.launch(), "fused step");
+    spg_status s = sw.status();
+    if (s != SPG_OK) return fail(ctx, s, "spg_unrolled: a fused step failed");
+    s = copy_volume_out(ctx, xK, buf[c], 4, d);
     if (s != SPG_OK) return s;
     return device_status(ctx);
 }
@@ -1156,6 +1266,7 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
     if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_backward: not available with the Fourier-domain data term");
     if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_backward: not available with alternative readings");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_backward: call spg_reweight first");
+    if (K > ctx->max_iters) return fail(ctx, SPG_EINVAL, "spg_backward: K above max_iters_per_round");
     const int C = ckpt_every > 0 ? ckpt_every : 10;
     const VolDesc &d = ctx->vols_h[0];
     const size_t vb = (size_t)ctx->total * 4;
@@ -1170,13 +1281,37 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
     CK(sc.get(&accb, vb), "alloc");
     CK(sc.get(&accw, vb), "alloc");
     CK(sc.get(&pp, (size_t)K * d.nz * AUX_SEG * 4 * sizeof(double)), "alloc scalar partials");
+    float *fG = nullptr, *fP = nullptr, *fH = nullptr;  // 3-vector scratch fields of the adjoint passes
+    CK(sc.get(&fG, vb * 3), "alloc");
+    CK(sc.get(&fP, vb * 3), "alloc");
+    CK(sc.get(&fH, vb * 3), "alloc");
     const auto beta = beta_table_host(ctx, K);
     auto vol_at = [&](float *base, int i) { return base + (size_t)i * ctx->total; };
 
+    // Plan every forward step through the fused kernel: the sweep from x_0
+    // (three rotating buffers, checkpoints of (x_k, x_{k-1}) copied out every
+    // C steps) and, per segment in reverse order, the recomputation of the
+    // segment's iterates from its checkpoint into seg[1..].
+    Sweep sw(ctx);
+    float *b3[3];
+    for (int q = 0; q < 3; q++) b3[q] = vol_at(seg, q);
+    {
+        int c = 0;
+        for (int k = 0; k < K; k++) {
+            sw.add(b3[c], b3[(c + 2) % 3], b3[(c + 1) % 3], k);
+            c = (c + 1) % 3;
+        }
+        for (int sgm = nck - 1; sgm >= 0; sgm--) {
+            const int k0 = sgm * C, k1 = std::min(K, k0 + C);
+            for (int k = k0; k < k1 - 1; k++) {
+                const int i = k - k0 + 1;
+                sw.add(vol_at(seg, i), vol_at(seg, i - 1), vol_at(seg, i + 1), k);
+            }
+        }
+    }
+    CK(sw.upload(), "plan the forward steps");
     // forward sweep, keeping (x_k, x_{k-1}) at every checkpoint
     {
-        float *b3[3];
-        for (int q = 0; q < 3; q++) b3[q] = vol_at(seg, q);
         CK(cudaMemcpyAsync(b3[0], ctx->X[ctx->cur()], vb, cudaMemcpyDeviceToDevice, ctx->stream), "copy x0");
         CK(cudaMemcpyAsync(b3[2], b3[0], vb, cudaMemcpyDeviceToDevice, ctx->stream), "copy x0");
         int c = 0;
@@ -1187,10 +1322,7 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
                                    ctx->stream),
                    "ckpt");
             }
-            CK(launch_plain_step(ctx->vols_d, d.nz, b3[c], b3[(c + 2) % 3], beta[k], ctx->B, ctx->W, ctx->bf16(),
-                                 ctx->OM1, ctx->OMTV, b3[(c + 1) % 3], ctx->stream),
-               "plain step");
-            ctx->launches += 1;
+            CK(sw.launch(), "fused step");
             c = (c + 1) % 3;
         }
     }
@@ -1208,13 +1340,7 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
         // seg[0] = x_{k0-1}, seg[1] = x_{k0}, seg[i+1] = x_{k0+i}
         CK(cudaMemcpyAsync(vol_at(seg, 0), vol_at(ck, 2 * sgm + 1), vb, cudaMemcpyDeviceToDevice, ctx->stream), "rst");
         CK(cudaMemcpyAsync(vol_at(seg, 1), vol_at(ck, 2 * sgm), vb, cudaMemcpyDeviceToDevice, ctx->stream), "rst");
-        for (int k = k0; k < k1 - 1; k++) {
-            const int i = k - k0 + 1;
-            CK(launch_plain_step(ctx->vols_d, d.nz, vol_at(seg, i), vol_at(seg, i - 1), beta[k], ctx->B, ctx->W,
-                                 ctx->bf16(), ctx->OM1, ctx->OMTV, vol_at(seg, i + 1), ctx->stream),
-               "recompute");
-            ctx->launches += 1;
-        }
+        for (int k = k0; k < k1 - 1; k++) CK(sw.launch(), "recompute");
         for (int k = k1 - 1; k >= k0; k--) {
             const int i = k - k0 + 1;
             AdjParams a;
@@ -1236,9 +1362,13 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
             a.gb = accb;
             a.gw = accw;
             a.plane_part = pp + (size_t)k * d.nz * AUX_SEG * 4;
+            a.G = fG;
+            a.P = fP;
+            a.HQ = fH;
+            a.stride = ctx->total;
             CK(launch_adjoint_mask(a, ctx->stream), "adjoint mask");
             CK(launch_adjoint_apply(a, ctx->stream), "adjoint apply");
-            ctx->launches += 2;
+            ctx->launches += 4;
             // rotate: dL/dx_k is complete; the old dL/dx_{k+1} buffer becomes dL/dx_{k-2}
             const int t = inext;
             inext = icur;

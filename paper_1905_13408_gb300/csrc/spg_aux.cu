@@ -706,8 +706,55 @@ __global__ void generic_step_kernel(GenericParams g)
 }
 
 // ---------------- adjoint of one step ----------------
-// Pass 1: m = gnext * [soft-threshold passes], the l1 and TV scalar partials,
-// gb += tau w m, gw += -tau (y - b) m.
+// Four passes over row segments, each a plain stencil of radius one on fields
+// the previous pass stored (component a of a 3-vector field at a * stride):
+//   1. G = D y and P = omtv grad h_mu(G) at every voxel;
+//   2. tvg = D^T P, the step's z, the soft-threshold mask m = gnext [pass],
+//      the l1 / TV scalar partials, gb += tau w m, gw += -tau (y - b) m;
+//   3. HQ = omtv H_mu(G) D m, H_mu = I/mu inside the smoothing ball and
+//      (I - e e^T)/|G| outside (the Hessian of Eq. 14);
+//   4. ybar = m - tau (w m + lambda_tv D^T HQ); gcur += (1+beta) ybar,
+//      gprev += -beta ybar.
+// The values equal those of evaluating every quantity on the fly at each
+// neighbour; storing them makes each pass a handful of loads per voxel.
+__device__ __forceinline__ long long lin(const VolDesc &V, int x, int y, int z)
+{
+    return V.off + ((long long)z * V.ny + y) * V.pitch + x;
+}
+
+__global__ void adjoint_grad_kernel(AdjParams a)
+{
+    const VolDesc V = a.vols[0];
+    const int z = blockIdx.x / AUX_SEG;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
+    const Field F{a.xk, a.xkm1, a.beta};
+    const long long S = a.stride;
+    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
+        const int x = t % V.nx, y = r0 + t / V.nx;
+        const long long i = lin(V, x, y, z);
+        float g[3];
+        grad_at(V, F, x, y, z, g);
+        const float s2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        const float sc = a.omtv[i] * fminf(1.0f / V.mu, rsqrtf(s2));
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            a.G[c * S + i] = g[c];
+            a.P[c * S + i] = g[c] * sc;
+        }
+    }
+}
+
+// sum_a f_a(v) - f_a(v + e_a), with f = 0 beyond the volume (Eq. 17).
+__device__ __forceinline__ float div_stored(const VolDesc &V, const float *f, long long S, int x, int y, int z)
+{
+    const long long i = lin(V, x, y, z);
+    const float fx = x + 1 < V.nx ? f[i + 1] : 0.f;
+    const float fy = y + 1 < V.ny ? f[S + i + V.pitch] : 0.f;
+    const float fz = z + 1 < V.nz ? f[2 * S + i + (long long)V.pitch * V.ny] : 0.f;
+    return (f[i] - fx) + (f[S + i] - fy) + (f[2 * S + i] - fz);
+}
+
 __global__ void adjoint_mask_kernel(AdjParams a)
 {
     __shared__ double scratch[32 * 4];
@@ -715,14 +762,13 @@ __global__ void adjoint_mask_kernel(AdjParams a)
     const int z = blockIdx.x / AUX_SEG;
     int r0, r1;
     seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
-    const Field F{a.xk, a.xkm1, a.beta};
     KSum k1, k2;
     for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
         const int x = t % V.nx, y = r0 + t / V.nx;
-        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+        const long long i = lin(V, x, y, z);
         const float d = a.xk[i] - a.xkm1[i];
         const float bv = ld_data(a.b, a.bf16, i), wv = ld_data(a.w, a.bf16, i);
-        const float tvg = div_at(V, F, a.omtv, x, y, z);
+        const float tvg = div_stored(V, a.P, a.stride, x, y, z);
         const float g = wv * ((a.xk[i] - bv) + a.beta * d) + V.lambda_tv * tvg;
         const float delta = a.beta * d - V.tau * g;
         const float zz = a.xk[i] + delta;
@@ -744,57 +790,52 @@ __global__ void adjoint_mask_kernel(AdjParams a)
     }
 }
 
-// omtv * H_mu(D y) (D m) at (x, y, z), zero outside; H_mu = I/mu inside the
-// smoothing ball, (I - e e^T)/|Dy| outside (the Hessian of Eq. 14).
-__device__ __forceinline__ void hv_at(const VolDesc &V, const Field &F, const float *m, const float *omtv, int x,
-                                      int y, int z, float h[3])
+__global__ void adjoint_hq_kernel(AdjParams a)
 {
-    if (x < 0 || y < 0 || z < 0 || x >= V.nx || y >= V.ny || z >= V.nz) {
-        h[0] = h[1] = h[2] = 0.f;
-        return;
-    }
-    float g[3];
-    grad_at(V, F, x, y, z, g);
-    const Field M{m, nullptr, 0.f};
-    float q[3];
-    grad_at(V, M, x, y, z, q);
-    const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
-    const float s = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-    const float om = omtv[i];
-    if (s <= V.mu) {
-        const float c = om / V.mu;
-        h[0] = q[0] * c;
-        h[1] = q[1] * c;
-        h[2] = q[2] * c;
-    } else {
-        const float inv = 1.0f / s;
-        const float e0 = g[0] * inv, e1 = g[1] * inv, e2 = g[2] * inv;
-        const float eq = e0 * q[0] + e1 * q[1] + e2 * q[2];
-        const float c = om * inv;
-        h[0] = (q[0] - e0 * eq) * c;
-        h[1] = (q[1] - e1 * eq) * c;
-        h[2] = (q[2] - e2 * eq) * c;
+    const VolDesc V = a.vols[0];
+    const int z = blockIdx.x / AUX_SEG;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
+    const Field M{a.m, nullptr, 0.f};
+    const long long S = a.stride;
+    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
+        const int x = t % V.nx, y = r0 + t / V.nx;
+        const long long i = lin(V, x, y, z);
+        float q[3];
+        grad_at(V, M, x, y, z, q);
+        const float g0 = a.G[i], g1 = a.G[S + i], g2 = a.G[2 * S + i];
+        const float s = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
+        const float om = a.omtv[i];
+        float h[3];
+        if (s <= V.mu) {
+            const float c = om / V.mu;
+            h[0] = q[0] * c;
+            h[1] = q[1] * c;
+            h[2] = q[2] * c;
+        } else {
+            const float inv = 1.0f / s;
+            const float e0 = g0 * inv, e1 = g1 * inv, e2 = g2 * inv;
+            const float eq = e0 * q[0] + e1 * q[1] + e2 * q[2];
+            const float c = om * inv;
+            h[0] = (q[0] - e0 * eq) * c;
+            h[1] = (q[1] - e1 * eq) * c;
+            h[2] = (q[2] - e2 * eq) * c;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) a.HQ[c * S + i] = h[c];
     }
 }
 
-// Pass 2: ybar = m - tau (w m + lambda_tv D^T(omtv H Dm)); gcur += (1+beta) ybar,
-// gprev += -beta ybar.
 __global__ void adjoint_apply_kernel(AdjParams a)
 {
     const VolDesc V = a.vols[0];
     const int z = blockIdx.x / AUX_SEG;
     int r0, r1;
     seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
-    const Field F{a.xk, a.xkm1, a.beta};
     for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
         const int x = t % V.nx, y = r0 + t / V.nx;
-        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
-        float hc[3], hx[3], hy[3], hz[3];
-        hv_at(V, F, a.m, a.omtv, x, y, z, hc);
-        hv_at(V, F, a.m, a.omtv, x + 1, y, z, hx);
-        hv_at(V, F, a.m, a.omtv, x, y + 1, z, hy);
-        hv_at(V, F, a.m, a.omtv, x, y, z + 1, hz);
-        const float dtv = (hc[0] - hx[0]) + (hc[1] - hy[1]) + (hc[2] - hz[2]);
+        const long long i = lin(V, x, y, z);
+        const float dtv = div_stored(V, a.HQ, a.stride, x, y, z);
         const float mv = a.m[i];
         const float ybar = mv - V.tau * (ld_data(a.w, a.bf16, i) * mv + V.lambda_tv * dtv);
         a.gcur[i] += (1.f + a.beta) * ybar;
@@ -875,12 +916,14 @@ cudaError_t launch_generic_step(const GenericParams &g, cudaStream_t s)
 
 cudaError_t launch_adjoint_mask(const AdjParams &a, cudaStream_t s)
 {
+    adjoint_grad_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a);
     adjoint_mask_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_apply(const AdjParams &a, cudaStream_t s)
 {
+    adjoint_hq_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a);
     adjoint_apply_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }

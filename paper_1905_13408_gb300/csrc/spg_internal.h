@@ -129,8 +129,12 @@ struct AdjParams {
     float *m;                // scratch volume: masked cotangent of z
     float *gcur, *gprev, *gb, *gw;
     double *plane_part;      // [nplanes * AUX_SEG][4]
+    float *G, *P, *HQ;       // scratch 3-vector fields, component c at c * stride
+    long long stride;
 };
+// Pass 1 and 2 of the adjoint (D y and p; mask, scalars, gb, gw): two kernels.
 cudaError_t launch_adjoint_mask(const AdjParams &a, cudaStream_t s);
+// Pass 3 and 4 (H D m; ybar and the cotangent update): two kernels.
 cudaError_t launch_adjoint_apply(const AdjParams &a, cudaStream_t s);
 cudaError_t launch_plain_step(const VolDesc *vols, int nplanes, const float *xk, const float *xkm1,
                               float beta, const void *b, const void *w, bool bf16, const float *om1,
