@@ -1,12 +1,13 @@
 // Auxiliary kernels of the GB300 SPG solver: input validation and dtype
 // conversion, the re-weighting pass (Eq. 11), the objective (Eq. 14 / 31),
-// the strong-convexity certificate, a plain (untiled) step used to recompute
-// forward iterates, and the two passes of the adjoint of one step.
+// the strong-convexity certificate, the passes of the adjoint of one step,
+// and the plain step used under alternative readings of the paper.
 //
-// All of them run once per round or less, so they use plain global loads;
-// every reduction keeps one partial per z-plane (one CTA per plane) and the
-// last CTA to finish sums the partials of each volume in plane order, so the
-// results are deterministic. No kernel here waits on another CTA.
+// None of them is on the fused hot path, so they use plain global loads;
+// each runs AUX_SEG CTAs per z-plane (one per row segment), every reduction
+// keeps one partial per segment, and the last CTA to finish sums the
+// partials of each volume in segment order, so the results are
+// deterministic. No kernel here waits on another CTA.
 #include <cuda_bf16.h>
 
 #include "spg_internal.h"
@@ -567,29 +568,6 @@ __global__ void certificate_kernel(AuxParams a, const float *xplus, const float 
     }
 }
 
-// ---------------- plain step (forward recomputation for the adjoint) ----------------
-__global__ void plain_step_kernel(const VolDesc *vols, const float *xk, const float *xkm1, float beta,
-                                  const void *b, const void *w, bool bf16, const float *om1, const float *omtv,
-                                  float *xout)
-{
-    const VolDesc V = vols[0];
-    const int z = blockIdx.x / AUX_SEG;
-    int r0, r1;
-    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
-    const Field F{xk, xkm1, beta};
-    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
-        const int x = t % V.nx, y = r0 + t / V.nx;
-        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
-        const float d = xk[i] - xkm1[i];
-        const float g = ld_data(w, bf16, i) * ((xk[i] - ld_data(b, bf16, i)) + beta * d) +
-                        V.lambda_tv * div_at(V, F, omtv, x, y, z);
-        const float delta = beta * d - V.tau * g;
-        const float zz = xk[i] + delta;
-        const float th = V.tau * V.lambda_l1 * om1[i];
-        xout[i] = fabsf(zz) < th ? 0.f : xk[i] + (zz > 0.f ? delta - th : delta + th);
-    }
-}
-
 // ---------------- one iteration under alternative readings ----------------
 // The fused step's arithmetic for volumes with SPG_READ_* flags, written
 // plainly: one CTA per row segment of a z-plane; D^T(p) re-evaluates p at the
@@ -897,14 +875,6 @@ cudaError_t launch_certificate(const AuxParams &a, const float *const *xbuf, con
 {
     certificate_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a, xbuf[0], xbuf[1], xbuf[2], xbuf[3], beta, b, w, bf16,
                                                          omtv);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_plain_step(const VolDesc *vols, int nplanes, const float *xk, const float *xkm1, float beta,
-                              const void *b, const void *w, bool bf16, const float *om1, const float *omtv,
-                              float *xout, cudaStream_t s)
-{
-    plain_step_kernel<<<nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(vols, xk, xkm1, beta, b, w, bf16, om1, omtv, xout);
     return cudaGetLastError();
 }
 

@@ -136,9 +136,6 @@ struct AdjParams {
 cudaError_t launch_adjoint_mask(const AdjParams &a, cudaStream_t s);
 // Pass 3 and 4 (H D m; ybar and the cotangent update): two kernels.
 cudaError_t launch_adjoint_apply(const AdjParams &a, cudaStream_t s);
-cudaError_t launch_plain_step(const VolDesc *vols, int nplanes, const float *xk, const float *xkm1,
-                              float beta, const void *b, const void *w, bool bf16, const float *om1,
-                              const float *omtv, float *xout, cudaStream_t s);
 cudaError_t launch_timeout_probe(DevState *st, long long timeout_ns, cudaStream_t s);
 // One iteration under alternative readings (VolDesc.readings != 0): the fused
 // step's arithmetic in a plain kernel over row segments of every plane, with
