@@ -4,6 +4,9 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <functional>
+#include <numeric>
+#include <queue>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -61,6 +64,7 @@ struct spg_ctx {
 
     VolDesc *vols_d = nullptr;
     WorkItem *items_d = nullptr;
+    int *sched_d = nullptr;   // per-CTA item ranges (grid + 1) then the item order
     TmapSet *tmaps_d = nullptr;
     int *plane_vol_d = nullptr;
     float *X[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -153,7 +157,7 @@ void free_all(spg_ctx *c)
     void *fs[] = {c->Ybuf, c->Fh, c->Yh, c->Nh, c->Ch, c->Nmax, c->fpart};
     for (void *p : fs)
         if (p) cudaFree(p);
-    void *ps[] = {c->vols_d, c->items_d, c->tmaps_d, c->plane_vol_d, c->X[0], c->X[1], c->X[2], c->X[3], c->B, c->W,
+    void *ps[] = {c->vols_d, c->items_d, c->sched_d, c->tmaps_d, c->plane_vol_d, c->X[0], c->X[1], c->X[2], c->X[3], c->B, c->W,
                   c->OM1, c->OMTV, c->beta_d, c->st_d, c->partials_d, c->hist_d, c->plane_part_d,
                   c->vol_out_d, c->maxw_d, c->rstats_d};
     for (void *p : ps)
@@ -239,6 +243,44 @@ cudaError_t encode_set(const spg_ctx *ctx, const VolDesc &d, const StepVariant &
     return e;
 }
 
+// Work of an item in plane steps: its planes plus the two-plane prologue of
+// the copy pipeline.
+long long item_cost(int z0, int z1) { return (long long)(z1 - z0) + 2; }
+
+// Longest-processing-time-first assignment of items to G CTAs: each item,
+// longest first, goes to the least-loaded CTA (lowest index on ties). Returns
+// the makespan in plane steps; with order/first given, fills the items of
+// CTA g as order[first[g] .. first[g+1]), longest first.
+long long lpt_schedule(const std::vector<long long> &cost, int G, std::vector<int> *order, std::vector<int> *first)
+{
+    const int n = (int)cost.size();
+    std::vector<int> idx(n);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    using Slot = std::pair<long long, int>;
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+    for (int g = 0; g < G; g++) heap.push({0, g});
+    std::vector<int> owner(order ? n : 0);
+    long long makespan = 0;
+    for (int i : idx) {
+        Slot sl = heap.top();
+        heap.pop();
+        sl.first += cost[i];
+        makespan = std::max(makespan, sl.first);
+        if (order) owner[i] = sl.second;
+        heap.push(sl);
+    }
+    if (order) {
+        first->assign(G + 1, 0);
+        for (int i = 0; i < n; i++) (*first)[owner[i] + 1]++;
+        for (int g = 0; g < G; g++) (*first)[g + 1] += (*first)[g];
+        order->assign(n, 0);
+        std::vector<int> pos(first->begin(), first->end() - 1);
+        for (int i : idx) (*order)[pos[owner[i]]++] = i;
+    }
+    return makespan;
+}
+
 // Work plan: tensor maps for the variant's boxes, work items, grid size.
 spg_status build_plan(spg_ctx *ctx, const StepVariant &v, int zchunk_opt)
 {
@@ -256,18 +298,44 @@ spg_status build_plan(spg_ctx *ctx, const StepVariant &v, int zchunk_opt)
         columns += cols;
         plane_tiles += cols * d.nz;
     }
-    // Planes per work item: one wave of equal items when every column fits
-    // (each column split into slots/columns chunks), else ~4 items per slot.
+    // Planes per work item: the z-chunk whose items, scheduled longest first
+    // over the resident CTAs, give the shortest makespan (one wave of equal
+    // items when every column fits; finer chunks balance uneven batches).
+    auto costs_for = [&](int chunk) {
+        std::vector<long long> c;
+        for (const auto &d : ctx->vols_h) {
+            const long long cols = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY);
+            const int nch = (d.nz + chunk - 1) / chunk;
+            for (int q = 0; q < nch; q++) {
+                const int z0 = (int)((long long)d.nz * q / nch), z1 = (int)((long long)d.nz * (q + 1) / nch);
+                if (z1 > z0) c.insert(c.end(), cols, item_cost(z0, z1));
+            }
+        }
+        return c;
+    };
+    int maxnz = 0;
+    for (const auto &d : ctx->vols_h) maxnz = std::max(maxnz, d.nz);
     int chunk;
     if (zchunk_opt > 0) {
         chunk = zchunk_opt;
-    } else if (columns <= slots) {
-        const long long nch = std::max<long long>(1, slots / columns);
-        int maxnz = 0;
-        for (const auto &d : ctx->vols_h) maxnz = std::max(maxnz, d.nz);
-        chunk = (int)((maxnz + nch - 1) / nch);
     } else {
-        chunk = (int)std::max<long long>(8, plane_tiles / (slots * 4));
+        std::vector<int> cand = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+        for (int k = 1; k <= 16; k++) cand.push_back((maxnz + k - 1) / k);
+        if (columns <= slots) cand.push_back((int)((maxnz + std::max<long long>(1, slots / columns) - 1) /
+                                                   std::max<long long>(1, slots / columns)));
+        long long best = -1;
+        chunk = maxnz;
+        for (int c : cand) {
+            if (c < 1 || c > maxnz) continue;
+            if (plane_tiles / c > 400000) continue;  // keep the plan small
+            const auto cost = costs_for(c);
+            const int G = (int)std::min<long long>((long long)cost.size(), slots);
+            const long long ms = lpt_schedule(cost, G, nullptr, nullptr);
+            if (best < 0 || ms < best || (ms == best && c > chunk)) {
+                best = ms;
+                chunk = c;
+            }
+        }
     }
     chunk = std::max(1, chunk);
 
@@ -294,10 +362,24 @@ spg_status build_plan(spg_ctx *ctx, const StepVariant &v, int zchunk_opt)
         CK(encode_set(ctx, ctx->vols_h[j], v, xq, &maps[j]), "tensor maps");
     }
 
+    // schedule: CTA g runs items order[first[g] .. first[g+1])
+    const int G = (int)std::min<long long>((long long)items.size(), slots);
+    std::vector<long long> cost(items.size());
+    for (size_t i = 0; i < items.size(); i++) cost[i] = item_cost(items[i].z0, items[i].z1);
+    std::vector<int> order, first;
+    lpt_schedule(cost, G, &order, &first);
+    std::vector<int> sched(first);
+    sched.insert(sched.end(), order.begin(), order.end());
+
     if (ctx->items_d) cudaFree(ctx->items_d);
     if (ctx->partials_d) cudaFree(ctx->partials_d);
+    if (ctx->sched_d) cudaFree(ctx->sched_d);
     ctx->items_d = nullptr;
     ctx->partials_d = nullptr;
+    ctx->sched_d = nullptr;
+    CK(dalloc(&ctx->sched_d, sched.size() * sizeof(int)), "alloc schedule");
+    CK(cudaMemcpyAsync(ctx->sched_d, sched.data(), sched.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream),
+       "upload schedule");
     CK(dalloc(&ctx->items_d, items.size() * sizeof(WorkItem)), "alloc items");
     CK(dalloc(&ctx->partials_d, items.size() * 4 * sizeof(double)), "alloc partials");
     CK(cudaMemcpyAsync(ctx->items_d, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
@@ -325,7 +407,7 @@ spg_status build_plan(spg_ctx *ctx, const StepVariant &v, int zchunk_opt)
     ctx->items_h = items;
     ctx->nitems = (int)items.size();
     ctx->ctas_per_sm = occ;
-    ctx->grid = (int)std::min<long long>(ctx->nitems, slots);
+    ctx->grid = G;
     if (ctx->gexec) {
         cudaGraphExecDestroy(ctx->gexec);
         ctx->gexec = nullptr;
@@ -338,6 +420,7 @@ StepParams step_params(const spg_ctx *c)
     StepParams p;
     p.vols = c->vols_d;
     p.items = c->items_d;
+    p.sched = c->sched_d;
     p.tmaps = c->tmaps_d;
     for (int q = 0; q < 4; q++) p.xbuf[q] = c->X[q];
     p.beta = c->beta_d;
@@ -604,6 +687,7 @@ struct Sweep {
         StepParams p;
         p.vols = vol;
         p.items = ctx->items_d;
+        p.sched = ctx->sched_d;
         p.tmaps = tm + launched;
         p.xbuf[cur] = E.xk;
         p.xbuf[(cur + 2) % 3] = E.xkm1;

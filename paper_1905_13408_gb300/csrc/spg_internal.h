@@ -65,6 +65,7 @@ struct DevState {
 struct StepParams {
     const VolDesc *vols;
     const WorkItem *items;
+    const int *sched;        // CTA g runs items sched[G+1+p] for p in [sched[g], sched[g+1]), G = gridDim.x
     const TmapSet *tmaps;
     float *xbuf[4];
     const float *beta;       // extrapolation table beta_k (float32)

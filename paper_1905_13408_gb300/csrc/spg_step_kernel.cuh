@@ -519,7 +519,8 @@ __global__ void __launch_bounds__(32 * (TY + 1), MINB)
     float *const xout_base = pick(nxt);
     float *const dout_base = XD ? pick(2 + nxt) : nullptr;
     if (tid == 0) {
-        const TmapSet *tm = P.tmaps + P.items[blockIdx.x < (unsigned)P.nitems ? blockIdx.x : 0].vol;
+        const int p0 = P.sched[blockIdx.x];
+        const TmapSet *tm = P.tmaps + P.items[P.sched[gridDim.x + 1 + (p0 < P.nitems ? p0 : 0)]].vol;
         prefetch_tmap(&tm->x[ia]);
         prefetch_tmap(&tm->x[ib]);
         prefetch_tmap(&tm->omtv);
@@ -530,7 +531,9 @@ __global__ void __launch_bounds__(32 * (TY + 1), MINB)
 
     Pipe pipe{0, 0, 0};
     bool aborted = false;
-    for (int it = blockIdx.x; it < P.nitems && !aborted; it += gridDim.x) {
+    const int p1 = P.sched[blockIdx.x + 1];
+    for (int p = P.sched[blockIdx.x]; p < p1 && !aborted; p++) {
+        const int it = P.sched[gridDim.x + 1 + p];
         const WorkItem W = P.items[it];
         bool done = false;
         if constexpr (!BF16 && XD) {
