@@ -58,7 +58,8 @@ typedef enum {
     SPG_ECUDA = -3,       /* CUDA runtime / driver error */
     SPG_ENOTREADY = -4,   /* call order violated (e.g. iterate before set_data/reweight) */
     SPG_ENONFINITE = -5,  /* a non-finite objective value or input was detected */
-    SPG_ETIMEOUT = -6     /* a bounded device-side wait gave up (context stays usable) */
+    SPG_ETIMEOUT = -6,    /* a bounded device-side wait gave up (context stays usable) */
+    SPG_ECHECK = -7       /* an index check of the checked build (-DSPG_CHECK) failed */
 } spg_status;
 
 typedef enum { SPG_F32 = 0, SPG_BF16 = 1 } spg_dtype;

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "spg.h"
+#include "spg_trace.h"
 #include "spg_cufft.h"
 #include "spg_internal.h"
 
@@ -424,6 +425,7 @@ StepParams step_params(const spg_ctx *c)
     p.tmaps = c->tmaps_d;
     for (int q = 0; q < 4; q++) p.xbuf[q] = c->X[q];
     p.beta = c->beta_d;
+    p.beta_len = c->max_iters;
     p.st = c->st_d;
     p.partials = c->partials_d;
     p.hist = c->hist_d;
@@ -462,6 +464,12 @@ spg_status device_status(spg_ctx *ctx)
         cudaStreamSynchronize(ctx->stream);
         if (st.err == SPG_ETIMEOUT) return fail(ctx, SPG_ETIMEOUT, "a device-side wait timed out");
         if (st.err == SPG_ENONFINITE) return fail(ctx, SPG_ENONFINITE, "non-finite objective value");
+        if (st.err == SPG_ECHECK) {
+            unsigned zero_u = 0;
+            cudaMemcpyAsync(&ctx->st_d->err_info, &zero_u, sizeof(unsigned), cudaMemcpyHostToDevice, ctx->stream);
+            cudaStreamSynchronize(ctx->stream);
+            return fail(ctx, SPG_ECHECK, "index check " + std::to_string(st.err_info) + " failed (checked build)");
+        }
         return fail(ctx, (spg_status)st.err, "device error");
     }
     return SPG_OK;
@@ -694,6 +702,7 @@ struct Sweep {
         p.xbuf[(cur + 1) % 3] = E.xout;
         p.xbuf[3] = nullptr;
         p.beta = ctx->beta_d;
+        p.beta_len = ctx->max_iters;
         p.st = st;
         p.partials = ctx->partials_d;
         p.hist = ctx->hist_d;
@@ -728,6 +737,7 @@ extern "C" {
 spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg_options *opt, void *stream,
                             spg_ctx **out)
 {
+    SPG_TRACE();
     if (!out || !params || nvol < 1) return fail(nullptr, SPG_EINVAL, "spg_create: bad arguments");
     *out = nullptr;
     for (int j = 0; j < nvol; j++)
@@ -878,11 +888,13 @@ spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg
 
 spg_status spg_create(const spg_volume_params *params, const spg_options *opt, void *stream, spg_ctx **out)
 {
+    SPG_TRACE();
     return spg_create_batch(1, params, opt, stream, out);
 }
 
 spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg_dtype src)
 {
+    SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !b || !w) return fail(ctx, SPG_EINVAL, "spg_set_data: bad arguments");
     if (src != SPG_F32 && src != SPG_BF16) return fail(ctx, SPG_EINVAL, "spg_set_data: bad dtype");
@@ -935,6 +947,7 @@ spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg
 
 spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const float *N_half)
 {
+    SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol != 0 || ctx->nvol != 1 || !y_half || !N_half)
         return fail(ctx, SPG_EINVAL, "spg_set_data_fourier: single-volume contexts, vol = 0, non-null arrays");
@@ -1000,6 +1013,7 @@ spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const
 
 spg_status spg_set_anchor(spg_ctx *ctx, int vol, float gamma, const float *x_anchor)
 {
+    SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !x_anchor || !(gamma >= 0.f) || !std::isfinite(gamma))
         return fail(ctx, SPG_EINVAL, "spg_set_anchor: bad arguments");
@@ -1019,6 +1033,7 @@ spg_status spg_set_anchor(spg_ctx *ctx, int vol, float gamma, const float *x_anc
 
 spg_status spg_param_scales(spg_ctx *ctx, int vol, double out[4])
 {
+    SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_param_scales: bad arguments");
     if (!ctx->data_set[vol]) return fail(ctx, SPG_ENOTREADY, "spg_param_scales: call spg_set_data first");
@@ -1036,6 +1051,7 @@ spg_status spg_param_scales(spg_ctx *ctx, int vol, double out[4])
 
 spg_status spg_set_x(spg_ctx *ctx, int vol, const float *x)
 {
+    SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !x) return fail(ctx, SPG_EINVAL, "spg_set_x: bad arguments");
     const VolDesc &d = ctx->vols_h[vol];
@@ -1060,6 +1076,7 @@ spg_status spg_set_x(spg_ctx *ctx, int vol, const float *x)
 
 spg_status spg_get_x(spg_ctx *ctx, int vol, float *x)
 {
+    SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !x) return fail(ctx, SPG_EINVAL, "spg_get_x: bad arguments");
     return copy_volume_out(ctx, x, ctx->X[ctx->cur()], 4, ctx->vols_h[vol]);
@@ -1067,6 +1084,7 @@ spg_status spg_get_x(spg_ctx *ctx, int vol, float *x)
 
 spg_status spg_reweight(spg_ctx *ctx)
 {
+    SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     for (int j = 0; j < ctx->nvol; j++)
         if (!ctx->data_set[j]) return fail(ctx, SPG_ENOTREADY, "spg_reweight: data not set for every volume");
@@ -1081,6 +1099,7 @@ spg_status spg_reweight(spg_ctx *ctx)
 
 spg_status spg_iterate(spg_ctx *ctx, int k)
 {
+    SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (k < 0) return fail(ctx, SPG_EINVAL, "spg_iterate: negative count");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_iterate: call spg_reweight first");
@@ -1095,6 +1114,7 @@ spg_status spg_iterate(spg_ctx *ctx, int k)
 
 spg_status spg_objective(spg_ctx *ctx, int vol, double out[4])
 {
+    SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_objective: bad arguments");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_objective: weights not set (call spg_reweight)");
@@ -1135,6 +1155,7 @@ spg_status spg_objective(spg_ctx *ctx, int vol, double out[4])
 
 spg_status spg_history(spg_ctx *ctx, int vol, double *host, int max_entries, int *n)
 {
+    SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !n || max_entries < 0 || (max_entries > 0 && !host))
         return fail(ctx, SPG_EINVAL, "spg_history: bad arguments");
@@ -1159,6 +1180,7 @@ spg_status spg_history(spg_ctx *ctx, int vol, double *host, int max_entries, int
 
 spg_status spg_round_stats(spg_ctx *ctx, int vol, double out[6])
 {
+    SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_round_stats: bad arguments");
     CK(cudaMemcpyAsync(out, ctx->rstats_d + (size_t)vol * 6, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
@@ -1168,6 +1190,7 @@ spg_status spg_round_stats(spg_ctx *ctx, int vol, double out[6])
 
 spg_status spg_certificate(spg_ctx *ctx, int vol, double *out)
 {
+    SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_certificate: bad arguments");
     if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_certificate: not available with alternative readings");
@@ -1193,6 +1216,7 @@ spg_status spg_certificate(spg_ctx *ctx, int vol, double *out)
 
 spg_status spg_counters(spg_ctx *ctx, long long *k_total, int *k_round)
 {
+    SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (k_total) *k_total = ctx->k_total;
     if (k_round) *k_round = ctx->k_round;
@@ -1203,6 +1227,7 @@ spg_status spg_counters(spg_ctx *ctx, long long *k_total, int *k_round)
 
 spg_status spg_get_state(spg_ctx *ctx, void *blob, size_t *size)
 {
+    SPG_TRACE();
     if (!ctx || !size) return fail(ctx, SPG_EINVAL, "spg_get_state: bad arguments");
     size_t need = sizeof(StateHeader);
     for (const auto &d : ctx->vols_h)
@@ -1251,6 +1276,7 @@ spg_status spg_get_state(spg_ctx *ctx, void *blob, size_t *size)
 
 spg_status spg_set_state(spg_ctx *ctx, const void *blob, size_t size)
 {
+    SPG_TRACE();
     if (!ctx || !blob) return fail(ctx, SPG_EINVAL, "spg_set_state: bad arguments");
     size_t need = 0;
     spg_get_state(ctx, nullptr, &need);
@@ -1314,6 +1340,7 @@ spg_status spg_set_state(spg_ctx *ctx, const void *blob, size_t size)
 
 spg_status spg_unrolled(spg_ctx *ctx, int K, float *xK)
 {
+    SPG_TRACE();
     if (!ctx || !xK || K < 0) return fail(ctx, SPG_EINVAL, "spg_unrolled: bad arguments");
     if (ctx->nvol != 1) return fail(ctx, SPG_EINVAL, "spg_unrolled: single-volume contexts only");
     if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_unrolled: not available with the Fourier-domain data term");
@@ -1345,6 +1372,7 @@ spg_status spg_unrolled(spg_ctx *ctx, int K, float *xK)
 spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *gw, double g_scalars[2],
                         int ckpt_every)
 {
+    SPG_TRACE();
     if (!ctx || !gx || !gb || !gw || !g_scalars || K < 1) return fail(ctx, SPG_EINVAL, "spg_backward: bad arguments");
     if (ctx->nvol != 1) return fail(ctx, SPG_EINVAL, "spg_backward: single-volume contexts only");
     if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_backward: not available with the Fourier-domain data term");
@@ -1480,6 +1508,7 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
 
 spg_status spg_probe_timeout(spg_ctx *ctx, long long timeout_ns)
 {
+    SPG_TRACE();
     if (!ctx || timeout_ns <= 0 || timeout_ns > kTimeoutNs) return fail(ctx, SPG_EINVAL, "spg_probe_timeout: bad arguments");
     CK(launch_timeout_probe(ctx->st_d, timeout_ns, ctx->stream), "timeout probe");
     ctx->launches += 1;
@@ -1535,6 +1564,7 @@ void cache_store(const std::string &key, int tile, int zchunk)
 
 spg_status spg_autotune(spg_ctx *ctx, int trial_iters, int info[6])
 {
+    SPG_TRACE();
     if (!ctx || trial_iters < 1) return fail(ctx, SPG_EINVAL, "spg_autotune: bad arguments");
     if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_autotune: not available with alternative readings");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_autotune: call spg_reweight first");
@@ -1633,6 +1663,7 @@ long long spg_launch_count(const spg_ctx *ctx) { return ctx ? ctx->launches : 0;
 
 spg_status spg_plan_info(const spg_ctx *ctx, int info[6])
 {
+    SPG_TRACE();
     if (!ctx || !info) return SPG_EINVAL;
     info[0] = 32 * ctx->var.vx;
     info[1] = ctx->var.ty;
@@ -1647,6 +1678,7 @@ const char *spg_last_error(const spg_ctx *ctx) { return ctx ? ctx->err.c_str() :
 
 void spg_destroy(spg_ctx *ctx)
 {
+    SPG_TRACE();
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
     free_all(ctx);

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "spg.h"
+#include "spg_trace.h"
 #include "spg_cufft.h"
 
 namespace {
@@ -119,6 +120,7 @@ extern "C" const char *spg_fsc_last_error(void) { return g_fsc_err.c_str(); }
 extern "C" spg_status spg_fsc(int n, const float *a, const float *b, int max_shells, double *fsc, double *counts,
                               void *stream)
 {
+    SPG_TRACE();
     if (n < 2 || !a || !b || !fsc || max_shells < n / 2 + 1)
         return fsc_fail(SPG_EINVAL, "spg_fsc: bad arguments (n >= 2, max_shells >= n/2 + 1)");
     if ((long long)n * n * n > (1LL << 31)) return fsc_fail(SPG_EINVAL, "spg_fsc: volume too large");

@@ -27,6 +27,7 @@
 #include <string>
 
 #include "spg.h"
+#include "spg_trace.h"
 
 namespace {
 
@@ -228,6 +229,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 extern "C" spg_status spg_grid_create(int n, int kernel, float h, void *stream, spg_grid **out)
 {
+    SPG_TRACE();
     if (!out) return gfail(nullptr, SPG_EINVAL, "spg_grid_create: null output");
     *out = nullptr;
     if (n < 4 || n % 2 || (kernel != 0 && kernel != 1) || !(h > 0.f))
@@ -253,6 +255,7 @@ extern "C" spg_status spg_grid_create(int n, int kernel, float h, void *stream, 
 extern "C" spg_status spg_grid_add(spg_grid *g, int m, const float *rot, const void *X, const float *ctf,
                                    const float *pw)
 {
+    SPG_TRACE();
     if (!g) return gfail(nullptr, SPG_EINVAL, "spg_grid_add: null accumulator");
     if (m < 1 || !rot || !X || !ctf) return gfail(g, SPG_EINVAL, "spg_grid_add: m >= 1 and non-null arrays");
     const int n = g->n;
@@ -297,6 +300,7 @@ extern "C" spg_status spg_grid_add(spg_grid *g, int m, const float *rot, const v
 
 extern "C" spg_status spg_grid_finish(spg_grid *g, void *y_half, float *N_half)
 {
+    SPG_TRACE();
     if (!g) return gfail(nullptr, SPG_EINVAL, "spg_grid_finish: null accumulator");
     if (!y_half || !N_half) return gfail(g, SPG_EINVAL, "spg_grid_finish: null output");
     const size_t half = g->half();
@@ -325,6 +329,7 @@ extern "C" spg_status spg_grid_finish(spg_grid *g, void *y_half, float *N_half)
 
 extern "C" spg_status spg_grid_reset(spg_grid *g)
 {
+    SPG_TRACE();
     if (!g) return gfail(nullptr, SPG_EINVAL, "spg_grid_reset: null accumulator");
     cudaError_t e = cudaMemsetAsync(g->acc, 0, g->half() * 4 * sizeof(double), g->stream);
     if (e != cudaSuccess) return cuda_fail(g, e, "spg_grid_reset");
@@ -338,6 +343,7 @@ extern "C" const char *spg_grid_last_error(const spg_grid *g) { return g ? g->er
 
 extern "C" void spg_grid_destroy(spg_grid *g)
 {
+    SPG_TRACE();
     if (!g) return;
     cudaStreamSynchronize(g->stream);
     if (g->acc) cudaFree(g->acc);
@@ -350,6 +356,7 @@ extern "C" const char *spg_backproject_last_error(void) { return g_grid_err.c_st
 extern "C" spg_status spg_backproject(int n, int m, const float *rot, const void *X, const float *ctf,
                                       const float *pw, int kernel, float h, void *y_half, float *N_half, void *stream)
 {
+    SPG_TRACE();
     spg_grid *g = nullptr;
     spg_status s = spg_grid_create(n, kernel, h, stream, &g);
     if (s != SPG_OK) return s;  // message already in g_grid_err

@@ -69,6 +69,7 @@ struct StepParams {
     const TmapSet *tmaps;
     float *xbuf[4];
     const float *beta;       // extrapolation table beta_k (float32)
+    int beta_len;            // its length
     DevState *st;
     double *partials;        // [nitems][4] objective sums (data, l1, tv) and restart dot of the last step
     double *hist;            // ring [hist_cap][nvol][5]

@@ -8,6 +8,7 @@
 #include <mutex>
 
 #include "spg.h"
+#include "spg_trace.h"
 
 namespace {
 
@@ -123,6 +124,7 @@ extern "C" spg_status spg_objective_noalloc(int nx, int ny, int nz, float lambda
                                             const float *x, const float *b, const float *w, const float *om1,
                                             const float *omtv, double *out, void *stream)
 {
+    SPG_TRACE();
     if (nx <= 0 || ny <= 0 || nz <= 0 || !x || !b || !w || !om1 || !omtv || !out || !(mu > 0.f)) {
         g_noalloc_err = "spg_objective_noalloc: bad arguments";
         return SPG_EINVAL;

@@ -108,6 +108,21 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// Index checks of the checked build (compiled with -DSPG_CHECK, in place of
+// a memory checker): SPG_GUARD(st, cond, code) is `true` in the production
+// build; in the checked build a false `cond` records SPG_ECHECK and `code` in
+// the device state and the guarded access is skipped.
+#ifdef SPG_CHECK
+__device__ __noinline__ void check_failed(DevState *st, unsigned code)
+{
+    atomicCAS(&st->err, 0, (int)SPG_ECHECK);
+    atomicCAS(&st->err_info, 0u, code);
+}
+#define SPG_GUARD(st, cond, code) ((cond) ? true : (::spg::check_failed((st), (code)), false))
+#else
+#define SPG_GUARD(st, cond, code) true
+#endif
+
 // Compensated float32 accumulator (Kahan): per-thread objective sums.
 struct KSum {
     float s = 0.f, c = 0.f;
@@ -262,7 +277,8 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
     const VolDesc V = P.vols[W.vol];
     const TmapSet *tm = P.tmaps + W.vol;
     const int nsteps = (W.z1 - W.z0) + 2;
-    const float beta = P.beta[V.kmom];  // per volume: restarts reset a volume's index
+    const float beta = SPG_GUARD(P.st, V.kmom >= 0 && V.kmom < P.beta_len, 2u) ? P.beta[V.kmom] : 0.f;
+    // (per volume: restarts reset a volume's extrapolation index)
     const float tau = V.tau, lam_tv = V.lambda_tv, tl1 = V.tau * V.lambda_l1;
     const float inv_mu = 1.0f / V.mu, half_inv_mu = 0.5f / V.mu, half_mu = 0.5f * V.mu;
     const float mu2 = V.mu * V.mu;
@@ -312,11 +328,13 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
 
         // ---- A: p on plane z at this thread's columns ----
         const int tr = r + 1;
-        float xc[VX], mc[VX], xu[VX], mu_[VX], dc[VX];
-        ld_vec<VX>(XK + tr * XW + 4 + VX * lane, xc);
-        ld_vec<VX>(XM + tr * XW + 4 + VX * lane, mc);
-        ld_vec<VX>(XK + (tr - 1) * XW + 4 + VX * lane, xu);
-        ld_vec<VX>(XM + (tr - 1) * XW + 4 + VX * lane, mu_);
+        float xc[VX] = {}, mc[VX] = {}, xu[VX] = {}, mu_[VX] = {}, dc[VX];
+        if (SPG_GUARD(P.st, tr >= 1 && tr * XW + 4 + VX * (lane + 1) <= XW * C::XH, 3u)) {
+            ld_vec<VX>(XK + tr * XW + 4 + VX * lane, xc);
+            ld_vec<VX>(XM + tr * XW + 4 + VX * lane, mc);
+            ld_vec<VX>(XK + (tr - 1) * XW + 4 + VX * lane, xu);
+            ld_vec<VX>(XM + (tr - 1) * XW + 4 + VX * lane, mu_);
+        }
         float xl = __shfl_up_sync(FULL, xc[VX - 1], 1);
         float ml = __shfl_up_sync(FULL, mc[VX - 1], 1);
         if (lane == 0) {
@@ -334,8 +352,8 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
         for (int i = 0; i < VX; i++) dc[i] = XD ? mc[i] : xc[i] - mc[i];
         float pc[3][VX];
         if (j >= 1) {
-            float om[VX];
-            ld_vec<VX>(OM + r * OW + VX * lane, om);
+            float om[VX] = {};
+            if (SPG_GUARD(P.st, r * OW + VX * (lane + 1) <= OW * C::OH, 5u)) ld_vec<VX>(OM + r * OW + VX * lane, om);
             if (z == 0) {
 #pragma unroll
                 for (int i = 0; i < VX; i++) {
@@ -367,7 +385,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
                 if (main_warp && z < W.z1) kt.add(tsum);
             }
             // +x halo column (only p_x is consumed), one lane per tile row
-            if (col_lane) {
+            if (col_lane && SPG_GUARD(P.st, (lane + 1) * XW + TX + 4 < XW * C::XH && lane * OW + TX < OW * C::OH, 4u)) {
                 const int cr = lane + 1, cc = TX + 4;
                 const float cx = XK[cr * XW + cc], cm = XM[cr * XW + cc];
                 const float cxl = XK[cr * XW + cc - 1], cml = XM[cr * XW + cc - 1];
@@ -382,7 +400,8 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
                 const float sc = in ? OM[lane * OW + TX] * fminf(inv_mu, rsqrtf(s2)) : 0.f;
                 sh.hx_ring[(j % 3) * 32 + lane] = ax * sc;
             }
-            st_vec<VX>(sh.py_ring + ((j % 3) * (TY + 1) + r) * TX + VX * lane, pc[1]);
+            if (SPG_GUARD(P.st, r <= TY && ((j % 3) * (TY + 1) + r) * TX + VX * (lane + 1) <= 3 * (TY + 1) * TX, 6u))
+                st_vec<VX>(sh.py_ring + ((j % 3) * (TY + 1) + r) * TX + VX * lane, pc[1]);
         } else {
 #pragma unroll
             for (int i = 0; i < VX; i++) pc[0][i] = pc[1][i] = pc[2][i] = 0.f;
@@ -408,11 +427,13 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
         // ---- B: write plane z-1 ----
         if (main_warp && j >= 2) {
             const int zo = z - 1;
-            float bb[VX], ww[VX], oo[VX], pyd[VX];
-            ld_data<VX, BF16>(base + C::OFF_B, r * TX + VX * lane, bb);
-            if constexpr (!FOURIER) ld_data<VX, BF16>(base + C::OFF_W, r * TX + VX * lane, ww);
-            ld_vec<VX>(reinterpret_cast<const float *>(base + C::OFF_O1) + r * TX + VX * lane, oo);
-            ld_vec<VX>(sh.py_ring + (((j - 1) % 3) * (TY + 1) + r + 1) * TX + VX * lane, pyd);
+            float bb[VX] = {}, ww[VX] = {}, oo[VX] = {}, pyd[VX] = {};
+            if (SPG_GUARD(P.st, r < TY && r * TX + VX * (lane + 1) <= TX * TY, 7u)) {
+                ld_data<VX, BF16>(base + C::OFF_B, r * TX + VX * lane, bb);
+                if constexpr (!FOURIER) ld_data<VX, BF16>(base + C::OFF_W, r * TX + VX * lane, ww);
+                ld_vec<VX>(reinterpret_cast<const float *>(base + C::OFF_O1) + r * TX + VX * lane, oo);
+                ld_vec<VX>(sh.py_ring + (((j - 1) % 3) * (TY + 1) + r + 1) * TX + VX * lane, pyd);
+            }
             float pxn = __shfl_down_sync(FULL, pp[0][0], 1);
             if (lane == 31) pxn = sh.hx_ring[((j - 1) % 3) * 32 + r];
             float out[VX], inc[VX];
@@ -442,8 +463,9 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
                 kl.add(lsum);
             }
             if constexpr (DOT) kr.add(rsum);
-            if (gy_in && gx0 < V.pitch) {
-                const long long o = V.off + ((long long)zo * V.ny + gy) * V.pitch + gx0;
+            const long long o = V.off + ((long long)zo * V.ny + gy) * V.pitch + gx0;
+            if (gy_in && gx0 < V.pitch &&
+                SPG_GUARD(P.st, zo >= 0 && zo < V.nz && gx0 + VX <= V.pitch, 8u)) {
                 st_vec<VX>(xout_base + o, out);
                 if constexpr (XD) st_vec<VX>(dout_base + o, inc);
             }
@@ -534,6 +556,7 @@ __global__ void __launch_bounds__(32 * (TY + 1), MINB)
     const int p1 = P.sched[blockIdx.x + 1];
     for (int p = P.sched[blockIdx.x]; p < p1 && !aborted; p++) {
         const int it = P.sched[gridDim.x + 1 + p];
+        if (!SPG_GUARD(P.st, p1 <= P.nitems && it >= 0 && it < P.nitems, 1u)) break;
         const WorkItem W = P.items[it];
         bool done = false;
         if constexpr (!BF16 && XD) {

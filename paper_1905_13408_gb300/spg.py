@@ -22,7 +22,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libspg.so")
 
-SPG_OK, SPG_EINVAL, SPG_ENOMEM, SPG_ECUDA, SPG_ENOTREADY, SPG_ENONFINITE, SPG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+SPG_OK, SPG_EINVAL, SPG_ENOMEM, SPG_ECUDA, SPG_ENOTREADY, SPG_ENONFINITE, SPG_ETIMEOUT, SPG_ECHECK = \
+    0, -1, -2, -3, -4, -5, -6, -7
 SPG_F32, SPG_BF16 = 0, 1
 SPG_FISTA, SPG_ISTA = 0, 1
 SPG_STORE_DELTA, SPG_STORE_PREV = 0, 1
@@ -30,7 +31,7 @@ TILES = {"auto": 0, "128x8": 1, "128x4": 2, "64x8": 3, "64x4": 4, "128x7": 6, "1
          "128x7s4": 9}
 
 _STATUS_NAMES = {0: "SPG_OK", -1: "SPG_EINVAL", -2: "SPG_ENOMEM", -3: "SPG_ECUDA", -4: "SPG_ENOTREADY",
-                 -5: "SPG_ENONFINITE", -6: "SPG_ETIMEOUT"}
+                 -5: "SPG_ENONFINITE", -6: "SPG_ETIMEOUT", -7: "SPG_ECHECK"}
 
 # Every entry point declared in include/spg.h.
 EXPORTS = ["spg_create", "spg_create_batch", "spg_set_data", "spg_set_x", "spg_get_x", "spg_reweight",
@@ -79,16 +80,20 @@ _lock = threading.Lock()
 
 
 def load():
-    """Load libspg.so (building it first if it is missing or stale)."""
+    """Load libspg.so (building it first if it is missing or stale). With
+    SPG_CHECKED=1 in the environment the checked build (device-side index
+    checks of the fused step, failures reported as SPG_ECHECK) is built and
+    loaded instead."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
         from . import build as _build
-        _build.build()
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"CUDA library {LIB_PATH} is missing; the solver has no CPU path")
-        lib = ctypes.CDLL(LIB_PATH)
+        checked = os.environ.get("SPG_CHECKED", "0") == "1"
+        path = _build.build(checked=checked)
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; the solver has no CPU path")
+        lib = ctypes.CDLL(path)
         P, V, I, LL, D = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double
         PP = ctypes.POINTER(ctypes.c_void_p)
         sigs = {
