@@ -562,9 +562,10 @@ def run_adjoint(args):
 
 
 def run_fourier(args):
-    """Fourier-domain data term of Eq. 31 at 512^3: per iteration y_k, its
-    real-to-complex transform, the residual spectrum, the inverse transform
-    and the fused step (cuFFT for the transforms)."""
+    """Fourier-domain data term of Eq. 31 at 512^3: per iteration the
+    real-to-complex transform of y_k, the residual spectrum, the inverse
+    transform and the fused step, which also writes y_{k+1} (cuFFT for the
+    transforms)."""
     import numpy as np
     import torch
 
@@ -595,9 +596,10 @@ def run_fourier(args):
     nvox = n ** 3
     peaks, kind = measured_peaks()
     # minimal bytes per voxel (a half-spectrum coefficient is half a voxel):
-    # y_k (12 B), forward transform (4 + 4), residual spectrum N F / V - C
-    # (4 + 2 + 4 + 4), inverse transform (4 + 4), fused step without w (28 B)
-    bpv = 12 + 8 + 14 + 8 + 28
+    # forward transform of y_k (4 + 4), residual spectrum N F / V - C
+    # (4 + 2 + 4 + 4), inverse transform (4 + 4), fused step without w that
+    # also writes the next y (28 + 4 B)
+    bpv = 8 + 14 + 8 + 32
     achieved = bpv * nvox * args.steps / (ms / 1e3) / 1e9
     print(json.dumps({"metric": "Gvoxel-iter/s, Fourier-domain data term (Eq. 31), 512^3",
                       "value": nvox * args.steps / (ms / 1e3) / 1e9, "unit": UNIT, "steps": args.steps,

@@ -94,6 +94,7 @@ struct spg_ctx {
     // Fourier-domain data term (single volume)
     bool fourier = false;
     float *Ybuf = nullptr;   // extrapolated point y_k (pitched)
+    bool y_fresh = false;    // Ybuf holds the next step's y (written by the previous fused step)
     float2 *Fh = nullptr;    // spectrum scratch
     float2 *Yh = nullptr;    // data spectrum y
     float *Nh = nullptr;     // weights N
@@ -435,6 +436,7 @@ StepParams step_params(const spg_ctx *c)
     p.hist_every = c->hist_every;
     p.restart = c->opt.restart ? 1 : 0;
     p.fourier = c->fourier ? 1 : 0;
+    p.ybuf = c->fourier ? c->Ybuf : nullptr;
     p.timeout_ns = kTimeoutNs;
     return p;
 }
@@ -519,8 +521,7 @@ cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
     if (ctx->fourier) {
         const VolDesc &d = ctx->vols_h[0];
         const double V = (double)d.nx * d.ny * d.nz;
-        cudaError_t e = launch_form_y(ctx->st_d, ctx->vols_d, ctx->beta_d, ctx->X, ctx->Ybuf, ctx->total, ctx->stream);
-        if (e != cudaSuccess) return e;
+        cudaError_t e = cudaSuccess;
         const spg::CufftApi &cf = spg::cufft_api();
         if (cf.exec_r2c(ctx->pr2c, ctx->Ybuf, reinterpret_cast<cufftComplex *>(ctx->Fh)) != CUFFT_SUCCESS)
             return cudaErrorUnknown;
@@ -529,7 +530,7 @@ cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
         if (cf.exec_c2r(ctx->pc2r, reinterpret_cast<cufftComplex *>(ctx->Fh), static_cast<float *>(ctx->B)) !=
             CUFFT_SUCCESS)
             return cudaErrorUnknown;
-        ctx->launches += 2;
+        ctx->launches += 1;
     }
     if (ctx->opt.readings) {
         GenericParams g;
@@ -557,7 +558,13 @@ cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
 spg_status launch_steps(spg_ctx *ctx, int k)
 {
     const StepParams p = step_params(ctx);
-    const long long per_iter = ctx->fourier ? 3 : 1;  // kernels of this library per iteration
+    const long long per_iter = ctx->fourier ? 2 : 1;  // kernels of this library per iteration
+    if (ctx->fourier && k > 0 && !ctx->y_fresh) {
+        // y_k of the first step; every fused step then writes the next one
+        CK(launch_form_y(ctx->st_d, ctx->vols_d, ctx->beta_d, ctx->X, ctx->Ybuf, ctx->total, ctx->stream), "form y");
+        ctx->launches += 1;
+        ctx->y_fresh = true;
+    }
     if (k >= kGraphLen && !ctx->gexec) {
         const long long counted = ctx->launches;  // capturing launches nothing
         cudaGraph_t g = nullptr;
@@ -712,6 +719,7 @@ struct Sweep {
         p.hist_every = 0;  // no objective, no history
         p.restart = 0;
         p.fourier = 0;
+        p.ybuf = nullptr;
         p.timeout_ns = kTimeoutNs;
         e = step_launch(v, ctx->grid, p, ctx->stream);
         ctx->launches += 1;
@@ -1006,6 +1014,7 @@ spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const
         ctx->gexec = nullptr;
     }
     ctx->fourier = true;
+    ctx->y_fresh = false;
     ctx->data_set[0] = 1;
     ctx->reweighted = false;
     return SPG_OK;
@@ -1054,6 +1063,7 @@ spg_status spg_set_x(spg_ctx *ctx, int vol, const float *x)
     SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !x) return fail(ctx, SPG_EINVAL, "spg_set_x: bad arguments");
+    ctx->y_fresh = false;
     const VolDesc &d = ctx->vols_h[vol];
     const int c = ctx->cur();
     spg_status s;
@@ -1094,6 +1104,7 @@ spg_status spg_reweight(spg_ctx *ctx)
     ctx->launches += 1;
     ctx->k_round = 0;
     ctx->reweighted = true;
+    ctx->y_fresh = false;  // the extrapolation restarts
     return SPG_OK;
 }
 
@@ -1130,6 +1141,7 @@ spg_status spg_objective(spg_ctx *ctx, int vol, double out[4])
         // data term 1/2 |y - D A x|^2 from the spectrum of x
         const VolDesc &d = ctx->vols_h[0];
         const double V = (double)d.nx * d.ny * d.nz;
+        ctx->y_fresh = false;  // the transform below works in the y buffer
         CK(cudaMemcpyAsync(ctx->Ybuf, ctx->X[ctx->cur()], (size_t)ctx->total * sizeof(float), cudaMemcpyDeviceToDevice,
                            ctx->stream),
            "copy x");
@@ -1281,6 +1293,7 @@ spg_status spg_set_state(spg_ctx *ctx, const void *blob, size_t size)
     size_t need = 0;
     spg_get_state(ctx, nullptr, &need);
     if (size < need) return fail(ctx, SPG_EINVAL, "spg_set_state: blob too small");
+    ctx->y_fresh = false;
     const char *p = static_cast<const char *>(blob);
     StateHeader h;
     std::memcpy(&h, p, sizeof(h));
@@ -1568,6 +1581,7 @@ spg_status spg_autotune(spg_ctx *ctx, int trial_iters, int info[6])
     if (!ctx || trial_iters < 1) return fail(ctx, SPG_EINVAL, "spg_autotune: bad arguments");
     if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_autotune: not available with alternative readings");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_autotune: call spg_reweight first");
+    ctx->y_fresh = false;
     const std::string key = tune_key(ctx);
     int tile = 0, zc = 0;
     spg_status s;

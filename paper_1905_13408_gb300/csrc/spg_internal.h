@@ -76,6 +76,7 @@ struct StepParams {
     int nitems, nvol, hist_cap, hist_every;
     int restart;             // gradient restart of the extrapolation, per volume
     int fourier;             // data gradient = b (A^H (N A y - D y) of the Fourier-domain term), no w tile
+    float *ybuf;             // Fourier-domain term: the step also writes y_{k+1} = x_{k+1} + beta_{k+1} d_{k+1} here
     long long timeout_ns;    // bound on any single barrier wait
 };
 

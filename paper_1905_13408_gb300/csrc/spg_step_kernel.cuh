@@ -278,6 +278,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
     const TmapSet *tm = P.tmaps + W.vol;
     const int nsteps = (W.z1 - W.z0) + 2;
     const float beta = SPG_GUARD(P.st, V.kmom >= 0 && V.kmom < P.beta_len, 2u) ? P.beta[V.kmom] : 0.f;
+    const float beta_next = (FOURIER && V.kmom + 1 < P.beta_len) ? P.beta[V.kmom + 1] : 0.f;
     // (per volume: restarts reset a volume's extrapolation index)
     const float tau = V.tau, lam_tv = V.lambda_tv, tl1 = V.tau * V.lambda_l1;
     const float inv_mu = 1.0f / V.mu, half_inv_mu = 0.5f / V.mu, half_mu = 0.5f * V.mu;
@@ -468,6 +469,15 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
                 SPG_GUARD(P.st, zo >= 0 && zo < V.nz && gx0 + VX <= V.pitch, 8u)) {
                 st_vec<VX>(xout_base + o, out);
                 if constexpr (XD) st_vec<VX>(dout_base + o, inc);
+                if constexpr (FOURIER) {
+                    // the next step's extrapolated point, input of its forward transform
+                    if (P.ybuf) {
+                        float yv[VX];
+#pragma unroll
+                        for (int i = 0; i < VX; i++) yv[i] = fmaf(beta_next, inc[i], out[i]);
+                        st_vec<VX>(P.ybuf + o, yv);
+                    }
+                }
             }
         }
 #pragma unroll
