@@ -30,10 +30,12 @@
  *  - Volumes are dense float32 (or bfloat16 where stated) arrays in C order
  *    [nz][ny][nx], x fastest, no padding. Pointers may be device pointers or
  *    host pointers (pinned or pageable): copies use unified addressing. The
- *    library never keeps or frees a caller pointer; it copies what it needs.
- *  - Work is enqueued on the CUDA stream given at creation (NULL = the legacy
- *    default stream). Entry points that return host values synchronise that
- *    stream; the others are asynchronous.
+ *    library never frees a caller pointer and keeps none beyond the call,
+ *    except where an entry point states otherwise (spg_grid_add reads device
+ *    inputs in place, in stream order).
+ *  - Work is enqueued on the CUDA stream given at creation (NULL: the
+ *    context creates and owns a stream). Entry points that return host
+ *    values synchronise that stream; the others are asynchronous.
  *  - Every call returns an spg_status; spg_last_error() gives a message. No
  *    C++ exception crosses this interface. There is no CPU fallback: without
  *    a usable CUDA device, spg_create fails with SPG_ECUDA.

@@ -854,22 +854,18 @@ spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg
     if ((e = dalloc(&ctx->maxw_d, (size_t)nvol * sizeof(double))) != cudaSuccess) return bail(e, "alloc");
     if ((e = dalloc(&ctx->rstats_d, (size_t)nvol * 6 * sizeof(double))) != cudaSuccess) return bail(e, "alloc");
 
-    for (int q = 0; q < ctx->nalloc(); q++) cudaMemsetAsync(ctx->X[q], 0, vb, ctx->stream);
-    cudaMemsetAsync(ctx->B, 0, db, ctx->stream);
-    cudaMemsetAsync(ctx->W, 0, db, ctx->stream);
-    cudaMemsetAsync(ctx->OM1, 0, vb, ctx->stream);
-    cudaMemsetAsync(ctx->OMTV, 0, vb, ctx->stream);
-    cudaMemsetAsync(ctx->st_d, 0, sizeof(DevState), ctx->stream);
-    cudaMemsetAsync(ctx->hist_d, 0, (size_t)ctx->hist_cap * nvol * 5 * sizeof(double), ctx->stream);
-    cudaMemsetAsync(ctx->rstats_d, 0, (size_t)nvol * 6 * sizeof(double), ctx->stream);
-    // extrapolation table, FP64 recurrence, stored as float32
-    std::vector<float> beta(ctx->max_iters);
-    double t = 1.0;
-    for (int k = 0; k < ctx->max_iters; k++) {
-        const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
-        beta[k] = ctx->opt.momentum == SPG_ISTA ? 0.f : (float)((t - 1.0) / tn);
-        t = tn;
+    {
+        const std::pair<void *, size_t> zero[] = {
+            {ctx->X[0], vb}, {ctx->X[1], vb}, {ctx->X[2], vb}, {ctx->X[3], vb}, {ctx->B, db}, {ctx->W, db},
+            {ctx->OM1, vb}, {ctx->OMTV, vb}, {ctx->st_d, sizeof(DevState)},
+            {ctx->hist_d, (size_t)ctx->hist_cap * nvol * 5 * sizeof(double)},
+            {ctx->rstats_d, (size_t)nvol * 6 * sizeof(double)}};
+        for (const auto &z : zero)
+            if (z.first && (e = cudaMemsetAsync(z.first, 0, z.second, ctx->stream)) != cudaSuccess)
+                return bail(e, "clear buffers");
     }
+    // extrapolation table, FP64 recurrence, stored as float32
+    const std::vector<float> beta = beta_table_host(ctx, ctx->max_iters);
     if ((e = cudaMemcpyAsync(ctx->beta_d, beta.data(), beta.size() * sizeof(float), cudaMemcpyHostToDevice,
                              ctx->stream)) != cudaSuccess)
         return bail(e, "upload beta");
