@@ -451,6 +451,7 @@ AuxParams aux_params(const spg_ctx *c)
     a.st = c->st_d;
     a.plane_part = c->plane_part_d;
     a.vol_out = c->vol_out_d;
+    a.readings = c->opt.readings;
     return a;
 }
 

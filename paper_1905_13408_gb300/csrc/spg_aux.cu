@@ -292,20 +292,13 @@ struct Field {
     }
 };
 
-// D u at (x, y, z) in volume V. Adopted reading: backward differences that
-// vanish on the first plane of each axis (Eq. 12); the SPG_READ_* flags of
-// the volume select forward differences and/or a periodic boundary.
-__device__ __forceinline__ void grad_at(const VolDesc &V, const Field &F, int x, int y, int z, float g[3])
+// D u at (x, y, z) under the SPG_READ_* flags of the volume (forward
+// differences and/or a periodic boundary); kept out of line so the adopted
+// reading's code below stays small.
+__device__ __noinline__ void grad_at_readings(const VolDesc &V, const Field &F, int x, int y, int z, float g[3])
 {
     const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
     const float xc = F.x(i), dc = F.d(i);
-    if (V.readings == 0) {
-        g[0] = x >= 1 ? (xc - F.x(i - 1)) + F.beta * (dc - F.d(i - 1)) : 0.f;
-        g[1] = y >= 1 ? (xc - F.x(i - V.pitch)) + F.beta * (dc - F.d(i - V.pitch)) : 0.f;
-        const long long ps = (long long)V.pitch * V.ny;
-        g[2] = z >= 1 ? (xc - F.x(i - ps)) + F.beta * (dc - F.d(i - ps)) : 0.f;
-        return;
-    }
     const bool fwd = (V.readings & SPG_READ_FORWARD) != 0, per = (V.readings & SPG_READ_PERIODIC) != 0;
     const int co[3] = {x, y, z}, ext[3] = {V.nx, V.ny, V.nz};
     const long long stp[3] = {1, V.pitch, (long long)V.pitch * V.ny};
@@ -325,6 +318,22 @@ __device__ __forceinline__ void grad_at(const VolDesc &V, const Field &F, int x,
             g[a] = (F.x(j) - xc) + F.beta * (F.d(j) - dc);
         }
     }
+}
+
+// D u at (x, y, z) in volume V. Adopted reading: backward differences that
+// vanish on the first plane of each axis (Eq. 12).
+__device__ __forceinline__ void grad_at(const VolDesc &V, const Field &F, int x, int y, int z, float g[3])
+{
+    if (V.readings != 0) {
+        grad_at_readings(V, F, x, y, z, g);
+        return;
+    }
+    const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
+    const float xc = F.x(i), dc = F.d(i);
+    g[0] = x >= 1 ? (xc - F.x(i - 1)) + F.beta * (dc - F.d(i - 1)) : 0.f;
+    g[1] = y >= 1 ? (xc - F.x(i - V.pitch)) + F.beta * (dc - F.d(i - V.pitch)) : 0.f;
+    const long long ps = (long long)V.pitch * V.ny;
+    g[2] = z >= 1 ? (xc - F.x(i - ps)) + F.beta * (dc - F.d(i - ps)) : 0.f;
 }
 
 // p = omtv * D u / max(mu, |D u|) at (x, y, z) (without omtv under
@@ -376,6 +385,131 @@ __device__ __forceinline__ float div_at(const VolDesc &V, const Field &F, const 
     return r;
 }
 
+// ---------------- row-vector walks for the adopted reading ----------------
+// The re-weighting and the objective read every voxel once plus three
+// neighbours; with one voxel per thread they wait on memory latency. The
+// adopted reading's kernels instead walk a row segment in 128-voxel chunks:
+// each warp takes a chunk of a row, each lane 4 consecutive voxels (16-byte
+// loads: rows start 32-byte aligned, the pitch being a multiple of 8 and
+// volume offsets of 64 elements). The x-neighbour of a lane's first voxel
+// comes from the lane before it (the first lane of a chunk loads it).
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
+__device__ __forceinline__ float4 ld4_data(const void *p, bool bf16, long long i)
+{
+    if (!bf16) return ld4(reinterpret_cast<const float *>(p) + i);
+    const uint2 u = *reinterpret_cast<const uint2 *>(reinterpret_cast<const uint16_t *>(p) + i);
+    return make_float4(__uint_as_float((u.x & 0xffffu) << 16), __uint_as_float(u.x & 0xffff0000u),
+                       __uint_as_float((u.y & 0xffffu) << 16), __uint_as_float(u.y & 0xffff0000u));
+}
+
+__device__ __forceinline__ void unpack4(const float4 v, float (&o)[4])
+{
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+}
+
+// x and D x (Eq. 12, zero on first planes) at voxels x0 .. x0+3 of row (y, z);
+// inactive lanes (x0 >= nx) get zeros but still take part in the shuffle.
+__device__ __forceinline__ void grad4_at(const VolDesc &V, const float *xs, int x0, int y, int z, int lane,
+                                         bool act, float (&xc)[4], float (&gx)[4], float (&gy)[4], float (&gz)[4])
+{
+    const long long row = V.off + ((long long)z * V.ny + y) * V.pitch;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 c = act ? ld4(xs + row + x0) : zero;
+    float xl = __shfl_up_sync(FULL, c.w, 1);
+    if (lane == 0) xl = (act && x0 >= 1) ? xs[row + x0 - 1] : c.x;
+    if (x0 == 0) xl = c.x;
+    const float4 u = (act && y >= 1) ? ld4(xs + row - V.pitch + x0) : c;
+    const float4 w = (act && z >= 1) ? ld4(xs + row - (long long)V.pitch * V.ny + x0) : c;
+    float uu[4], ww[4];
+    unpack4(c, xc);
+    unpack4(u, uu);
+    unpack4(w, ww);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        gx[q] = xc[q] - (q ? xc[q - 1] : xl);
+        gy[q] = xc[q] - uu[q];
+        gz[q] = xc[q] - ww[q];
+    }
+}
+
+__global__ void reweight4_kernel(AuxParams a, const float *xcur, float *om1, float *omtv, const double *maxw,
+                                 double *rstats, VolDesc *vols_rw);
+__global__ void objective4_kernel(AuxParams a, const float *xcur, const void *b, const void *w, bool bf16,
+                                  const float *om1, const float *omtv);
+
+// Last CTA of a re-weighting launch: per-volume max omtv, nnz, sums, and
+// tau = 1/L (FP64), then the round restarts.
+__device__ void reweight_finish(const AuxParams &a, const double *maxw, double *rstats, VolDesc *vols_rw,
+                                double *scratch)
+{
+    for (int v = 0; v < a.nvol; v++) {
+        const VolDesc W = a.vols[v];
+        double m = 0, c3[3] = {0, 0, 0};
+        for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG; q += blockDim.x) {
+            const double *pp = a.plane_part + (long long)q * 4;
+            m = fmax(m, __ldcg(pp + 0));
+            c3[0] += __ldcg(pp + 1);
+            c3[1] += __ldcg(pp + 2);
+            c3[2] += __ldcg(pp + 3);
+        }
+        m = block_max(m, scratch);
+        block_sum<3>(c3, scratch);
+        const double n = c3[0], s1 = c3[1], s2 = c3[2];
+        if (threadIdx.x == 0) {
+            const double L = maxw[v] + 12.0 * (double)W.lambda_tv * m / (double)W.mu;
+            const double tau = 1.0 / L;
+            double *o = rstats + (long long)v * 6;
+            o[0] = m;
+            o[1] = n;
+            o[2] = s1;
+            o[3] = s2;
+            o[4] = L;
+            o[5] = tau;
+            vols_rw[v].tau = (float)tau;
+            vols_rw[v].kmom = 0;  // extrapolation restarts with the round
+            vols_rw[v].beta_last = 0.f;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.st->k_round = 0;
+        a.st->ticket_aux = 0;
+        __threadfence();
+    }
+}
+
+// Last CTA of an objective launch: per-volume (data, l1, tv, total).
+__device__ void objective_finish(const AuxParams &a, double *scratch)
+{
+    for (int v = 0; v < a.nvol; v++) {
+        const VolDesc W = a.vols[v];
+        double c3[3] = {0, 0, 0};
+        for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG; q += blockDim.x) {
+            const double *pp = a.plane_part + (long long)q * 4;
+            c3[0] += __ldcg(pp + 0);
+            c3[1] += __ldcg(pp + 1);
+            c3[2] += __ldcg(pp + 2);
+        }
+        block_sum<3>(c3, scratch);
+        if (threadIdx.x != 0) continue;
+        const double d = c3[0], l = c3[1], t = c3[2];
+        double *o = a.vol_out + (long long)v * 8;
+        o[0] = d;
+        o[1] = (double)W.lambda_l1 * l;
+        o[2] = (double)W.lambda_tv * t;
+        o[3] = o[0] + o[1] + o[2];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.st->ticket_aux = 0;
+        __threadfence();
+    }
+}
+
 // ---------------- re-weighting (Eq. 11, eps scaling of Sec. 2.5) ----------------
 __global__ void reweight_kernel(AuxParams a, const float *xcur, float *om1, float *omtv, const double *maxw,
                                 double *rstats, VolDesc *vols_rw)
@@ -419,40 +553,7 @@ __global__ void reweight_kernel(AuxParams a, const float *xcur, float *om1, floa
         pp[3] = s[2];
     }
     if (!last_block(&a.st->ticket_aux, &flag)) return;
-    for (int v = 0; v < a.nvol; v++) {
-        const VolDesc W = a.vols[v];
-        double m = 0, c3[3] = {0, 0, 0};
-        for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG; q += blockDim.x) {
-            const double *pp = a.plane_part + (long long)q * 4;
-            m = fmax(m, __ldcg(pp + 0));
-            c3[0] += __ldcg(pp + 1);
-            c3[1] += __ldcg(pp + 2);
-            c3[2] += __ldcg(pp + 3);
-        }
-        m = block_max(m, scratch);
-        block_sum<3>(c3, scratch);
-        const double n = c3[0], s1 = c3[1], s2 = c3[2];
-        if (threadIdx.x == 0) {
-            const double L = maxw[v] + 12.0 * (double)W.lambda_tv * m / (double)W.mu;
-            const double tau = 1.0 / L;
-            double *o = rstats + (long long)v * 6;
-            o[0] = m;
-            o[1] = n;
-            o[2] = s1;
-            o[3] = s2;
-            o[4] = L;
-            o[5] = tau;
-            vols_rw[v].tau = (float)tau;
-            vols_rw[v].kmom = 0;  // extrapolation restarts with the round
-            vols_rw[v].beta_last = 0.f;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        a.st->k_round = 0;
-        a.st->ticket_aux = 0;
-        __threadfence();
-    }
+    reweight_finish(a, maxw, rstats, vols_rw, scratch);
 }
 
 // ---------------- objective F(x) at the current iterate ----------------
@@ -495,29 +596,119 @@ __global__ void objective_kernel(AuxParams a, const float *xcur, const void *b, 
         pp[3] = 0;
     }
     if (!last_block(&a.st->ticket_aux, &flag)) return;
-    for (int v = 0; v < a.nvol; v++) {
-        const VolDesc W = a.vols[v];
-        double c3[3] = {0, 0, 0};
-        for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG; q += blockDim.x) {
-            const double *pp = a.plane_part + (long long)q * 4;
-            c3[0] += __ldcg(pp + 0);
-            c3[1] += __ldcg(pp + 1);
-            c3[2] += __ldcg(pp + 2);
+    objective_finish(a, scratch);
+}
+
+// Re-weighting of the adopted reading, row-vector walk (same results as
+// reweight_kernel; padding columns of the pitch get zero weights).
+__global__ void reweight4_kernel(AuxParams a, const float *xcur, float *om1, float *omtv, const double *maxw,
+                                 double *rstats, VolDesc *vols_rw)
+{
+    __shared__ double scratch[32 * 4];
+    __shared__ int flag;
+    const int plane = blockIdx.x / AUX_SEG;
+    const int vol = a.plane_vol[plane];
+    const VolDesc V = a.vols[vol];
+    const int z = plane - V.plane_begin;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nchunk = (V.nx + 127) / 128;
+    float fmx = 0.f, nnz = 0.f;
+    KSum c1, c2;
+    for (int rc = warp; rc < (r1 - r0) * nchunk; rc += nwarps) {
+        const int y = r0 + rc / nchunk, x0 = (rc % nchunk) * 128 + 4 * lane;
+        const bool act = x0 < V.nx;
+        float xc[4], gx[4], gy[4], gz[4], o1[4], ot[4];
+        grad4_at(V, xcur, x0, y, z, lane, act, xc, gx, gy, gz);
+        float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const bool valid = act && x0 + q < V.nx;
+            const float gn = sqrtf(gx[q] * gx[q] + gy[q] * gy[q] + gz[q] * gz[q]);
+            o1[q] = valid ? V.eps / (fabsf(xc[q]) + V.eps) : 0.f;
+            ot[q] = valid ? V.eps_tv / (gn + V.eps_tv) : 0.f;
+            fmx = fmaxf(fmx, ot[q]);
+            nnz += (valid && xc[q] != 0.f) ? 1.f : 0.f;
+            s1 += o1[q];
+            s2 += ot[q];
         }
-        block_sum<3>(c3, scratch);
-        if (threadIdx.x != 0) continue;
-        const double d = c3[0], l = c3[1], t = c3[2];
-        double *o = a.vol_out + (long long)v * 8;
-        o[0] = d;
-        o[1] = (double)W.lambda_l1 * l;
-        o[2] = (double)W.lambda_tv * t;
-        o[3] = o[0] + o[1] + o[2];
+        if (act) {
+            const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x0;
+            *reinterpret_cast<float4 *>(om1 + i) = make_float4(o1[0], o1[1], o1[2], o1[3]);
+            *reinterpret_cast<float4 *>(omtv + i) = make_float4(ot[0], ot[1], ot[2], ot[3]);
+        }
+        c1.add(s1);
+        c2.add(s2);
     }
-    __syncthreads();
+    const double mx = block_max((double)fmx, scratch);
+    double sm[3] = {(double)nnz, c1.value(), c2.value()};
+    block_sum<3>(sm, scratch);
     if (threadIdx.x == 0) {
-        a.st->ticket_aux = 0;
-        __threadfence();
+        double *pp = a.plane_part + (long long)blockIdx.x * 4;
+        pp[0] = mx;
+        pp[1] = sm[0];
+        pp[2] = sm[1];
+        pp[3] = sm[2];
     }
+    if (!last_block(&a.st->ticket_aux, &flag)) return;
+    reweight_finish(a, maxw, rstats, vols_rw, scratch);
+}
+
+// Objective of the adopted reading, row-vector walk (same sums as
+// objective_kernel; padding columns contribute nothing).
+__global__ void objective4_kernel(AuxParams a, const float *xcur, const void *b, const void *w, bool bf16,
+                                  const float *om1, const float *omtv)
+{
+    __shared__ double scratch[32 * 4];
+    __shared__ int flag;
+    const int plane = blockIdx.x / AUX_SEG;
+    const int vol = a.plane_vol[plane];
+    const VolDesc V = a.vols[vol];
+    const int z = plane - V.plane_begin;
+    int r0, r1;
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nchunk = (V.nx + 127) / 128;
+    const float mu = V.mu;
+    KSum kd, kl, kt;
+    for (int rc = warp; rc < (r1 - r0) * nchunk; rc += nwarps) {
+        const int y = r0 + rc / nchunk, x0 = (rc % nchunk) * 128 + 4 * lane;
+        const bool act = x0 < V.nx;
+        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x0;
+        float xc[4], gx[4], gy[4], gz[4], o1[4], ot[4], bv[4], wv[4];
+        grad4_at(V, xcur, x0, y, z, lane, act, xc, gx, gy, gz);
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        unpack4(act ? ld4(om1 + i) : zero, o1);
+        unpack4(act ? ld4(omtv + i) : zero, ot);
+        unpack4((act && w) ? ld4_data(b, bf16, i) : zero, bv);
+        unpack4((act && w) ? ld4_data(w, bf16, i) : zero, wv);
+        float sd = 0.f, sl = 0.f, st = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (!(act && x0 + q < V.nx)) continue;
+            const float qq = gx[q] * gx[q] + gy[q] * gy[q] + gz[q] * gz[q];
+            const float h = qq <= mu * mu ? qq * (0.5f / mu) : qq * rsqrtf(qq) - 0.5f * mu;
+            const float r = xc[q] - bv[q];
+            sd += 0.5f * wv[q] * r * r;
+            sl += o1[q] * fabsf(xc[q]);
+            st += ot[q] * h;
+        }
+        kd.add(sd);
+        kl.add(sl);
+        kt.add(st);
+    }
+    double sm[3] = {kd.value(), kl.value(), kt.value()};
+    block_sum<3>(sm, scratch);
+    if (threadIdx.x == 0) {
+        double *pp = a.plane_part + (long long)blockIdx.x * 4;
+        pp[0] = sm[0];
+        pp[1] = sm[1];
+        pp[2] = sm[2];
+        pp[3] = 0;
+    }
+    if (!last_block(&a.st->ticket_aux, &flag)) return;
+    objective_finish(a, scratch);
 }
 
 // ---------------- certificate |r|^2 of the last step ----------------
@@ -859,14 +1050,20 @@ cudaError_t launch_convert_to_f32(const uint16_t *src, float *dst, long long n, 
 cudaError_t launch_reweight(const AuxParams &a, const float *const *xbuf, float *om1, float *omtv,
                             const double *maxw, double *rstats, VolDesc *vols_rw, cudaStream_t s)
 {
-    reweight_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a, xbuf[0], om1, omtv, maxw, rstats, vols_rw);
+    if (a.readings == 0)
+        reweight4_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a, xbuf[0], om1, omtv, maxw, rstats, vols_rw);
+    else
+        reweight_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a, xbuf[0], om1, omtv, maxw, rstats, vols_rw);
     return cudaGetLastError();
 }
 
 cudaError_t launch_objective(const AuxParams &a, const float *const *xbuf, const void *b, const void *w,
                              bool bf16, const float *om1, const float *omtv, cudaStream_t s)
 {
-    objective_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a, xbuf[0], b, w, bf16, om1, omtv);
+    if (a.readings == 0)
+        objective4_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a, xbuf[0], b, w, bf16, om1, omtv);
+    else
+        objective_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a, xbuf[0], b, w, bf16, om1, omtv);
     return cudaGetLastError();
 }
 

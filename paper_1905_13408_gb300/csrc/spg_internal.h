@@ -103,6 +103,7 @@ struct AuxParams {
     DevState *st;
     double *plane_part;      // [nplanes * AUX_SEG][4]
     double *vol_out;         // [nvol][8]
+    int readings;            // SPG_READ_* flags of the context (0: the row-vector kernels)
 };
 
 cudaError_t launch_validate(const AuxParams &a, int vol, int nz, const void *b, const void *w, bool bf16,
