@@ -144,6 +144,30 @@ def test_vol512_first_iterations_match_oracle():
     np.testing.assert_allclose(st[0, 4:], ref.rstats[0, 4:], rtol=1e-6)
 
 
+def test_vol512_objective_at_the_gap():
+    """The benchmark's 512^3 round-1 subproblem run for the 159 iterations it
+    needs to reach a relative gap of 1e-3: the final iterate and objective
+    against the FP64 oracle run for the same 159 iterations (about 2.1e10
+    voxel-iterations of oracle work)."""
+    vol, hyper, _, _ = synth.workload("vol512")
+    shape = vol.b.shape
+    K = 159
+    s = make_solver(shape, hyper)
+    s.set_data(0, torch.from_numpy(vol.b).cuda(), torch.from_numpy(vol.w).cuda())
+    s.reweight()
+    s.iterate(K)
+    x = s.get_x(0).cpu().numpy()
+    obj = s.objective(0)
+    s.close()
+    p = oparams(shape, hyper)
+    ref = oracle.solve(vol.b, vol.w, p, 1, K, with_hist=False)
+    want = oracle.objective(ref.x, vol.b, vol.w, ref.om1, ref.omtv, p)
+    err = rel_l2(x, ref.x)
+    print(f"512^3 after {K} iterations: rel-L2 {err:.2e}, objective rel {abs(obj[3] - want[3]) / abs(want[3]):.2e}")
+    assert err <= 1e-5
+    np.testing.assert_allclose(obj[3], want[3], rtol=1e-6)
+
+
 def test_vol512_sampled_step():
     """512^3 at the benchmark's launch configuration: after 25 iterations of
     round 1, one more step is checked at 20000 sampled voxels against the
