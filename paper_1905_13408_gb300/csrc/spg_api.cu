@@ -1488,15 +1488,16 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
             a.P = fP;
             a.HQ = fH;
             a.stride = ctx->total;
+            a.prev_fresh = k >= 1 ? 1 : 0;  // dL/dx_{k-1} gets its first contribution here
             CK(launch_adjoint_mask(a, ctx->stream), "adjoint mask");
             CK(launch_adjoint_apply(a, ctx->stream), "adjoint apply");
             ctx->launches += 4;
-            // rotate: dL/dx_k is complete; the old dL/dx_{k+1} buffer becomes dL/dx_{k-2}
+            // rotate: dL/dx_k is complete; the old dL/dx_{k+1} buffer becomes dL/dx_{k-2},
+            // which the next step writes (no clearing needed)
             const int t = inext;
             inext = icur;
             icur = iprev;
             iprev = t;
-            CK(cudaMemsetAsync(ga[iprev], 0, vb, ctx->stream), "memset");
         }
     }
     if ((s = copy_volume_out(ctx, gb, accb, 4, d)) != SPG_OK) return s;

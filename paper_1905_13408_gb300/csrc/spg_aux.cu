@@ -875,141 +875,269 @@ __global__ void generic_step_kernel(GenericParams g)
 }
 
 // ---------------- adjoint of one step ----------------
-// Four passes over row segments, each a plain stencil of radius one on fields
-// the previous pass stored (component a of a 3-vector field at a * stride):
+// Four passes over row segments, each a stencil of radius one on fields the
+// previous pass stored (component c of a 3-vector field at c * stride):
 //   1. G = D y and P = omtv grad h_mu(G) at every voxel;
 //   2. tvg = D^T P, the step's z, the soft-threshold mask m = gnext [pass],
 //      the l1 / TV scalar partials, gb += tau w m, gw += -tau (y - b) m;
 //   3. HQ = omtv H_mu(G) D m, H_mu = I/mu inside the smoothing ball and
 //      (I - e e^T)/|G| outside (the Hessian of Eq. 14);
 //   4. ybar = m - tau (w m + lambda_tv D^T HQ); gcur += (1+beta) ybar,
-//      gprev += -beta ybar.
+//      gprev += -beta ybar (gprev is written, not accumulated, when it has
+//      no earlier contribution).
 // The values equal those of evaluating every quantity on the fly at each
-// neighbour; storing them makes each pass a handful of loads per voxel.
-__device__ __forceinline__ long long lin(const VolDesc &V, int x, int y, int z)
+// neighbour. Each pass walks rows like the re-weighting: 4 voxels per lane
+// with 16-byte loads, x-neighbours by shuffle; padding columns of the pitch
+// get zeros in every stored field, so they read as the zero outside the
+// volume.
+struct Lane4 {
+    int x0, y, z, lane;
+    bool act;
+    long long i;  // element index of voxel x0 of the row
+};
+
+__device__ __forceinline__ float4 ldz4(const float *p, bool ok)
 {
-    return V.off + ((long long)z * V.ny + y) * V.pitch + x;
+    return ok ? *reinterpret_cast<const float4 *>(p) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
+
+__device__ __forceinline__ void st4(float *p, const float (&v)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// f at x0-1 .. x0+2 (the backward x-neighbours of the lane's voxels), x0-1
+// from the previous lane or, for a chunk's first lane, loaded; f(x0-1) := f(x0)
+// at the volume's first column (zero difference).
+__device__ __forceinline__ void left4(const float *f, const Lane4 &L, const float (&c)[4], float (&l)[4])
+{
+    float xl = __shfl_up_sync(FULL, c[3], 1);
+    if (L.lane == 0) xl = (L.act && L.x0 >= 1) ? f[L.i - 1] : c[0];
+    if (L.x0 == 0) xl = c[0];
+    l[0] = xl;
+    l[1] = c[0];
+    l[2] = c[1];
+    l[3] = c[2];
+}
+
+// f at x0+1 .. x0+4 (the forward x-neighbours), zero beyond the volume.
+__device__ __forceinline__ void right4(const VolDesc &V, const float *f, const Lane4 &L, const float (&c)[4],
+                                       float (&r)[4])
+{
+    float xr = __shfl_down_sync(FULL, c[0], 1);
+    if (L.lane == 31) xr = (L.act && L.x0 + 4 < V.nx) ? f[L.i + 4] : 0.f;
+    r[0] = c[1];
+    r[1] = c[2];
+    r[2] = c[3];
+    r[3] = xr;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if (L.x0 + q + 1 >= V.nx) r[q] = 0.f;
+}
+
+#define ADJ_WALK_BEGIN                                                                  \
+    const VolDesc V = a.vols[0];                                                        \
+    const int zz_ = blockIdx.x / AUX_SEG;                                               \
+    int r0, r1;                                                                         \
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);                                       \
+    const int lane_ = threadIdx.x & 31, warp_ = threadIdx.x >> 5, nw_ = blockDim.x >> 5; \
+    const int nchunk_ = (V.nx + 127) / 128;                                             \
+    const long long S = a.stride, PS = (long long)V.pitch * V.ny;                       \
+    for (int rc = warp_; rc < (r1 - r0) * nchunk_; rc += nw_) {                         \
+        Lane4 L;                                                                        \
+        L.y = r0 + rc / nchunk_;                                                        \
+        L.z = zz_;                                                                      \
+        L.x0 = (rc % nchunk_) * 128 + 4 * lane_;                                        \
+        L.lane = lane_;                                                                 \
+        L.act = L.x0 < V.nx;                                                            \
+        L.i = V.off + ((long long)L.z * V.ny + L.y) * V.pitch + L.x0;
+#define ADJ_WALK_END }
 
 __global__ void adjoint_grad_kernel(AdjParams a)
 {
-    const VolDesc V = a.vols[0];
-    const int z = blockIdx.x / AUX_SEG;
-    int r0, r1;
-    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
-    const Field F{a.xk, a.xkm1, a.beta};
-    const long long S = a.stride;
-    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
-        const int x = t % V.nx, y = r0 + t / V.nx;
-        const long long i = lin(V, x, y, z);
+    ADJ_WALK_BEGIN
+    float xc[4], mc[4], xu[4], mu_[4], xw[4], mw[4], xl[4], ml[4], ot[4];
+    unpack4(ldz4(a.xk + L.i, L.act), xc);
+    unpack4(ldz4(a.xkm1 + L.i, L.act), mc);
+    left4(a.xk, L, xc, xl);
+    left4(a.xkm1, L, mc, ml);
+    if (L.y >= 1) {
+        unpack4(ldz4(a.xk + L.i - V.pitch, L.act), xu);
+        unpack4(ldz4(a.xkm1 + L.i - V.pitch, L.act), mu_);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; q++) xu[q] = xc[q], mu_[q] = mc[q];
+    }
+    if (L.z >= 1) {
+        unpack4(ldz4(a.xk + L.i - PS, L.act), xw);
+        unpack4(ldz4(a.xkm1 + L.i - PS, L.act), mw);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; q++) xw[q] = xc[q], mw[q] = mc[q];
+    }
+    unpack4(ldz4(a.omtv + L.i, L.act), ot);
+    float G[3][4], P[3][4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const float dc = xc[q] - mc[q];
         float g[3];
-        grad_at(V, F, x, y, z, g);
+        g[0] = (xc[q] - xl[q]) + a.beta * (dc - (xl[q] - ml[q]));
+        g[1] = (xc[q] - xu[q]) + a.beta * (dc - (xu[q] - mu_[q]));
+        g[2] = (xc[q] - xw[q]) + a.beta * (dc - (xw[q] - mw[q]));
+        const bool valid = L.act && L.x0 + q < V.nx;
         const float s2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-        const float sc = a.omtv[i] * fminf(1.0f / V.mu, rsqrtf(s2));
+        const float sc = ot[q] * fminf(1.0f / V.mu, rsqrtf(s2));
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            a.G[c * S + i] = g[c];
-            a.P[c * S + i] = g[c] * sc;
+            G[c][q] = valid ? g[c] : 0.f;
+            P[c][q] = valid ? g[c] * sc : 0.f;
         }
     }
-}
-
-// sum_a f_a(v) - f_a(v + e_a), with f = 0 beyond the volume (Eq. 17).
-__device__ __forceinline__ float div_stored(const VolDesc &V, const float *f, long long S, int x, int y, int z)
-{
-    const long long i = lin(V, x, y, z);
-    const float fx = x + 1 < V.nx ? f[i + 1] : 0.f;
-    const float fy = y + 1 < V.ny ? f[S + i + V.pitch] : 0.f;
-    const float fz = z + 1 < V.nz ? f[2 * S + i + (long long)V.pitch * V.ny] : 0.f;
-    return (f[i] - fx) + (f[S + i] - fy) + (f[2 * S + i] - fz);
+    if (L.act) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            st4(a.G + c * S + L.i, G[c]);
+            st4(a.P + c * S + L.i, P[c]);
+        }
+    }
+    ADJ_WALK_END
 }
 
 __global__ void adjoint_mask_kernel(AdjParams a)
 {
     __shared__ double scratch[32 * 4];
-    const VolDesc V = a.vols[0];
-    const int z = blockIdx.x / AUX_SEG;
-    int r0, r1;
-    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
     KSum k1, k2;
-    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
-        const int x = t % V.nx, y = r0 + t / V.nx;
-        const long long i = lin(V, x, y, z);
-        const float d = a.xk[i] - a.xkm1[i];
-        const float bv = ld_data(a.b, a.bf16, i), wv = ld_data(a.w, a.bf16, i);
-        const float tvg = div_stored(V, a.P, a.stride, x, y, z);
-        const float g = wv * ((a.xk[i] - bv) + a.beta * d) + V.lambda_tv * tvg;
+    ADJ_WALK_BEGIN
+    float p0[4], p1[4], p2[4], px[4], py[4], pz[4];
+    unpack4(ldz4(a.P + L.i, L.act), p0);
+    unpack4(ldz4(a.P + S + L.i, L.act), p1);
+    unpack4(ldz4(a.P + 2 * S + L.i, L.act), p2);
+    right4(V, a.P, L, p0, px);
+    unpack4(ldz4(a.P + S + L.i + V.pitch, L.act && L.y + 1 < V.ny), py);
+    unpack4(ldz4(a.P + 2 * S + L.i + PS, L.act && L.z + 1 < V.nz), pz);
+    float xk[4], xm[4], bv[4], wv[4], o1[4], gn[4], gb[4], gw[4], m[4];
+    unpack4(ldz4(a.xk + L.i, L.act), xk);
+    unpack4(ldz4(a.xkm1 + L.i, L.act), xm);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    unpack4(L.act ? ld4_data(a.b, a.bf16, L.i) : zero, bv);
+    unpack4(L.act ? ld4_data(a.w, a.bf16, L.i) : zero, wv);
+    unpack4(ldz4(a.om1 + L.i, L.act), o1);
+    unpack4(ldz4(a.gnext + L.i, L.act), gn);
+    unpack4(ldz4(a.gb + L.i, L.act), gb);
+    unpack4(ldz4(a.gw + L.i, L.act), gw);
+    float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const bool valid = L.act && L.x0 + q < V.nx;
+        const float d = xk[q] - xm[q];
+        const float tvg = (p0[q] - px[q]) + (p1[q] - py[q]) + (p2[q] - pz[q]);
+        const float g = wv[q] * ((xk[q] - bv[q]) + a.beta * d) + V.lambda_tv * tvg;
         const float delta = a.beta * d - V.tau * g;
-        const float zz = a.xk[i] + delta;
-        const float th = V.tau * V.lambda_l1 * a.om1[i];
+        const float zz = xk[q] + delta;
+        const float th = V.tau * V.lambda_l1 * o1[q];
         const bool pass = fabsf(zz) > th || th <= 0.f;
-        const float m = pass ? a.gnext[i] : 0.f;
-        a.m[i] = m;
+        m[q] = (valid && pass) ? gn[q] : 0.f;
         const float sg = zz > 0.f ? 1.f : (zz < 0.f ? -1.f : 0.f);
-        k1.add(-V.tau * a.om1[i] * sg * m);
-        k2.add(-V.tau * tvg * m);
-        a.gb[i] += V.tau * wv * m;
-        a.gw[i] += -V.tau * ((a.xk[i] - bv) + a.beta * d) * m;
+        s1 += -V.tau * o1[q] * sg * m[q];
+        s2 += -V.tau * tvg * m[q];
+        gb[q] += V.tau * wv[q] * m[q];
+        gw[q] += -V.tau * ((xk[q] - bv[q]) + a.beta * d) * m[q];
     }
-    double s[2] = {k1.value(), k2.value()};
-    block_sum<2>(s, scratch);
+    if (L.act) {
+        st4(a.m + L.i, m);
+        st4(a.gb + L.i, gb);
+        st4(a.gw + L.i, gw);
+    }
+    k1.add(s1);
+    k2.add(s2);
+    ADJ_WALK_END
+    double sm[2] = {k1.value(), k2.value()};
+    block_sum<2>(sm, scratch);
     if (threadIdx.x == 0) {
-        a.plane_part[(long long)blockIdx.x * 4 + 0] = s[0];
-        a.plane_part[(long long)blockIdx.x * 4 + 1] = s[1];
+        a.plane_part[(long long)blockIdx.x * 4 + 0] = sm[0];
+        a.plane_part[(long long)blockIdx.x * 4 + 1] = sm[1];
     }
 }
 
 __global__ void adjoint_hq_kernel(AdjParams a)
 {
-    const VolDesc V = a.vols[0];
-    const int z = blockIdx.x / AUX_SEG;
-    int r0, r1;
-    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
-    const Field M{a.m, nullptr, 0.f};
-    const long long S = a.stride;
-    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
-        const int x = t % V.nx, y = r0 + t / V.nx;
-        const long long i = lin(V, x, y, z);
-        float q[3];
-        grad_at(V, M, x, y, z, q);
-        const float g0 = a.G[i], g1 = a.G[S + i], g2 = a.G[2 * S + i];
-        const float s = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
-        const float om = a.omtv[i];
-        float h[3];
+    ADJ_WALK_BEGIN
+    float mc[4], ml[4], mu_[4], mw[4], g0[4], g1[4], g2[4], ot[4];
+    unpack4(ldz4(a.m + L.i, L.act), mc);
+    left4(a.m, L, mc, ml);
+    if (L.y >= 1) unpack4(ldz4(a.m + L.i - V.pitch, L.act), mu_);
+    else
+        for (int q = 0; q < 4; q++) mu_[q] = mc[q];
+    if (L.z >= 1) unpack4(ldz4(a.m + L.i - PS, L.act), mw);
+    else
+        for (int q = 0; q < 4; q++) mw[q] = mc[q];
+    unpack4(ldz4(a.G + L.i, L.act), g0);
+    unpack4(ldz4(a.G + S + L.i, L.act), g1);
+    unpack4(ldz4(a.G + 2 * S + L.i, L.act), g2);
+    unpack4(ldz4(a.omtv + L.i, L.act), ot);
+    float H[3][4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const bool valid = L.act && L.x0 + q < V.nx;
+        const float qx = mc[q] - ml[q], qy = mc[q] - mu_[q], qz = mc[q] - mw[q];
+        const float s = sqrtf(g0[q] * g0[q] + g1[q] * g1[q] + g2[q] * g2[q]);
+        float h0, h1, h2;
         if (s <= V.mu) {
-            const float c = om / V.mu;
-            h[0] = q[0] * c;
-            h[1] = q[1] * c;
-            h[2] = q[2] * c;
+            const float c = ot[q] / V.mu;
+            h0 = qx * c;
+            h1 = qy * c;
+            h2 = qz * c;
         } else {
             const float inv = 1.0f / s;
-            const float e0 = g0 * inv, e1 = g1 * inv, e2 = g2 * inv;
-            const float eq = e0 * q[0] + e1 * q[1] + e2 * q[2];
-            const float c = om * inv;
-            h[0] = (q[0] - e0 * eq) * c;
-            h[1] = (q[1] - e1 * eq) * c;
-            h[2] = (q[2] - e2 * eq) * c;
+            const float e0 = g0[q] * inv, e1 = g1[q] * inv, e2 = g2[q] * inv;
+            const float eq = e0 * qx + e1 * qy + e2 * qz;
+            const float c = ot[q] * inv;
+            h0 = (qx - e0 * eq) * c;
+            h1 = (qy - e1 * eq) * c;
+            h2 = (qz - e2 * eq) * c;
         }
-#pragma unroll
-        for (int c = 0; c < 3; c++) a.HQ[c * S + i] = h[c];
+        H[0][q] = valid ? h0 : 0.f;
+        H[1][q] = valid ? h1 : 0.f;
+        H[2][q] = valid ? h2 : 0.f;
     }
+    if (L.act) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) st4(a.HQ + c * S + L.i, H[c]);
+    }
+    ADJ_WALK_END
 }
 
 __global__ void adjoint_apply_kernel(AdjParams a)
 {
-    const VolDesc V = a.vols[0];
-    const int z = blockIdx.x / AUX_SEG;
-    int r0, r1;
-    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
-    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
-        const int x = t % V.nx, y = r0 + t / V.nx;
-        const long long i = lin(V, x, y, z);
-        const float dtv = div_stored(V, a.HQ, a.stride, x, y, z);
-        const float mv = a.m[i];
-        const float ybar = mv - V.tau * (ld_data(a.w, a.bf16, i) * mv + V.lambda_tv * dtv);
-        a.gcur[i] += (1.f + a.beta) * ybar;
-        a.gprev[i] += -a.beta * ybar;
+    ADJ_WALK_BEGIN
+    float h0[4], h1[4], h2[4], hx[4], hy[4], hz[4], m[4], wv[4], gc[4], gp[4] = {0.f, 0.f, 0.f, 0.f};
+    unpack4(ldz4(a.HQ + L.i, L.act), h0);
+    unpack4(ldz4(a.HQ + S + L.i, L.act), h1);
+    unpack4(ldz4(a.HQ + 2 * S + L.i, L.act), h2);
+    right4(V, a.HQ, L, h0, hx);
+    unpack4(ldz4(a.HQ + S + L.i + V.pitch, L.act && L.y + 1 < V.ny), hy);
+    unpack4(ldz4(a.HQ + 2 * S + L.i + PS, L.act && L.z + 1 < V.nz), hz);
+    unpack4(ldz4(a.m + L.i, L.act), m);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    unpack4(L.act ? ld4_data(a.w, a.bf16, L.i) : zero, wv);
+    unpack4(ldz4(a.gcur + L.i, L.act), gc);
+    const bool alias = a.gprev == a.gcur;  // k = 0: x_{-1} = x_0
+    if (!alias && !a.prev_fresh) unpack4(ldz4(a.gprev + L.i, L.act), gp);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const bool valid = L.act && L.x0 + q < V.nx;
+        const float dtv = (h0[q] - hx[q]) + (h1[q] - hy[q]) + (h2[q] - hz[q]);
+        const float ybar = valid ? m[q] - V.tau * (wv[q] * m[q] + V.lambda_tv * dtv) : 0.f;
+        gc[q] += (1.f + a.beta) * ybar;
+        if (alias) gc[q] += -a.beta * ybar;
+        else if (a.prev_fresh) gp[q] = -a.beta * ybar;
+        else gp[q] += -a.beta * ybar;
     }
+    if (L.act) {
+        st4(a.gcur + L.i, gc);
+        if (!alias) st4(a.gprev + L.i, gp);
+    }
+    ADJ_WALK_END
 }
 
 }  // namespace

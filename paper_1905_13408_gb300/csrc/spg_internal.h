@@ -134,7 +134,8 @@ struct AdjParams {
     float *gcur, *gprev, *gb, *gw;
     double *plane_part;      // [nplanes * AUX_SEG][4]
     float *G, *P, *HQ;       // scratch 3-vector fields, component c at c * stride
-    long long stride;
+    long long stride;        // a multiple of 4 elements (16-byte aligned components)
+    int prev_fresh;          // gprev has no earlier contribution: write it instead of adding
 };
 // Pass 1 and 2 of the adjoint (D y and p; mask, scalars, gb, gw): two kernels.
 cudaError_t launch_adjoint_mask(const AdjParams &a, cudaStream_t s);
