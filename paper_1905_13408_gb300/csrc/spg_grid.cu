@@ -15,8 +15,9 @@
 // or, mirrored, at -n, whichever lies in the stored half spectrum
 // [n][n][n/2+1] (both on the planes kx = 0 and kx = n/2). This halves both
 // the atomics and the accumulator against a full-spectrum scatter and gives
-// the same sums. One thread per image coefficient forms its deposits in
-// FP32 and adds them with FP64 atomics into an interleaved accumulator
+// the same sums. A CTA takes a 16 x 16 tile of one image's coefficients,
+// sums their FP32 deposits in a shared-memory box and adds each touched
+// point once, with FP64 atomics, into an interleaved accumulator
 // (Re num, Im num, N, unused: one 32-byte sector per grid point). A finishing
 // pass writes the Eq. 31 data term: N' = V N and
 // y = (-1)^(kx+ky+kz) num / sqrt(N), the sign moving the
@@ -24,6 +25,8 @@
 // solver's convention; n even).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <climits>
 #include <string>
 
 #include "spg.h"
@@ -63,80 +66,177 @@ __device__ __forceinline__ void deposit(double *acc, int n, int x, int y, int z,
     }
 }
 
-__global__ void __launch_bounds__(kThreads) scatter_kernel(int n, int m, const float *__restrict__ rot,
-                                                           const float2 *__restrict__ X,
-                                                           const float *__restrict__ ctf,
-                                                           const float *__restrict__ pw, int kernel, float h,
-                                                           double *acc)
+// One image coefficient's contribution: the first grid point of its support
+// on each axis and the per-axis kernel factors (the kernel factorises over
+// the axes: a product of 1-D Gaussians, or of 1-D hat functions); the
+// factors and the deposits are FP32 (the FP64 pipe is narrow), positions and
+// the nearest-point / floor decisions FP64 so they match a double-precision
+// reference.
+struct Sample {
+    int bx, by, bz;
+    float wx[3], wy[3], wz[3];
+    float vre, vim, vcc;
+};
+
+__device__ __forceinline__ void make_sample(int n, const float *__restrict__ rot, const float2 *__restrict__ X,
+                                            const float *__restrict__ ctf, const float *__restrict__ pw, int kernel,
+                                            float h, int img, int kx, int ky, Sample &S)
 {
-    const int rows = n / 2;  // ky = 0 .. n/2 - 1
-    const long long per_image = (long long)rows * n;
-    const long long total = per_image * m;
-    const float rmax2 = (n * 0.5f - 2.0f) * (n * 0.5f - 2.0f);
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int img = (int)(q / per_image);
-        const int rem = (int)(q % per_image);
-        const int ky = rem / n, col = rem % n;
-        const int kx = fidx(col, n);
-        if (ky == 0 && kx < 0) continue;  // the mate half of row 0
-        if ((float)(kx * kx + ky * ky) > rmax2) continue;
-        const bool self_mate = (kx == 0 && ky == 0);
-        const float *R = rot + (long long)img * 9;  // row-major 3x3; columns 0 and 1 span the image plane
-        // positions in double so the nearest-point decisions match a double-precision reference
-        const double px = __dadd_rn(__dmul_rn(R[0], kx), __dmul_rn(R[1], ky));
-        const double py = __dadd_rn(__dmul_rn(R[3], kx), __dmul_rn(R[4], ky));
-        const double pz = __dadd_rn(__dmul_rn(R[6], kx), __dmul_rn(R[7], ky));
-        const long long src = (long long)img * n * n + (long long)ky * n + col;
-        const float2 x = X[src];
-        const float c = ctf[src];
-        const float pc = pw ? pw[img] * c : c;
-        const float vre = pc * x.x, vim = pc * x.y, vcc = pc * c;
-        // The kernel weight factorises over the axes (a product of 1-D
-        // Gaussians, or of 1-D hat functions); the factors and the deposits
-        // are FP32 (the FP64 pipe is narrow), only the sums are FP64.
-        float wx[3], wy[3], wz[3];
-        int bx, by, bz;
-        if (kernel == 0) {
-            bx = __double2int_rn(px);
-            by = __double2int_rn(py);
-            bz = __double2int_rn(pz);
-            const float fx = (float)(px - bx), fy = (float)(py - by), fz = (float)(pz - bz);
-            const float ih = 1.0f / h;
+    const float *R = rot + (long long)img * 9;  // row-major 3x3; columns 0 and 1 span the image plane
+    const double px = __dadd_rn(__dmul_rn(R[0], kx), __dmul_rn(R[1], ky));
+    const double py = __dadd_rn(__dmul_rn(R[3], kx), __dmul_rn(R[4], ky));
+    const double pz = __dadd_rn(__dmul_rn(R[6], kx), __dmul_rn(R[7], ky));
+    const long long src = (long long)img * n * n + (long long)ky * n + wrap(kx, n);
+    const float2 x = X[src];
+    const float c = ctf[src];
+    const float pc = pw ? pw[img] * c : c;
+    S.vre = pc * x.x;
+    S.vim = pc * x.y;
+    S.vcc = pc * c;
+    if (kernel == 0) {
+        S.bx = __double2int_rn(px);
+        S.by = __double2int_rn(py);
+        S.bz = __double2int_rn(pz);
+        const float fx = (float)(px - S.bx), fy = (float)(py - S.by), fz = (float)(pz - S.bz);
+        const float ih = 1.0f / h;
 #pragma unroll
-            for (int d = 0; d < 3; d++) {
-                const float ex = fx - (d - 1), ey = fy - (d - 1), ez = fz - (d - 1);
-                wx[d] = expf(-ex * ex * ih);
-                wy[d] = expf(-ey * ey * ih);
-                wz[d] = expf(-ez * ez * ih);
-            }
-            bx -= 1;
-            by -= 1;
-            bz -= 1;
-        } else {
-            const double flx = floor(px), fly = floor(py), flz = floor(pz);
-            bx = (int)flx;
-            by = (int)fly;
-            bz = (int)flz;
-            const float fx = (float)(px - flx), fy = (float)(py - fly), fz = (float)(pz - flz);
-            wx[0] = 1.f - fx;
-            wx[1] = fx;
-            wy[0] = 1.f - fy;
-            wy[1] = fy;
-            wz[0] = 1.f - fz;
-            wz[1] = fz;
-            wx[2] = wy[2] = wz[2] = 0.f;
+        for (int d = 0; d < 3; d++) {
+            const float ex = fx - (d - 1), ey = fy - (d - 1), ez = fz - (d - 1);
+            S.wx[d] = expf(-ex * ex * ih);
+            S.wy[d] = expf(-ey * ey * ih);
+            S.wz[d] = expf(-ez * ez * ih);
         }
-        const int span = kernel == 0 ? 3 : 2;
-        for (int dz = 0; dz < span; dz++)
-            for (int dy = 0; dy < span; dy++) {
-                const float kyz = wy[dy] * wz[dz];
-                for (int dx = 0; dx < span; dx++) {
-                    const float K = wx[dx] * kyz;
-                    deposit(acc, n, bx + dx, by + dy, bz + dz, (double)(K * vre), (double)(K * vim),
-                            (double)(K * vcc), self_mate);
+        S.bx -= 1;
+        S.by -= 1;
+        S.bz -= 1;
+    } else {
+        const double flx = floor(px), fly = floor(py), flz = floor(pz);
+        S.bx = (int)flx;
+        S.by = (int)fly;
+        S.bz = (int)flz;
+        const float fx = (float)(px - flx), fy = (float)(py - fly), fz = (float)(pz - flz);
+        S.wx[0] = 1.f - fx;
+        S.wx[1] = fx;
+        S.wy[0] = 1.f - fy;
+        S.wy[1] = fy;
+        S.wz[0] = 1.f - fz;
+        S.wz[1] = fz;
+        S.wx[2] = S.wy[2] = S.wz[2] = 0.f;
+    }
+}
+
+// All deposits of one sample straight into the FP64 accumulator.
+__device__ __forceinline__ void deposit_sample(double *acc, int n, int span, const Sample &S, bool self_mate)
+{
+    for (int dz = 0; dz < span; dz++)
+        for (int dy = 0; dy < span; dy++) {
+            const float kyz = S.wy[dy] * S.wz[dz];
+            for (int dx = 0; dx < span; dx++) {
+                const float K = S.wx[dx] * kyz;
+                deposit(acc, n, S.bx + dx, S.by + dy, S.bz + dz, (double)(K * S.vre), (double)(K * S.vim),
+                        (double)(K * S.vcc), self_mate);
+            }
+        }
+}
+
+// One CTA grids a 16 x 16 tile of one image's half spectrum (kx in tile
+// columns, ky >= 0): the tile's deposits are first summed in FP32 in a
+// shared-memory box covering the support of all its samples, then each
+// touched box point goes to the FP64 accumulator once (with its mirror
+// point, as deposit() does). Neighbouring coefficients share most of their
+// support points, so this issues several times fewer global atomics than
+// depositing every sample directly. A tile whose box does not fit, and the
+// coefficient k = 0 (its own mate), deposit directly.
+constexpr int kTile = 16;
+constexpr int kBoxCap = 8192;  // box points (3 floats each: 96 KB)
+
+__global__ void __launch_bounds__(kTile * kTile) scatter_tile_kernel(int n, int m, const float *__restrict__ rot,
+                                                                     const float2 *__restrict__ X,
+                                                                     const float *__restrict__ ctf,
+                                                                     const float *__restrict__ pw, int kernel,
+                                                                     float h, double *acc)
+{
+    extern __shared__ float box[];  // [kBoxCap][3]
+    __shared__ int red[8][6];
+    __shared__ int geo[7];  // lo x, y, z; dims x, y, z; use box
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int span = kernel == 0 ? 3 : 2;
+    const int ntx = (n + kTile - 1) / kTile, nty = (n / 2 + kTile - 1) / kTile;
+    const long long ntiles = (long long)m * nty * ntx;
+    const float rmax2 = (n * 0.5f - 2.0f) * (n * 0.5f - 2.0f);
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int img = (int)(t / ((long long)nty * ntx));
+        const int rem = (int)(t % ((long long)nty * ntx));
+        const int kx = -n / 2 + (rem % ntx) * kTile + tid % kTile;
+        const int ky = (rem / ntx) * kTile + tid / kTile;
+        const bool ok = kx < n / 2 && ky < n / 2 && (ky > 0 || kx >= 0) && (float)(kx * kx + ky * ky) <= rmax2;
+        const bool self_mate = kx == 0 && ky == 0;
+        Sample S;
+        if (ok) make_sample(n, rot, X, ctf, pw, kernel, h, img, kx, ky, S);
+        // bounding box of the tile's supports (the self-mate sample goes direct)
+        const bool inbox = ok && !self_mate;
+        int v[6] = {inbox ? S.bx : INT_MAX, inbox ? S.by : INT_MAX, inbox ? S.bz : INT_MAX,
+                    inbox ? S.bx : INT_MIN, inbox ? S.by : INT_MIN, inbox ? S.bz : INT_MIN};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                const int u = __shfl_down_sync(0xffffffffu, v[c], o);
+                v[c] = c < 3 ? min(v[c], u) : max(v[c], u);
+            }
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < 6; c++) red[warp][c] = v[c];
+        __syncthreads();
+        if (tid == 0) {
+            int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+            for (int w = 0; w < kTile * kTile / 32; w++)
+                for (int c = 0; c < 3; c++) {
+                    lo[c] = min(lo[c], red[w][c]);
+                    hi[c] = max(hi[c], red[w][3 + c]);
+                }
+            long long vol = 0;
+            if (lo[0] != INT_MAX) {
+                vol = 1;
+                for (int c = 0; c < 3; c++) {
+                    geo[c] = lo[c];
+                    geo[3 + c] = hi[c] - lo[c] + span;
+                    vol *= geo[3 + c];
                 }
             }
+            geo[6] = (vol > 0 && vol <= kBoxCap) ? (int)vol : 0;
+        }
+        __syncthreads();
+        const int vol = geo[6];
+        if (vol > 0) {
+            for (int q = tid; q < 3 * vol; q += blockDim.x) box[q] = 0.f;
+            __syncthreads();
+            if (inbox) {
+                const int dx0 = S.bx - geo[0], dy0 = S.by - geo[1], dz0 = S.bz - geo[2];
+                for (int dz = 0; dz < span; dz++)
+                    for (int dy = 0; dy < span; dy++) {
+                        const float kyz = S.wy[dy] * S.wz[dz];
+                        float *row = box + 3 * (((dz0 + dz) * geo[4] + (dy0 + dy)) * geo[3] + dx0);
+                        for (int dx = 0; dx < span; dx++) {
+                            const float K = S.wx[dx] * kyz;
+                            atomicAdd(row + 3 * dx + 0, K * S.vre);
+                            atomicAdd(row + 3 * dx + 1, K * S.vim);
+                            atomicAdd(row + 3 * dx + 2, K * S.vcc);
+                        }
+                    }
+            }
+            __syncthreads();
+            for (int q = tid; q < vol; q += blockDim.x) {
+                const float re = box[3 * q], im = box[3 * q + 1], w = box[3 * q + 2];
+                if (re == 0.f && im == 0.f && w == 0.f) continue;
+                const int gx = geo[0] + q % geo[3], gy = geo[1] + (q / geo[3]) % geo[4], gz = geo[2] + q / (geo[3] * geo[4]);
+                deposit(acc, n, gx, gy, gz, (double)re, (double)im, (double)w, false);
+            }
+        } else if (inbox) {
+            deposit_sample(acc, n, span, S, false);
+        }
+        if (ok && self_mate) deposit_sample(acc, n, span, S, true);
+        __syncthreads();  // the box and geo are reused by the next tile
     }
 }
 
@@ -288,8 +388,16 @@ extern "C" spg_status spg_grid_add(spg_grid *g, int m, const float *rot, const v
         a.dev = dst;
         off += align256(a.bytes);
     }
-    const long long work = (long long)m * (n / 2) * n;
-    scatter_kernel<<<blocks_for(work), kThreads, 0, g->stream>>>(
+    // the tile kernel's shared box exceeds the default 48 KB (set per call: per device)
+    e = cudaFuncSetAttribute(scatter_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kBoxCap * 3 * (int)sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(g, e, "spg_grid_add: configure");
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles = (long long)m * ((n / 2 + kTile - 1) / kTile) * ((n + kTile - 1) / kTile);
+    const int grid = (int)std::min<long long>(tiles, (long long)std::max(nsm, 1) * 2 * 4);
+    scatter_tile_kernel<<<grid, kTile * kTile, kBoxCap * 3 * sizeof(float), g->stream>>>(
         n, m, static_cast<const float *>(in[0].dev), static_cast<const float2 *>(in[1].dev),
         static_cast<const float *>(in[2].dev), static_cast<const float *>(in[3].dev), g->kernel, g->h, g->acc);
     e = cudaGetLastError();
