@@ -15,7 +15,7 @@
 // or, mirrored, at -n, whichever lies in the stored half spectrum
 // [n][n][n/2+1] (both on the planes kx = 0 and kx = n/2). This halves both
 // the atomics and the accumulator against a full-spectrum scatter and gives
-// the same sums. A CTA takes a 16 x 16 tile of one image's coefficients,
+// the same sums. A CTA takes an 8 x 8 tile of one image's coefficients,
 // sums their FP32 deposits in a shared-memory box and adds each touched
 // point once, with FP64 atomics, into an interleaved accumulator
 // (Re num, Im num, N, unused: one 32-byte sector per grid point). A finishing
@@ -139,7 +139,7 @@ __device__ __forceinline__ void deposit_sample(double *acc, int n, int span, con
         }
 }
 
-// One CTA grids a 16 x 16 tile of one image's half spectrum (kx in tile
+// One CTA grids an 8 x 8 tile of one image's half spectrum (kx in tile
 // columns, ky >= 0): the tile's deposits are first summed in FP32 in a
 // shared-memory box covering the support of all its samples, then each
 // touched box point goes to the FP64 accumulator once (with its mirror
@@ -147,8 +147,8 @@ __device__ __forceinline__ void deposit_sample(double *acc, int n, int span, con
 // support points, so this issues several times fewer global atomics than
 // depositing every sample directly. A tile whose box does not fit, and the
 // coefficient k = 0 (its own mate), deposit directly.
-constexpr int kTile = 16;
-constexpr int kBoxCap = 8192;  // box points (3 floats each: 96 KB)
+constexpr int kTile = 8;
+constexpr int kBoxCap = 1536;  // box points (3 floats each: 18 KB)
 
 __global__ void __launch_bounds__(kTile * kTile) scatter_tile_kernel(int n, int m, const float *__restrict__ rot,
                                                                      const float2 *__restrict__ X,
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kTile * kTile) scatter_tile_kernel(int n, int 
                                                                      float h, double *acc)
 {
     extern __shared__ float box[];  // [kBoxCap][3]
-    __shared__ int red[8][6];
+    __shared__ int red[kTile * kTile / 32][6];
     __shared__ int geo[7];  // lo x, y, z; dims x, y, z; use box
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int span = kernel == 0 ? 3 : 2;
@@ -396,7 +396,7 @@ extern "C" spg_status spg_grid_add(spg_grid *g, int m, const float *rot, const v
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long tiles = (long long)m * ((n / 2 + kTile - 1) / kTile) * ((n + kTile - 1) / kTile);
-    const int grid = (int)std::min<long long>(tiles, (long long)std::max(nsm, 1) * 2 * 4);
+    const int grid = (int)std::min<long long>(tiles, (long long)std::max(nsm, 1) * 12 * 4);
     scatter_tile_kernel<<<grid, kTile * kTile, kBoxCap * 3 * sizeof(float), g->stream>>>(
         n, m, static_cast<const float *>(in[0].dev), static_cast<const float2 *>(in[1].dev),
         static_cast<const float *>(in[2].dev), static_cast<const float *>(in[3].dev), g->kernel, g->h, g->acc);
