@@ -619,6 +619,7 @@ class UnrolledSPG:
                 out = torch.empty_like(b_)
                 spg_unrolled(s.handle, K, out)
                 fctx.solver = s
+                fctx.scalar_like = (l1_, tv_)
                 return out
 
             @staticmethod
@@ -628,8 +629,9 @@ class UnrolledSPG:
                 gw = torch.empty_like(gx)
                 gs = spg_backward(s.handle, K, gx.contiguous(), gb, gw, ckpt_every)
                 s.close()
-                dev = gx.device
-                return gb, gw, torch.tensor(gs[0], device=dev), torch.tensor(gs[1], device=dev)
+                l1_, tv_ = fctx.scalar_like
+                return (gb, gw, torch.tensor(gs[0], dtype=l1_.dtype, device=l1_.device),
+                        torch.tensor(gs[1], dtype=tv_.dtype, device=tv_.device))
 
         l1 = lambda_l1 if isinstance(lambda_l1, torch.Tensor) else torch.tensor(float(lambda_l1))
         tv = lambda_tv if isinstance(lambda_tv, torch.Tensor) else torch.tensor(float(lambda_tv))
