@@ -405,11 +405,12 @@ def test_bounded_wait_times_out_and_context_survives():
     s.close()
 
 
-def test_adjoint_matches_oracle():
+@pytest.mark.parametrize("shape", [(12, 14, 20), (7, 9, 150), (5, 3, 131)])
+def test_adjoint_matches_oracle(shape):
     """Hand-written adjoint of K unrolled steps (weights 1, tau fixed)
-    against the oracle's FP64 adjoint."""
-    shape = (12, 14, 20)
-    vol = synth.make_volume(shape, blobs=6, radius=4, seed=70)
+    against the oracle's FP64 adjoint; rows of several 128-voxel chunks and
+    ragged ends exercise the row-vector passes' lane boundaries."""
+    vol = synth.make_volume(shape, blobs=6, radius=min(shape) / 3 + 1, seed=70)
     hyper = dict(HYPER, mu=0.02)
     K = 12
     b = torch.from_numpy(vol.b).cuda()
