@@ -241,8 +241,10 @@ def test_anchor_term_matches_oracle():
     assert rel_l2(x, ref.x) <= 2e-6
 
 
-def test_objective_and_reweight_match_oracle():
-    shape = (21, 34, 77)
+@pytest.mark.parametrize("shape", [(21, 34, 77), (9, 5, 261), (3, 200, 1), (4, 3, 2)])
+def test_objective_and_reweight_match_oracle(shape):
+    """Row-vector re-weighting and objective kernels: one and several
+    128-voxel chunks per row, ragged ends, single-column volumes."""
     vol = synth.make_volume(shape, blobs=20, radius=8, seed=8)
     rng = np.random.default_rng(9)
     x0 = np.where(rng.random(shape) < 0.3, 0.0, rng.standard_normal(shape)).astype(np.float32)
