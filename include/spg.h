@@ -242,7 +242,10 @@ spg_status spg_set_anchor(spg_ctx *ctx, int vol, float gamma, const float *x_anc
  * the data term, w b is the kernel-regression numerator (the inverse
  * transform of D y in Eq. 31, up to normalisation), so the paper's rules
  * read lambda_l1 = c1 RMS(w b) eps, lambda_tv = c2 RMS(w b) eps_tv and
- * gamma = c3 mean(w). Synchronises. */
+ * gamma = c3 mean(w). With the Fourier-domain data term (spg_set_data_fourier)
+ * the same rules read off the spectrum: out = {RMS(A^H D y), mean(N'),
+ * max(N'), min(N')} over the full spectrum (RMS by Parseval, A unitary).
+ * Synchronises. */
 spg_status spg_param_scales(spg_ctx *ctx, int vol, double out[4]);
 
 /* Set / read the current iterate of volume `vol` (float32, nx*ny*nz).

@@ -1044,6 +1044,23 @@ spg_status spg_param_scales(spg_ctx *ctx, int vol, double out[4])
     if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_param_scales: bad arguments");
     if (!ctx->data_set[vol]) return fail(ctx, SPG_ENOTREADY, "spg_param_scales: call spg_set_data first");
     const VolDesc &d = ctx->vols_h[vol];
+    if (ctx->fourier) {
+        // from the spectrum: RMS(A^H D y) (Parseval), mean, max and min of N
+        Scratch sc;
+        double *part = nullptr;
+        CK(sc.get(&part, (1024 * 4 + 4) * sizeof(double)), "alloc");
+        CK(launch_spec_scales(ctx->Ch, ctx->Nh, d.nz, d.ny, d.nx, part, part + 4096, ctx->stream), "scales");
+        ctx->launches += 2;
+        double o[4];
+        CK(cudaMemcpyAsync(o, part + 4096, sizeof(o), cudaMemcpyDeviceToHost, ctx->stream), "read scales");
+        CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+        const double V = (double)d.nx * d.ny * d.nz;
+        out[0] = std::sqrt(o[0]);
+        out[1] = o[1] / V;
+        out[2] = o[2];
+        out[3] = o[3];
+        return SPG_OK;
+    }
     CK(launch_scales(aux_params(ctx), vol, d.nz, ctx->B, ctx->W, ctx->bf16(), ctx->stream), "scales");
     ctx->launches += 1;
     double o[8];

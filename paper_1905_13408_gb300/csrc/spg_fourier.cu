@@ -84,6 +84,71 @@ __global__ void spec_value_kernel(const float2 *F, const float2 *Y, const float 
     }
 }
 
+// Sec. 2.5 scales from the spectrum, full-spectrum sums through the half
+// layout (coefficients 0 < h < nx/2 counted twice): partials[block] =
+// {sum |C|^2, sum N, max N, min N} with C = sqrt(N) y / sqrt(V), so that
+// sum |C|^2 = |D y|^2 / V = |A^H D y|^2 / V (A unitary) = RMS(A^H D y)^2.
+__global__ void spec_scales_kernel(const float2 *C, const float *N, int nz, int ny, int nx, double *partials)
+{
+    __shared__ double red[4][32];
+    const int nxh = nx / 2 + 1;
+    const long long n = (long long)nz * ny * nxh;
+    double s1 = 0.0, s2 = 0.0, mx = 0.0, mn = 1e300;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int h = (int)(i % nxh);
+        const double wgt = (h == 0 || (nx % 2 == 0 && h == nx / 2)) ? 1.0 : 2.0;
+        const double cx = C[i].x, cy = C[i].y, nv = N[i];
+        s1 += wgt * (cx * cx + cy * cy);
+        s2 += wgt * nv;
+        mx = fmax(mx, nv);
+        mn = fmin(mn, nv);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = s1;
+        red[1][threadIdx.x >> 5] = s2;
+        red[2][threadIdx.x >> 5] = mx;
+        red[3][threadIdx.x >> 5] = mn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0, c = 0.0, d = 1e300;
+        for (int w = 0; w < (int)(blockDim.x / 32); w++) {
+            a += red[0][w];
+            b += red[1][w];
+            c = fmax(c, red[2][w]);
+            d = fmin(d, red[3][w]);
+        }
+        double *p = partials + (long long)blockIdx.x * 4;
+        p[0] = a;
+        p[1] = b;
+        p[2] = c;
+        p[3] = d;
+    }
+}
+
+__global__ void sum_scales_kernel(const double *partials, int nblocks, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0.0, b = 0.0, c = 0.0, d = 1e300;
+        for (int i = 0; i < nblocks; i++) {
+            a += partials[i * 4 + 0];
+            b += partials[i * 4 + 1];
+            c = fmax(c, partials[i * 4 + 2]);
+            d = fmin(d, partials[i * 4 + 3]);
+        }
+        out[0] = a;
+        out[1] = b;
+        out[2] = c;
+        out[3] = d;
+    }
+}
+
 __global__ void sum_partials_kernel(const double *partials, int n, double *out)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -134,6 +199,15 @@ cudaError_t launch_spec_data_value(const float2 *F, const float2 *Y, const float
     const int g = 1024;
     spec_value_kernel<<<g, 256, 0, s>>>(F, Y, N, nz, ny, nx, scale, partials);
     sum_partials_kernel<<<1, 32, 0, s>>>(partials, g, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_scales(const float2 *C, const float *N, int nz, int ny, int nx, double *partials,
+                               double *out, cudaStream_t s)
+{
+    const int g = 1024;
+    spec_scales_kernel<<<g, 256, 0, s>>>(C, N, nz, ny, nx, partials);
+    sum_scales_kernel<<<1, 32, 0, s>>>(partials, g, out);
     return cudaGetLastError();
 }
 

@@ -163,6 +163,9 @@ cudaError_t launch_generic_step(const GenericParams &g, cudaStream_t s);
 // y = x_k + beta d_k over the whole pitched volume (cur and beta read on the device).
 cudaError_t launch_form_y(const DevState *st, const VolDesc *vols, const float *beta, float *const *xbuf,
                           float *y, long long n, cudaStream_t s);
+// out = {RMS(A^H D y)^2, sum N, max N, min N} over the full spectrum (partials: 1024 x 4 doubles).
+cudaError_t launch_spec_scales(const float2 *C, const float *N, int nz, int ny, int nx, double *partials,
+                               double *out, cudaStream_t s);
 // F <- N F scale - C over n half-spectrum coefficients.
 cudaError_t launch_spec_scale(float2 *F, const float *N, const float2 *C, long long n, float scale, cudaStream_t s);
 // F = Y * sqrt(N) * scale.

@@ -77,3 +77,19 @@ def test_constant_weight_matches_real_space_solve():
     xr = s.get_x(0).cpu().numpy()
     s.close()
     assert rel_l2(xf, xr.astype(np.float64)) <= 1e-5
+
+
+def test_fourier_param_scales():
+    """Sec. 2.5 scales with the Fourier-domain term: RMS(A^H D y) by
+    Parseval from the spectrum, and mean / max / min of N over the full
+    spectrum, against the real-space c of the oracle."""
+    shape = (16, 20, 24)
+    fv = synth.make_fourier_volume(shape, blobs=8, radius=5, seed=64)
+    s = spg.SPG(dict(shape=shape, **HYPER))
+    s.set_data_fourier(0, synth.half_spectrum(fv.y).astype(np.complex64), synth.half_spectrum(fv.N).astype(np.float32))
+    sc = s.param_scales(0)
+    s.close()
+    got = [sc["rms_wb"], sc["mean_w"], sc["max_w"], sc["min_w"]]
+    c = fourier.data_parts(fv.y, fv.N)
+    want = [np.sqrt(np.mean(c * c)), fv.N.mean(), fv.N.max(), fv.N.min()]
+    np.testing.assert_allclose(got, want, rtol=2e-5)
