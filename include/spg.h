@@ -166,7 +166,7 @@ spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg
  * point, transforms it (cuFFT, loaded at run time), scales the spectrum by
  * N and transforms back to get A^H N A y - A^H D y for the fused step;
  * L = max N + 12 lambda_tv max(omtv) / mu. Needs SPG_F32 data storage and
- * SPG_STORE_DELTA; certificate, adjoint and anchor are not available in this
+ * SPG_STORE_DELTA; certificate and adjoint are not available in this
  * mode. The objective history records the l1 and TV terms only (its data
  * column is 0); spg_objective returns all terms. spg_set_data switches back
  * to the real-space data term. Synchronises. */
@@ -233,8 +233,12 @@ const char *spg_backproject_last_error(void);
  * the volume by b' and w' (computed in float32 on the device, rounded to the
  * storage dtype). x_anchor is a float32 volume (host or device), typically
  * the previous maximisation step's solution; gamma >= 0. Objective values
- * reported afterwards omit the constant. Call after spg_set_data and before
- * spg_reweight. Synchronises. */
+ * reported afterwards omit the constant. With the Fourier-domain data term
+ * (after spg_set_data_fourier) the term enters the spectrum pass instead:
+ * its gradient 2 gamma (y - a) = A^H(2 gamma A y - 2 gamma A a), so the step
+ * uses N + 2 gamma and sqrt(N) y / sqrt(V) + 2 gamma (A a) / sqrt(V); the
+ * objective then includes gamma |x - a|^2 itself. Either way L grows by
+ * 2 gamma. Call after the data and before spg_reweight. Synchronises. */
 spg_status spg_set_anchor(spg_ctx *ctx, int vol, float gamma, const float *x_anchor);
 
 /* Parameter scales of Sec. 2.5 for volume `vol`, from the stored b and w:

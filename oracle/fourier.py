@@ -31,14 +31,18 @@ def data_value(x, y, N):
 
 
 def objective(x, y, N, om1, omtv, p):
+    """{data, l1, tv, total}; with p.gamma > 0 the data part includes the
+    implicit-gradient term gamma |x - anchor|^2 of Eq. 31 (the real-space
+    oracle's objective with w = 0 is exactly that term)."""
     o = oracle.objective(x, np.zeros(x.shape), np.zeros(x.shape), om1, omtv, p)
-    d = data_value(x, y, N)
+    d = data_value(x, y, N) + (o[0] if p.gamma > 0 else 0.0)
     return np.array([d, o[1], o[2], d + o[1] + o[2]])
 
 
 def solve(y, N, p, rounds, iters, x0=None, with_hist=True):
     """Reweighted FISTA solve of the Eq. 31 objective (same schedule as
-    oracle.solve): returns (x, hist[rounds, iters, 4], rstats[rounds, 6])."""
+    oracle.solve), with the gamma |x - anchor|^2 term when p.gamma > 0:
+    returns (x, hist[rounds, iters, 4], rstats[rounds, 6])."""
     shape = tuple(p.shape)
     x = np.zeros(shape) if x0 is None else np.array(x0, dtype=np.float64)
     c = data_parts(y, N)
@@ -47,7 +51,7 @@ def solve(y, N, p, rounds, iters, x0=None, with_hist=True):
     beta = oracle.beta_table(iters, p.momentum)
     for r in range(rounds):
         om1, omtv, st = oracle.reweight(x, p)
-        L = float(N.max()) + 12.0 * p.lambda_tv * st[0] / p.mu
+        L = float(N.max()) + 12.0 * p.lambda_tv * st[0] / p.mu + (2.0 * p.gamma if p.gamma > 0 else 0.0)
         tau = 1.0 / L
         rst[r, :4] = st
         rst[r, 4:] = (L, tau)
@@ -57,6 +61,8 @@ def solve(y, N, p, rounds, iters, x0=None, with_hist=True):
                 hist[r, k] = objective(x, y, N, om1, omtv, p)
             yk = x + beta[k] * (x - xp)
             g = grad_data(yk, N, c) + p.lambda_tv * oracle.tv_grad(yk, omtv, p)
+            if p.gamma > 0:  # implicit-gradient term of Eq. 22 / Eq. 31
+                g = g + 2.0 * p.gamma * (yk - p.anchor)
             z = yk - tau * g
             t = tau * p.lambda_l1 * om1
             xn = np.sign(z) * np.maximum(np.abs(z) - t, 0.0)

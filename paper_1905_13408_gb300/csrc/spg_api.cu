@@ -99,6 +99,10 @@ struct spg_ctx {
     float2 *Yh = nullptr;    // data spectrum y
     float *Nh = nullptr;     // weights N
     float2 *Ch = nullptr;    // data spectrum sqrt(N) y / sqrt(V) subtracted in the spectrum pass
+    float gamma_f = 0.f;     // implicit-gradient weight with the Fourier-domain term
+    float *Anc = nullptr;    // its anchor (pitched volume)
+    float *Nst = nullptr;    // N + 2 gamma and C + 2 gamma A a / V: what the step uses when gamma_f > 0
+    float2 *Cst = nullptr;
     float *Nmax = nullptr;
     double *fpart = nullptr; // reduction partials of the Fourier data value
     cufftHandle pr2c = 0, pc2r = 0;
@@ -156,7 +160,7 @@ void free_all(spg_ctx *c)
         spg::cufft_api().destroy(c->pr2c);
         spg::cufft_api().destroy(c->pc2r);
     }
-    void *fs[] = {c->Ybuf, c->Fh, c->Yh, c->Nh, c->Ch, c->Nmax, c->fpart};
+    void *fs[] = {c->Ybuf, c->Fh, c->Yh, c->Nh, c->Ch, c->Nmax, c->fpart, c->Anc, c->Nst, c->Cst};
     for (void *p : fs)
         if (p) cudaFree(p);
     void *ps[] = {c->vols_d, c->items_d, c->sched_d, c->tmaps_d, c->plane_vol_d, c->X[0], c->X[1], c->X[2], c->X[3], c->B, c->W,
@@ -526,7 +530,9 @@ cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
         const spg::CufftApi &cf = spg::cufft_api();
         if (cf.exec_r2c(ctx->pr2c, ctx->Ybuf, reinterpret_cast<cufftComplex *>(ctx->Fh)) != CUFFT_SUCCESS)
             return cudaErrorUnknown;
-        e = launch_spec_scale(ctx->Fh, ctx->Nh, ctx->Ch, ctx->nhalf, (float)(1.0 / V), ctx->stream);
+        const bool anc = ctx->gamma_f > 0.f;
+        e = launch_spec_scale(ctx->Fh, anc ? ctx->Nst : ctx->Nh, anc ? ctx->Cst : ctx->Ch, ctx->nhalf, (float)(1.0 / V),
+                              ctx->stream);
         if (e != cudaSuccess) return e;
         if (cf.exec_c2r(ctx->pc2r, reinterpret_cast<cufftComplex *>(ctx->Fh), static_cast<float *>(ctx->B)) !=
             CUFFT_SUCCESS)
@@ -1011,6 +1017,7 @@ spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const
         ctx->gexec = nullptr;
     }
     ctx->fourier = true;
+    ctx->gamma_f = 0.f;  // new data: no anchor term until spg_set_anchor
     ctx->y_fresh = false;
     ctx->data_set[0] = 1;
     ctx->reweighted = false;
@@ -1024,8 +1031,41 @@ spg_status spg_set_anchor(spg_ctx *ctx, int vol, float gamma, const float *x_anc
     if (vol < 0 || vol >= ctx->nvol || !x_anchor || !(gamma >= 0.f) || !std::isfinite(gamma))
         return fail(ctx, SPG_EINVAL, "spg_set_anchor: bad arguments");
     if (!ctx->data_set[vol]) return fail(ctx, SPG_ENOTREADY, "spg_set_anchor: call spg_set_data first");
-    if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_set_anchor: not available with the Fourier-domain data term");
     const VolDesc &d = ctx->vols_h[vol];
+    if (ctx->fourier) {
+        // gamma |x - a|^2 enters the spectrum pass (N + 2 gamma, C + 2 gamma A a / V) and L (+ 2 gamma)
+        if (!ctx->Anc) {
+            CK(dalloc(&ctx->Anc, (size_t)ctx->total * sizeof(float)), "alloc");
+            CK(dalloc(&ctx->Nst, (size_t)ctx->nhalf * sizeof(float)), "alloc");
+            CK(dalloc(&ctx->Cst, (size_t)ctx->nhalf * sizeof(float2)), "alloc");
+            CK(cudaMemsetAsync(ctx->Anc, 0, (size_t)ctx->total * sizeof(float), ctx->stream), "memset");
+        }
+        spg_status s = copy_volume_in(ctx, ctx->Anc, 4, d, x_anchor);
+        if (s != SPG_OK) return s;
+        const double V = (double)d.nx * d.ny * d.nz;
+        if (spg::cufft_api().exec_r2c(ctx->pr2c, ctx->Anc, reinterpret_cast<cufftComplex *>(ctx->Fh)) != CUFFT_SUCCESS)
+            return fail(ctx, SPG_ECUDA, "spg_set_anchor: transform");
+        CK(launch_spec_anchor(ctx->Nh, ctx->Ch, ctx->Fh, ctx->nhalf, 2.f * gamma, (float)(1.0 / V), ctx->Nst, ctx->Cst,
+                              ctx->stream),
+           "anchor spectrum");
+        ctx->launches += 1;
+        float nmax = 0.f;
+        CK(launch_spec_max(ctx->Nh, ctx->nhalf, ctx->Nmax, ctx->stream), "max N");
+        ctx->launches += 1;
+        CK(cudaMemcpyAsync(&nmax, ctx->Nmax, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream), "read max N");
+        CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+        const double m = (double)nmax + 2.0 * gamma;
+        CK(cudaMemcpyAsync(ctx->maxw_d, &m, sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "write max N");
+        CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+        ctx->gamma_f = gamma;
+        if (ctx->gexec) {
+            cudaGraphExecDestroy(ctx->gexec);  // the spectrum pass reads other buffers now
+            ctx->gexec = nullptr;
+        }
+        ctx->y_fresh = false;
+        ctx->reweighted = false;
+        return SPG_OK;
+    }
     // stage the anchor in the l1-weight buffer (re-set by the next spg_reweight)
     spg_status s = copy_volume_in(ctx, ctx->OM1, 4, d, x_anchor);
     if (s != SPG_OK) return s;
@@ -1170,6 +1210,16 @@ spg_status spg_objective(spg_ctx *ctx, int vol, double out[4])
         CK(cudaMemcpyAsync(&dv, ctx->fpart + 1024, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "read");
         CK(cudaStreamSynchronize(ctx->stream), "synchronise");
         o[0] = dv;
+        if (ctx->gamma_f > 0.f) {  // + gamma |x - a|^2
+            CK(launch_sq_diff(ctx->X[ctx->cur()], ctx->Anc, d.nx, d.pitch, (long long)d.nz * d.ny * d.pitch, ctx->fpart,
+                              ctx->fpart + 1024, ctx->stream),
+               "anchor value");
+            ctx->launches += 2;
+            double sq = 0;
+            CK(cudaMemcpyAsync(&sq, ctx->fpart + 1024, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "read");
+            CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+            o[0] += (double)ctx->gamma_f * sq;
+        }
         o[3] = o[0] + o[1] + o[2];
     }
     spg_status s = device_status(ctx);

@@ -49,6 +49,40 @@ __global__ void spec_prep_kernel(float2 *F, const float2 *Y, const float *N, lon
     }
 }
 
+// The implicit-gradient term gamma |x - a|^2 (Eq. 22, Eq. 31) in the
+// spectrum pass: its gradient 2 gamma (y - a) = A^H (2 gamma A y - 2 gamma A a),
+// so the step uses N + 2 gamma and C + 2 gamma FA / V (FA the unnormalised
+// transform of the anchor a).
+__global__ void spec_anchor_kernel(const float *N, const float2 *C, const float2 *FA, long long n, float two_gamma,
+                                   float inv_v, float *Nst, float2 *Cst)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        Nst[i] = N[i] + two_gamma;
+        const float2 c = C[i], f = FA[i];
+        Cst[i] = make_float2(fmaf(two_gamma * inv_v, f.x, c.x), fmaf(two_gamma * inv_v, f.y, c.y));
+    }
+}
+
+// sum over the volume's voxels of (x - a)^2 (pitched layout, padding skipped).
+__global__ void sq_diff_kernel(const float *x, const float *a, int nx, int pitch, long long n, double *partials)
+{
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if ((int)(i % pitch) >= nx) continue;
+        const double d = (double)x[i] - (double)a[i];
+        acc += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); w++) s += red[w];
+        partials[blockIdx.x] = s;
+    }
+}
+
 __global__ void spec_max_kernel(const float *N, long long n, unsigned int *out)
 {
     float m = 0.f;
@@ -208,6 +242,22 @@ cudaError_t launch_spec_scales(const float2 *C, const float *N, int nz, int ny, 
     const int g = 1024;
     spec_scales_kernel<<<g, 256, 0, s>>>(C, N, nz, ny, nx, partials);
     sum_scales_kernel<<<1, 32, 0, s>>>(partials, g, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_anchor(const float *N, const float2 *C, const float2 *FA, long long n, float two_gamma,
+                               float inv_v, float *Nst, float2 *Cst, cudaStream_t s)
+{
+    spec_anchor_kernel<<<grid_for(n), 256, 0, s>>>(N, C, FA, n, two_gamma, inv_v, Nst, Cst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sq_diff(const float *x, const float *a, int nx, int pitch, long long n, double *partials,
+                           double *out, cudaStream_t s)
+{
+    const int g = 1024;
+    sq_diff_kernel<<<g, 256, 0, s>>>(x, a, nx, pitch, n, partials);
+    sum_partials_kernel<<<1, 32, 0, s>>>(partials, g, out);
     return cudaGetLastError();
 }
 

@@ -166,6 +166,12 @@ cudaError_t launch_form_y(const DevState *st, const VolDesc *vols, const float *
 // out = {RMS(A^H D y)^2, sum N, max N, min N} over the full spectrum (partials: 1024 x 4 doubles).
 cudaError_t launch_spec_scales(const float2 *C, const float *N, int nz, int ny, int nx, double *partials,
                                double *out, cudaStream_t s);
+// Nst = N + two_gamma, Cst = C + two_gamma inv_v FA (the implicit-gradient term in the spectrum pass).
+cudaError_t launch_spec_anchor(const float *N, const float2 *C, const float2 *FA, long long n, float two_gamma,
+                               float inv_v, float *Nst, float2 *Cst, cudaStream_t s);
+// *out = sum of (x - a)^2 over the volume's voxels (pitched, n elements; partials: 1024 doubles).
+cudaError_t launch_sq_diff(const float *x, const float *a, int nx, int pitch, long long n, double *partials,
+                           double *out, cudaStream_t s);
 // F <- N F scale - C over n half-spectrum coefficients.
 cudaError_t launch_spec_scale(float2 *F, const float *N, const float2 *C, long long n, float scale, cudaStream_t s);
 // F = Y * sqrt(N) * scale.

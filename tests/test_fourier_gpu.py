@@ -93,3 +93,30 @@ def test_fourier_param_scales():
     c = fourier.data_parts(fv.y, fv.N)
     want = [np.sqrt(np.mean(c * c)), fv.N.mean(), fv.N.max(), fv.N.min()]
     np.testing.assert_allclose(got, want, rtol=2e-5)
+
+
+def test_fourier_anchor_matches_oracle():
+    """The implicit-gradient term gamma |x - a|^2 with the Fourier-domain data
+    term (Eq. 31): the spectrum pass uses N + 2 gamma and the anchor's
+    transform; iterate and data-plus-anchor value against the oracle."""
+    shape = (20, 24, 28)
+    fv = synth.make_fourier_volume(shape, blobs=10, radius=5, seed=65)
+    hyper = dict(HYPER, mu=0.02)
+    anchor = (0.2 * np.random.default_rng(66).standard_normal(shape)).astype(np.float32)
+    gamma = 0.3 * float(fv.N.mean())
+    s = spg.SPG(dict(shape=shape, **hyper))
+    s.set_data_fourier(0, synth.half_spectrum(fv.y).astype(np.complex64), synth.half_spectrum(fv.N).astype(np.float32))
+    s.set_anchor(0, gamma, anchor)
+    s.solve(2, 40)
+    x = s.get_x(0).cpu().numpy().astype(np.float64)
+    obj = s.objective(0)
+    st = s.round_stats(0)
+    s.close()
+    p = oracle.Params(shape, **hyper, gamma=gamma, anchor=anchor.astype(np.float64))
+    xr, hr, rr = fourier.solve(fv.y, fv.N, p, 2, 40, with_hist=False)
+    err = rel_l2(x, xr)
+    print(f"fourier + anchor: rel-L2 {err:.3e}")
+    assert err <= 1e-5
+    np.testing.assert_allclose(st[4], rr[1, 4], rtol=1e-6)  # L of round 2 includes 2 gamma
+    want = fourier.data_value(x, fv.y, fv.N) + gamma * float(((x - anchor) ** 2).sum())
+    np.testing.assert_allclose(obj[0], want, rtol=1e-5)

@@ -7,17 +7,20 @@ from oracle import fourier
 from paper_1905_13408_gb300 import synth
 
 
-def test_constant_weight_reduces_to_the_real_space_solve():
+@pytest.mark.parametrize("gamma", [0.0, 0.7])
+def test_constant_weight_reduces_to_the_real_space_solve(gamma):
     """With N = w0 everywhere and y = sqrt(w0) A b, 1/2 |y - D A x|^2 equals
     1/2 w0 |x - b|^2 (A unitary), so the Fourier-form solve must reproduce the
-    pinned real-space oracle exactly (up to FFT rounding)."""
+    pinned real-space oracle exactly (up to FFT rounding), also with the
+    implicit-gradient term gamma |x - a|^2 (two implementations of it)."""
     shape = (10, 12, 14)
     vol = synth.make_volume(shape, blobs=6, radius=3, seed=51)
     w0 = 2.5
     N = np.full(shape, w0)
     b = vol.b.astype(np.float64)
     y = np.sqrt(w0) * np.fft.fftn(b, norm="ortho")
-    p = oracle.Params(shape, mu=0.02)
+    anchor = np.random.default_rng(50).standard_normal(shape) * 0.3
+    p = oracle.Params(shape, mu=0.02, gamma=gamma, anchor=anchor if gamma > 0 else None)
     xf, hf, rf = fourier.solve(y, N, p, 2, 30)
     ref = oracle.solve(b, np.full(shape, w0), p, 2, 30)
     np.testing.assert_allclose(xf, ref.x, atol=1e-11)
