@@ -404,7 +404,7 @@ def run_spg(args):
     if not adopted:
         args.no_e2e = args.no_gap = args.no_cpu_baseline = True
     if not args.no_e2e:
-        e2e = measure_e2e(vol, hyper, args, stream)
+        e2e = measure_e2e(vol, hyper, args, stream, world=world)
     gap = None
     if not args.no_gap and rank == 0:
         gap = time_to_gap(vol, hyper, args, stream)
@@ -430,14 +430,16 @@ def run_spg(args):
     return 0
 
 
-def measure_e2e(vol, hyper, args, stream, iters=100, reps=3):
+def measure_e2e(vol, hyper, args, stream, iters=100, reps=3, world=1):
     """Through the public API with host buffers. Each step uploads b and w from
     pinned host memory (with the device validation), re-weights, runs `iters`
     fused iterations, reads the objective and downloads x to pinned host
     memory. Two contexts on two streams alternate between steps, so a step's
     upload and the previous step's objective and download overlap iterations
     (the serving pattern); the same steps run back to back on one context are
-    reported beside it."""
+    reported beside it. With several ranks every rank runs its own volume;
+    the times are taken between barriers, their maximum over ranks is the
+    job's time and the rate counts all ranks' voxels."""
     import torch
 
     from paper_1905_13408_gb300 import spg
@@ -456,9 +458,15 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=3):
     torch.cuda.synchronize()
     nvox = vol.b.size
 
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
     # one context, steps back to back
     s = ctxs[0]
     phases = {"upload_validate": 0.0, "reweight_iterate_objective": 0.0, "download": 0.0}
+    barrier()
     t0 = time.perf_counter()
     for _ in range(reps):
         ta = time.perf_counter()
@@ -474,12 +482,14 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=3):
         phases["upload_validate"] += tb - ta
         phases["reweight_iterate_objective"] += tc - tb
         phases["download"] += td - tc
-    seq = nvox * iters * reps / (time.perf_counter() - t0) / 1e9
+    t_seq = max_over_ranks(time.perf_counter() - t0, world)
+    seq = world * nvox * iters * reps / t_seq / 1e9
 
     # two contexts: step i+1 is uploaded and enqueued while step i iterates,
     # and step i's objective and download overlap step i+1's iterations
     steps = 2 * reps
     torch.cuda.synchronize()
+    barrier()
     t0 = time.perf_counter()
     ctxs[0].set_data(0, b_h, w_h)
     ctxs[0].reweight()
@@ -493,12 +503,12 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=3):
         cur.objective(0)               # synchronises cur's stream
         cur.get_x(0, x_h)
         streams[i % 2].synchronize()
-    dt = time.perf_counter() - t0
+    dt = max_over_ranks(time.perf_counter() - t0, world)
     for c in ctxs:
         c.close()
-    return {"value": nvox * iters * steps / dt / 1e9, "unit": UNIT,
-            "h2d_bytes_per_step": int(b_h.numel() * 4 + w_h.numel() * 4),
-            "d2h_bytes_per_step": int(x_h.numel() * 4 + 4 * 8),
+    return {"value": world * nvox * iters * steps / dt / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": int(world * (b_h.numel() * 4 + w_h.numel() * 4)),
+            "d2h_bytes_per_step": int(world * (x_h.numel() * 4 + 4 * 8)),
             "step": f"upload b,w from pinned host (validated), re-weight, {iters} fused iterations, objective, "
                     f"download x; two contexts on two streams alternate, so a step's upload and the previous "
                     f"step's objective and download overlap iterations",
