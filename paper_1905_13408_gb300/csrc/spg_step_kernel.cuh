@@ -172,13 +172,14 @@ __device__ __forceinline__ void ld_data(const unsigned char *tile, int idx, floa
         ld_vec<VX>(reinterpret_cast<const float *>(tile) + idx, v);
     } else {
         const uint16_t *t = reinterpret_cast<const uint16_t *>(tile) + idx;
+        // the low half moves up by 16 bits, the high half is masked in place
         if constexpr (VX == 4) {
             uint2 u = *reinterpret_cast<const uint2 *>(t);
-            v[0] = bf16_bits_to_f32(u.x & 0xffffu); v[1] = bf16_bits_to_f32(u.x >> 16);
-            v[2] = bf16_bits_to_f32(u.y & 0xffffu); v[3] = bf16_bits_to_f32(u.y >> 16);
+            v[0] = __uint_as_float(u.x << 16); v[1] = __uint_as_float(u.x & 0xffff0000u);
+            v[2] = __uint_as_float(u.y << 16); v[3] = __uint_as_float(u.y & 0xffff0000u);
         } else if constexpr (VX == 2) {
             uint32_t u = *reinterpret_cast<const uint32_t *>(t);
-            v[0] = bf16_bits_to_f32(u & 0xffffu); v[1] = bf16_bits_to_f32(u >> 16);
+            v[0] = __uint_as_float(u << 16); v[1] = __uint_as_float(u & 0xffff0000u);
         } else {
             v[0] = bf16_bits_to_f32(t[0]);
         }
@@ -455,7 +456,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
                 out[i] = xz[i] + inc[i];
                 if constexpr (DOT) rsum = fmaf(fmaf(beta, dz[i], -inc[i]), inc[i], rsum);  // (y - x+).(x+ - x)
                 if constexpr (REC) {
-                    if constexpr (!FOURIER) dsum = fmaf(0.5f * ww[i] * res, res, dsum);
+                    if constexpr (!FOURIER) dsum = fmaf(ww[i] * res, res, dsum);  // halved once per item
                     lsum = fmaf(oo[i], fabsf(xz[i]), lsum);
                 }
             }
@@ -492,7 +493,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
 
     if (!aborted && (REC || DOT)) {
         // block reduction of the item's sums, fixed order
-        double v[4] = {kd.value(), kl.value(), kt.value(), kr.value()};
+        double v[4] = {0.5 * kd.value(), kl.value(), kt.value(), kr.value()};
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
