@@ -88,7 +88,7 @@ typedef struct {
     float lambda_tv;   /* beta of Eq. 8-11 */
     float mu;          /* Nesterov smoothing parameter of Eq. 14 */
     float eps;         /* epsilon of Eq. 9/11 for the l1 weights */
-    float eps_tv;      /* epsilon' of Eq. 31 for the TV weights */
+    float eps_tv;      /* epsilon' of the TV weights (Sec. 2.5; the paper uses eps' <= eps) */
 } spg_volume_params;
 
 /* Context-wide options. Zero-initialised options are valid defaults. */
@@ -107,7 +107,7 @@ typedef struct {
                                  extrapolation (per volume, whenever <y_k - x_{k+1}, x_{k+1} - x_k> > 0,
                                  O'Donoghue and Candes 2015); decided on the device every iteration */
     int readings;             /* 0: the adopted readings of the paper (the fused path); otherwise an
-                                 OR of SPG_READ_* flags, run by a plain two-pass path (below) */
+                                 OR of SPG_READ_* flags, run by a plain one-kernel step (below) */
 } spg_options;
 
 /* Alternative readings of the paper, for spg_options.readings. The adopted
@@ -130,8 +130,9 @@ typedef struct {
 enum { SPG_READ_FORWARD = 1, SPG_READ_PERIODIC = 2, SPG_READ_POST_DIV = 4 };
 
 /* Tile codes for spg_options.tile: x extent = 32 * vx, y extent = ty.
- * SPG_TILE_128x7_S4 is the 128x7 tile with a 4-deep copy pipeline (3 is the
- * default depth of that tile). */
+ * SPG_TILE_128x7_S4 is the 128x7 tile with a 4-deep copy pipeline, the
+ * built-in choice for volumes that fill 128-wide tiles; SPG_TILE_128x7 is the
+ * same tile with 3 stages. */
 enum { SPG_TILE_AUTO = 0, SPG_TILE_128x8 = 1, SPG_TILE_128x4 = 2, SPG_TILE_64x8 = 3,
        SPG_TILE_64x4 = 4, SPG_TILE_128x7 = 6, SPG_TILE_128x15 = 7, SPG_TILE_64x7 = 8,
        SPG_TILE_128x7_S4 = 9 };
@@ -142,7 +143,8 @@ enum { SPG_TILE_AUTO = 0, SPG_TILE_128x8 = 1, SPG_TILE_128x4 = 2, SPG_TILE_64x8 
  * the two gold-standard half-maps independently, Sec. 2 and Sec. 2.3).
  * params: one (or nvol) descriptions, copied. opt: NULL for defaults.
  * stream: a cudaStream_t or NULL. On success *out owns all device memory it
- * allocated (about 7 float32 volumes per volume). Errors: SPG_EINVAL for a
+ * allocated (8 volumes of 4 bytes per voxel with SPG_STORE_DELTA, 7 with
+ * SPG_STORE_PREV; b and w take 2 bytes with SPG_BF16). Errors: SPG_EINVAL for a
  * non-positive size or parameter, SPG_ENOMEM, SPG_ECUDA. */
 spg_status spg_create(const spg_volume_params *params, const spg_options *opt, void *stream,
                       spg_ctx **out);
@@ -162,10 +164,11 @@ spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg
  * (A x = FFT(x) / sqrt(nx ny nz)) and D = diag sqrt(N). y_half (complex64,
  * interleaved re/im) and N_half (float32, N >= 0) hold the real-to-complex
  * half spectrum [nz][ny][nx/2+1] of a Hermitian y and a centro-symmetric N;
- * host or device pointers, copied. Each iteration then forms the extrapolated
- * point, transforms it (cuFFT, loaded at run time), scales the spectrum by
- * N and transforms back to get A^H N A y - A^H D y for the fused step;
- * L = max N + 12 lambda_tv max(omtv) / mu. Needs SPG_F32 data storage and
+ * host or device pointers, copied. Each iteration then transforms the
+ * extrapolated point y_k (cuFFT, loaded at run time; y_k is written by the
+ * previous fused step), forms the residual spectrum N A y_k - D y and
+ * transforms back to get the data gradient A^H (N A y_k - D y) for the fused
+ * step; L = max N + 12 lambda_tv max(omtv) / mu. Needs SPG_F32 data storage and
  * SPG_STORE_DELTA; certificate and adjoint are not available in this
  * mode. The objective history records the l1 and TV terms only (its data
  * column is 0); spg_objective returns all terms. spg_set_data switches back
