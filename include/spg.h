@@ -299,9 +299,10 @@ spg_status spg_counters(spg_ctx *ctx, long long *k_total, int *k_round);
 
 /* Checkpoint / resume. A state blob holds, for every volume, x_k, then d_k
  * (SPG_STORE_DELTA) or x_{k-1} (SPG_STORE_PREV), om1, omtv, tau, and the
- * counters; spg_set_state on a context created with
- * the same parameters continues bit-identically. With blob == NULL,
- * spg_get_state only sets *size. Synchronise. */
+ * counters; spg_set_state on a context created with the same parameters
+ * continues bit-identically. The data (b and w, or the Fourier-domain
+ * spectra and anchor) are not in the blob: a new context needs them set
+ * first. With blob == NULL, spg_get_state only sets *size. Synchronise. */
 spg_status spg_get_state(spg_ctx *ctx, void *blob, size_t *size);
 spg_status spg_set_state(spg_ctx *ctx, const void *blob, size_t size);
 
