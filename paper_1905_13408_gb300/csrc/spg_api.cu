@@ -103,6 +103,7 @@ struct spg_ctx {
     float *Anc = nullptr;    // its anchor (pitched volume)
     float *Nst = nullptr;    // N + 2 gamma and C + 2 gamma A a / V: what the step uses when gamma_f > 0
     float2 *Cst = nullptr;
+    float *certQ = nullptr;  // 3-vector field of the certificate passes (allocated on first use)
     float *Nmax = nullptr;
     double *fpart = nullptr; // reduction partials of the Fourier data value
     cufftHandle pr2c = 0, pc2r = 0;
@@ -160,7 +161,7 @@ void free_all(spg_ctx *c)
         spg::cufft_api().destroy(c->pr2c);
         spg::cufft_api().destroy(c->pc2r);
     }
-    void *fs[] = {c->Ybuf, c->Fh, c->Yh, c->Nh, c->Ch, c->Nmax, c->fpart, c->Anc, c->Nst, c->Cst};
+    void *fs[] = {c->Ybuf, c->Fh, c->Yh, c->Nh, c->Ch, c->Nmax, c->fpart, c->Anc, c->Nst, c->Cst, c->certQ};
     for (void *p : fs)
         if (p) cudaFree(p);
     void *ps[] = {c->vols_d, c->items_d, c->sched_d, c->tmaps_d, c->plane_vol_d, c->X[0], c->X[1], c->X[2], c->X[3], c->B, c->W,
@@ -1278,9 +1279,10 @@ spg_status spg_certificate(spg_ctx *ctx, int vol, double *out)
     const int k = (c + ctx->nbuf() - 1) % ctx->nbuf();
     const float *xb[4] = {ctx->X[c], ctx->X[k], ctx->xd() ? nullptr : ctx->X[ctx->aux_of(k)],
                           ctx->xd() ? ctx->X[ctx->aux_of(k)] : nullptr};
-    CK(launch_certificate(aux_params(ctx), xb, ctx->beta_d, ctx->B, ctx->W, ctx->bf16(), ctx->OMTV, ctx->stream),
+    if (!ctx->certQ) CK(dalloc(&ctx->certQ, (size_t)ctx->total * 3 * sizeof(float)), "alloc certificate field");
+    CK(launch_certificate4(aux_params(ctx), xb, ctx->W, ctx->bf16(), ctx->OMTV, ctx->certQ, ctx->total, ctx->stream),
        "certificate");
-    ctx->launches += 1;
+    ctx->launches += 2;
     double o[8];
     CK(cudaMemcpyAsync(o, ctx->vol_out_d + (size_t)vol * 8, sizeof(o), cudaMemcpyDeviceToHost, ctx->stream),
        "read certificate");

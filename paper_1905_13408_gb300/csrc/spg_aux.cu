@@ -711,54 +711,6 @@ __global__ void objective4_kernel(AuxParams a, const float *xcur, const void *b,
     objective_finish(a, scratch);
 }
 
-// ---------------- certificate |r|^2 of the last step ----------------
-// r = grad f(x+) - grad f(y) + (y - x+)/tau
-//   = (y - x+)(1/tau - w) + lambda_tv (D^T p(x+) - D^T p(y)),  y - x+ = (x_k - x+) + beta d.
-__global__ void certificate_kernel(AuxParams a, const float *xplus, const float *xk, const float *xkm1,
-                                   const float *dk, const float *beta_tab, const void *b, const void *w, bool bf16,
-                                   const float *omtv)
-{
-    __shared__ double scratch[32 * 4];
-    __shared__ int flag;
-    const int plane = blockIdx.x / AUX_SEG;
-    const int vol = a.plane_vol[plane];
-    const VolDesc V = a.vols[vol];
-    const int z = plane - V.plane_begin;
-    int r0, r1;
-    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);
-    (void)beta_tab;
-    const float beta = V.beta_last;  // extrapolation weight of the step that produced x+
-    const Field Fy{xk, xkm1, beta, dk};
-    const Field Fx{xplus, nullptr, 0.f};
-    (void)b;
-    KSum ks;
-    for (int t = threadIdx.x; t < (r1 - r0) * V.nx; t += blockDim.x) {
-        const int x = t % V.nx, y = r0 + t / V.nx;
-        const long long i = V.off + ((long long)z * V.ny + y) * V.pitch + x;
-        const float dy = (xk[i] - xplus[i]) + beta * Fy.d(i);
-        const float dv = div_at(V, Fx, omtv, x, y, z) - div_at(V, Fy, omtv, x, y, z);
-        const float r = dy * (1.0f / V.tau - ld_data(w, bf16, i)) + V.lambda_tv * dv;
-        ks.add(r * r);
-    }
-    double s[1] = {ks.value()};
-    block_sum<1>(s, scratch);
-    if (threadIdx.x == 0) a.plane_part[(long long)blockIdx.x * 4] = s[0];
-    if (!last_block(&a.st->ticket_aux, &flag)) return;
-    for (int v = 0; v < a.nvol; v++) {
-        const VolDesc W = a.vols[v];
-        double acc[1] = {0};
-        for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG; q += blockDim.x)
-            acc[0] += __ldcg(a.plane_part + (long long)q * 4);
-        block_sum<1>(acc, scratch);
-        if (threadIdx.x == 0) a.vol_out[(long long)v * 8 + 4] = acc[0];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        a.st->ticket_aux = 0;
-        __threadfence();
-    }
-}
-
 // ---------------- one iteration under alternative readings ----------------
 // The fused step's arithmetic for volumes with SPG_READ_* flags, written
 // plainly: one CTA per row segment of a z-plane; D^T(p) re-evaluates p at the
@@ -1140,6 +1092,139 @@ __global__ void adjoint_apply_kernel(AdjParams a)
     ADJ_WALK_END
 }
 
+// ---------------- certificate, two row-vector passes ----------------
+// Q = P(x+) - P(y) with P = omtv grad h_mu(D .), stored as 3 fields; then
+// r = (y - x+)(1/tau - w) + lambda_tv D^T Q and the sum of r^2 (D^T is
+// linear: D^T P(x+) - D^T P(y) = D^T Q), each P evaluated once per voxel.
+// xbuf = {x_{k+1}, x_k, x_{k-1} or null, d_k or null}.
+#define CERT_WALK_BEGIN                                                                  \
+    const int plane_ = blockIdx.x / AUX_SEG;                                             \
+    const VolDesc V = a.vols[a.plane_vol[plane_]];                                       \
+    const int zz_ = plane_ - V.plane_begin;                                              \
+    int r0, r1;                                                                          \
+    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);                                        \
+    const int lane_ = threadIdx.x & 31, warp_ = threadIdx.x >> 5, nw_ = blockDim.x >> 5; \
+    const int nchunk_ = (V.nx + 127) / 128;                                              \
+    const long long PS = (long long)V.pitch * V.ny;                                      \
+    for (int rc = warp_; rc < (r1 - r0) * nchunk_; rc += nw_) {                          \
+        Lane4 L;                                                                         \
+        L.y = r0 + rc / nchunk_;                                                         \
+        L.z = zz_;                                                                       \
+        L.x0 = (rc % nchunk_) * 128 + 4 * lane_;                                         \
+        L.lane = lane_;                                                                  \
+        L.act = L.x0 < V.nx;                                                             \
+        L.i = V.off + ((long long)L.z * V.ny + L.y) * V.pitch + L.x0;
+
+// D y at the lane's voxels, y = x + beta d with d = aux (increment storage)
+// or x - aux; differences of x and of d are taken separately (Eq. 12).
+__device__ __forceinline__ void grad4_y(const VolDesc &V, const float *x, const float *aux, bool xd, float beta,
+                                        const Lane4 &L, long long PS, float (&g)[3][4])
+{
+    float xc[4], ac[4], xl[4], al[4], xu[4], au[4], xw[4], aw[4];
+    unpack4(ldz4(x + L.i, L.act), xc);
+    unpack4(ldz4(aux + L.i, L.act), ac);
+    left4(x, L, xc, xl);
+    left4(aux, L, ac, al);
+    if (L.y >= 1) {
+        unpack4(ldz4(x + L.i - V.pitch, L.act), xu);
+        unpack4(ldz4(aux + L.i - V.pitch, L.act), au);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; q++) xu[q] = xc[q], au[q] = ac[q];
+    }
+    if (L.z >= 1) {
+        unpack4(ldz4(x + L.i - PS, L.act), xw);
+        unpack4(ldz4(aux + L.i - PS, L.act), aw);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; q++) xw[q] = xc[q], aw[q] = ac[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const float dc = xd ? ac[q] : xc[q] - ac[q];
+        const float dl = xd ? al[q] : xl[q] - al[q];
+        const float du = xd ? au[q] : xu[q] - au[q];
+        const float dw = xd ? aw[q] : xw[q] - aw[q];
+        g[0][q] = (xc[q] - xl[q]) + beta * (dc - dl);
+        g[1][q] = (xc[q] - xu[q]) + beta * (dc - du);
+        g[2][q] = (xc[q] - xw[q]) + beta * (dc - dw);
+    }
+}
+
+__global__ void certificate_q_kernel(AuxParams a, const float *xplus, const float *xk, const float *aux, int xd,
+                                     const float *omtv, float *Q, long long S)
+{
+    CERT_WALK_BEGIN
+    float gp[3][4], gy[3][4], ot[4], q3[3][4];
+    grad4_y(V, xplus, xplus, false, 0.f, L, PS, gp);
+    grad4_y(V, xk, aux, xd != 0, V.beta_last, L, PS, gy);
+    unpack4(ldz4(omtv + L.i, L.act), ot);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const bool valid = L.act && L.x0 + q < V.nx;
+        const float sp = ot[q] * fminf(1.0f / V.mu, rsqrtf(gp[0][q] * gp[0][q] + gp[1][q] * gp[1][q] + gp[2][q] * gp[2][q]));
+        const float sy = ot[q] * fminf(1.0f / V.mu, rsqrtf(gy[0][q] * gy[0][q] + gy[1][q] * gy[1][q] + gy[2][q] * gy[2][q]));
+#pragma unroll
+        for (int c = 0; c < 3; c++) q3[c][q] = valid ? gp[c][q] * sp - gy[c][q] * sy : 0.f;
+    }
+    if (L.act) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) st4(Q + c * S + L.i, q3[c]);
+    }
+    ADJ_WALK_END
+}
+
+__global__ void certificate_r_kernel(AuxParams a, const float *xplus, const float *xk, const float *aux, int xd,
+                                     const void *w, bool bf16, const float *Q, long long S)
+{
+    __shared__ double scratch[32 * 4];
+    __shared__ int flag;
+    KSum ks;
+    CERT_WALK_BEGIN
+    float q0[4], q1[4], q2[4], qx[4], qy[4], qz[4], xp[4], xc[4], ac[4], wv[4];
+    unpack4(ldz4(Q + L.i, L.act), q0);
+    unpack4(ldz4(Q + S + L.i, L.act), q1);
+    unpack4(ldz4(Q + 2 * S + L.i, L.act), q2);
+    right4(V, Q, L, q0, qx);
+    unpack4(ldz4(Q + S + L.i + V.pitch, L.act && L.y + 1 < V.ny), qy);
+    unpack4(ldz4(Q + 2 * S + L.i + PS, L.act && L.z + 1 < V.nz), qz);
+    unpack4(ldz4(xplus + L.i, L.act), xp);
+    unpack4(ldz4(xk + L.i, L.act), xc);
+    unpack4(ldz4(aux + L.i, L.act), ac);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    unpack4(L.act ? ld4_data(w, bf16, L.i) : zero, wv);
+    const float beta = V.beta_last;  // extrapolation weight of the step that produced x+
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        if (!(L.act && L.x0 + q < V.nx)) continue;
+        const float d = xd ? ac[q] : xc[q] - ac[q];
+        const float dy = (xc[q] - xp[q]) + beta * d;
+        const float dv = (q0[q] - qx[q]) + (q1[q] - qy[q]) + (q2[q] - qz[q]);
+        const float r = dy * (1.0f / V.tau - wv[q]) + V.lambda_tv * dv;
+        acc += r * r;
+    }
+    ks.add(acc);
+    ADJ_WALK_END
+    double sm[1] = {ks.value()};
+    block_sum<1>(sm, scratch);
+    if (threadIdx.x == 0) a.plane_part[(long long)blockIdx.x * 4] = sm[0];
+    if (!last_block(&a.st->ticket_aux, &flag)) return;
+    for (int v = 0; v < a.nvol; v++) {
+        const VolDesc W = a.vols[v];
+        double accv[1] = {0};
+        for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG; q += blockDim.x)
+            accv[0] += __ldcg(a.plane_part + (long long)q * 4);
+        block_sum<1>(accv, scratch);
+        if (threadIdx.x == 0) a.vol_out[(long long)v * 8 + 4] = accv[0];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.st->ticket_aux = 0;
+        __threadfence();
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_validate(const AuxParams &a, int vol, int nz, const void *b, const void *w, bool bf16,
@@ -1195,11 +1280,15 @@ cudaError_t launch_objective(const AuxParams &a, const float *const *xbuf, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_certificate(const AuxParams &a, const float *const *xbuf, const float *beta, const void *b,
-                               const void *w, bool bf16, const float *omtv, cudaStream_t s)
+cudaError_t launch_certificate4(const AuxParams &a, const float *const *xbuf, const void *w, bool bf16,
+                                const float *omtv, float *Q, long long stride, cudaStream_t s)
 {
-    certificate_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a, xbuf[0], xbuf[1], xbuf[2], xbuf[3], beta, b, w, bf16,
-                                                         omtv);
+    const bool xd = xbuf[3] != nullptr;
+    const float *aux = xd ? xbuf[3] : xbuf[2];
+    certificate_q_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a, xbuf[0], xbuf[1], aux, xd ? 1 : 0, omtv, Q,
+                                                                     stride);
+    certificate_r_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a, xbuf[0], xbuf[1], aux, xd ? 1 : 0, w, bf16, Q,
+                                                                     stride);
     return cudaGetLastError();
 }
 

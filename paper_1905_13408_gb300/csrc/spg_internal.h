@@ -114,9 +114,11 @@ cudaError_t launch_reweight(const AuxParams &a, const float *const *xbuf, float 
                             const double *maxw, double *rstats, VolDesc *vols_rw, cudaStream_t s);
 cudaError_t launch_objective(const AuxParams &a, const float *const *xbuf, const void *b, const void *w,
                              bool bf16, const float *om1, const float *omtv, cudaStream_t s);
-// xbuf = {x_{k+1}, x_k, x_{k-1} or null, d_k or null}
-cudaError_t launch_certificate(const AuxParams &a, const float *const *xbuf, const float *beta,
-                               const void *b, const void *w, bool bf16, const float *omtv, cudaStream_t s);
+// Strong-convexity certificate of the last step, xbuf = {x_{k+1}, x_k,
+// x_{k-1} or null, d_k or null}: two row-vector passes (Q = P(x+) - P(y) stored in
+// 3 fields of `stride` elements each, then the residual sum).
+cudaError_t launch_certificate4(const AuxParams &a, const float *const *xbuf, const void *w, bool bf16,
+                                const float *omtv, float *Q, long long stride, cudaStream_t s);
 
 // Adjoint of one step (spg_aux.cu): given gnext = dL/dx_{k+1} and the step's
 // inputs, accumulates into gcur (dL/dx_k), gprev (dL/dx_{k-1}), gb, gw and the

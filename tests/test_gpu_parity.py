@@ -264,10 +264,14 @@ def test_objective_and_reweight_match_oracle(shape):
     np.testing.assert_allclose(obj, fo, rtol=1e-6)
 
 
-def test_certificate_matches_oracle():
-    shape = (16, 24, 40)
-    vol = synth.make_volume(shape, blobs=10, radius=5, seed=10)
-    s = make_solver(shape)
+@pytest.mark.parametrize("shape,storage", [((16, 24, 40), "delta"), ((9, 13, 150), "delta"), ((16, 24, 40), "prev"),
+                                           ((5, 6, 131), "prev")])
+def test_certificate_matches_oracle(shape, storage):
+    """Strong-convexity certificate |r|^2 of the last step (two row-vector
+    passes) against the oracle's, for both iterate storages and rows of
+    several 128-voxel chunks."""
+    vol = synth.make_volume(shape, blobs=10, radius=min(shape) / 3 + 1, seed=10)
+    s = make_solver(shape, storage=storage)
     s.set_data(0, vol.b, vol.w)
     s.reweight()
     s.iterate(30)
