@@ -494,10 +494,15 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=3, world=1):
     ctxs[0].set_data(0, b_h, w_h)
     ctxs[0].reweight()
     ctxs[0].iterate(iters)
+    done = torch.cuda.Event()
     for i in range(steps):
         cur, nxt = ctxs[i % 2], ctxs[(i + 1) % 2]
+        done.record(streams[i % 2])    # cur's iterations are queued before this point
         if i + 1 < steps:
             nxt.set_data(0, b_h, w_h)  # copies and validates on nxt's stream
+            # nxt's iterations start when cur's are done: the fused launches of the
+            # two contexts never share the GPU, only copies and small kernels overlap
+            streams[(i + 1) % 2].wait_event(done)
             nxt.reweight()
             nxt.iterate(iters)         # asynchronous on nxt's stream
         cur.objective(0)               # synchronises cur's stream
