@@ -549,3 +549,24 @@ def test_beyond_int32_voxel_count():
         want = oracle.step_sampled(xk, xkm1, beta, float(tau), bb, ww, None, None, p, np.array([idx]))[0]
         got = float(x2[z, y, x])
         assert abs(got - want) <= 2e-6 * max(1.0, abs(want)), (z, y, x, got, want)
+
+
+def test_many_uneven_volumes_in_one_batch():
+    """40 volumes of random shapes (1 to 40 voxels per axis) in one context:
+    every volume matches its own oracle solve (planner, per-volume state and
+    per-volume reductions across many small items)."""
+    rng = np.random.default_rng(123)
+    shapes = [tuple(int(v) for v in rng.integers(1, 41, 3)) for _ in range(40)]
+    vols = [synth.make_volume(sh, blobs=3, radius=max(1.0, min(sh) / 3), seed=300 + j) for j, sh in enumerate(shapes)]
+    hyp = [dict(HYPER, lambda_tv=float(rng.uniform(0.05, 0.2))) for _ in shapes]
+    s = spg.SPG([dict(shape=sh, **h) for sh, h in zip(shapes, hyp)])
+    for j, v in enumerate(vols):
+        s.set_data(j, v.b, v.w)
+    s.solve(2, 15)
+    xs = [s.get_x(j).cpu().numpy() for j in range(len(shapes))]
+    hists = [s.history(j) for j in range(len(shapes))]
+    s.close()
+    for sh, h, v, x, hist in zip(shapes, hyp, vols, xs, hists):
+        ref = oracle.solve(v.b, v.w, oparams(sh, h), 2, 15)
+        assert rel_l2(x, ref.x) <= 2e-6, sh
+        np.testing.assert_allclose(hist[:, 4], ref.hist.reshape(-1, 4)[:, 3], rtol=1e-6, atol=1e-9)
