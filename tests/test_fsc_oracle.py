@@ -51,3 +51,13 @@ def test_independent_noise_is_uncorrelated():
     c, cnt = ofsc.fsc(a, b)
     z = np.abs(c[2:]) * np.sqrt(cnt[2:] / 2)
     assert np.all(z < 5)
+
+
+def test_resolution_shell_is_the_first_crossing_after_the_origin():
+    """The 0.143 criterion (Sec. 2.3): the first shell k >= 1 whose FSC is
+    below the threshold; shell 0 (the mean) never decides it, and a curve
+    that stays above it reports one past the last shell."""
+    assert ofsc.resolution_shell(np.array([1.0, 0.95, 0.6, 0.2, 0.1, 0.05])) == 4
+    assert ofsc.resolution_shell(np.array([0.0, 0.9, 0.3, 0.1])) == 3
+    assert ofsc.resolution_shell(np.array([1.0, 0.9, 0.8]), threshold=0.5) == 3
+    assert ofsc.resolution_shell(np.array([1.0, 0.9, 0.8]), threshold=0.85) == 2

@@ -107,3 +107,23 @@ def test_noiseless_slices_recover_the_transform():
         assert corr > min_corr, kernel
         if max_rel is not None:
             assert np.abs(g - t).max() / np.abs(F).max() < max_rel
+
+
+def test_fourier_term_is_fitted_by_the_phantom():
+    """Eq. 31 from gridded images: with y, N' from to_fourier_term, the phantom
+    itself (a volume with its origin at array index 0, as the unitary DFT A
+    takes it) nearly zeroes the residual y - sqrt(N') A x wherever slices cross
+    (|k| <= 8), with the images' own CTF, while the zero volume leaves all of
+    y. A dropped (-1)^k centring sign, a missing voxel-count factor in N' or a
+    missing square root each leave a residual of the order of y itself."""
+    n = 32
+    pd = synth.make_projection_data(n, blobs=6, radius=3.0, n_images=150, seed=74, noise_sd=0.0)
+    num, N = gridding.grid(pd.X, pd.ctf, pd.rot, n, "trilinear")
+    y, Nq = gridding.to_fourier_term(num, N)
+    f = np.fft.fftfreq(n) * n
+    r = np.sqrt(f[:, None, None] ** 2 + f[None, :, None] ** 2 + f[None, None, :] ** 2)
+    sel = (r <= 8) & (N > 0)
+    Ax = np.fft.fftn(pd.phantom.astype(np.float64), norm="ortho")
+    res = y - np.sqrt(Nq) * Ax
+    assert np.linalg.norm(res[sel]) < 0.05 * np.linalg.norm(y[sel])
+    assert np.all(y[N == 0] == 0)
