@@ -359,6 +359,7 @@ def run_spg(args):
 
     readings = dict(difference=args.difference, boundary=args.boundary, tv_weight=args.tv_weight)
     adopted = readings == dict(difference="backward", boundary="neumann", tv_weight="inside")
+    fused = adopted or readings == dict(difference="forward", boundary="neumann", tv_weight="inside")
     s = spg.SPG(dict(shape=vol.b.shape, **hyper), data_dtype=args.dtype, tile=args.tile, zchunk=args.zchunk,
                 stream=stream.cuda_stream, max_iters=max(100000, args.steps + args.warmup + 16),
                 hist_every=args.hist_every, storage=args.storage, **readings)
@@ -398,6 +399,7 @@ def run_spg(args):
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": bpv * nvox,
             "kernel": "spg_step_kernel (fused iteration + objective)" if adopted
+            else "spg_step_kernel on the axis-reversed volume (forward differences)" if fused
             else "generic_step_kernel (alternative readings %s)" % readings}
 
     e2e = None

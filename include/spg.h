@@ -106,8 +106,8 @@ typedef struct {
     int restart;              /* 0: fixed FISTA schedule (default); 1: gradient restart of the
                                  extrapolation (per volume, whenever <y_k - x_{k+1}, x_{k+1} - x_k> > 0,
                                  O'Donoghue and Candes 2015); decided on the device every iteration */
-    int readings;             /* 0: the adopted readings of the paper (the fused path); otherwise an
-                                 OR of SPG_READ_* flags, run by a plain one-kernel step (below) */
+    int readings;             /* 0: the adopted readings of the paper; otherwise an OR of
+                                 SPG_READ_* flags (below) */
 } spg_options;
 
 /* Alternative readings of the paper, for spg_options.readings. The adopted
@@ -121,8 +121,22 @@ typedef struct {
  *                      as Eq. 20 prints it (not the gradient of any objective
  *                      unless omtv is constant).
  * They apply to the re-weighting (|D x|), the objective (TV term) and the
- * iteration. A context with readings != 0 iterates with one plain kernel per
- * step instead of the fused one (it re-evaluates the differences at every
+ * iteration.
+ *
+ * SPG_READ_FORWARD alone runs the fused kernels, on volumes held with every
+ * axis reversed: with R that reversal, forward differences are -R D_b R, and
+ * the Huber term, the weights, the data and l1 terms commute with R, so the
+ * forward-difference solve of (b, w) is R applied to the backward-difference
+ * solve of (R b, R w). Every volume is reversed as it enters the context
+ * (spg_set_data, spg_set_x, spg_set_anchor, spg_set_state, the gradient given
+ * to spg_backward) and as it leaves (spg_get_x, spg_get_state, spg_unrolled's
+ * x_K, spg_backward's gradients), so callers see their own orientation;
+ * reading a volume out reverses the context's copy twice on its stream. Every
+ * entry point of the real-space data term is available, at the adopted
+ * path's speed; the Fourier-domain data term is not.
+ *
+ * Any other non-zero combination iterates with one plain kernel per step
+ * instead of the fused one (it re-evaluates the differences at every
  * neighbour from global memory: about a ninth of the fused step's speed, a
  * path for comparing readings, not for production) and needs float32 data
  * with the real-space data term; restart, the certificate, the adjoint and

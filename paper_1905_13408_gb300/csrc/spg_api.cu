@@ -57,6 +57,13 @@ struct spg_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int num_sms = 0;
+    // Forward differences alone run the adopted kernels on a layout with every
+    // axis reversed: with R the reversal, D_f x = -R D_b R x, and h_mu, the
+    // weights, the data term and the l1 term commute with R, so the solve of
+    // (b, w) under forward differences is R applied to the backward-difference
+    // solve of (R b, R w). Volumes are reversed on the way in and out.
+    bool reversed = false;
+    int kread = 0;  // readings the kernels implement (0: the fused path)
 
     std::vector<VolDesc> vols_h;
     std::vector<int> plane_vol_h;
@@ -456,7 +463,7 @@ AuxParams aux_params(const spg_ctx *c)
     a.st = c->st_d;
     a.plane_part = c->plane_part_d;
     a.vol_out = c->vol_out_d;
-    a.readings = c->opt.readings;
+    a.readings = c->kread;
     return a;
 }
 
@@ -503,12 +510,17 @@ spg_status copy_volume_in(spg_ctx *ctx, void *dst_base, size_t es, const VolDesc
         CK(cudaMemcpy2DAsync(dst, (size_t)d.pitch * es, src, (size_t)d.nx * es, (size_t)d.nx * es,
                              (size_t)d.ny * d.nz, cudaMemcpyDefault, ctx->stream),
            "copy volume in");
+    if (ctx->reversed) CK(launch_reverse_axes(dst, es, d.nx, d.ny, d.nz, d.pitch, ctx->stream), "reverse axes");
     return SPG_OK;
 }
 
+// With reversed axes the context's volume is reversed in place, copied and
+// reversed back (stream-ordered; the destination may be host memory).
 spg_status copy_volume_out(spg_ctx *ctx, void *dst, const void *src_base, size_t es, const VolDesc &d)
 {
     const char *src = static_cast<const char *>(src_base) + (size_t)d.off * es;
+    char *src_rw = const_cast<char *>(src);
+    if (ctx->reversed) CK(launch_reverse_axes(src_rw, es, d.nx, d.ny, d.nz, d.pitch, ctx->stream), "reverse axes");
     if (d.pitch == d.nx)
         CK(cudaMemcpyAsync(dst, src, (size_t)d.nx * d.ny * d.nz * es, cudaMemcpyDefault, ctx->stream),
            "copy volume out");
@@ -516,6 +528,7 @@ spg_status copy_volume_out(spg_ctx *ctx, void *dst, const void *src_base, size_t
         CK(cudaMemcpy2DAsync(dst, (size_t)d.nx * es, src, (size_t)d.pitch * es, (size_t)d.nx * es,
                              (size_t)d.ny * d.nz, cudaMemcpyDefault, ctx->stream),
            "copy volume out");
+    if (ctx->reversed) CK(launch_reverse_axes(src_rw, es, d.nx, d.ny, d.nz, d.pitch, ctx->stream), "reverse axes");
     return SPG_OK;
 }
 
@@ -540,7 +553,7 @@ cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
             return cudaErrorUnknown;
         ctx->launches += 1;
     }
-    if (ctx->opt.readings) {
+    if (ctx->kread) {
         GenericParams g;
         g.vols = ctx->vols_d;
         g.plane_vol = ctx->plane_vol_d;
@@ -782,7 +795,9 @@ spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg
         delete ctx;
         return fail(nullptr, SPG_EINVAL, "spg_create: bad readings flags");
     }
-    if (ctx->opt.readings && (ctx->opt.data_dtype != SPG_F32 || ctx->opt.restart)) {
+    ctx->reversed = ctx->opt.readings == SPG_READ_FORWARD;
+    ctx->kread = ctx->reversed ? 0 : ctx->opt.readings;
+    if (ctx->kread && (ctx->opt.data_dtype != SPG_F32 || ctx->opt.restart)) {
         delete ctx;
         return fail(nullptr, SPG_EINVAL, "spg_create: alternative readings need float32 data and no restart");
     }
@@ -820,7 +835,7 @@ spg_status spg_create_batch(int nvol, const spg_volume_params *params, const spg
         d.eps_tv = p.eps_tv;
         d.tau = 0.f;
         d.plane_begin = plane;
-        d.readings = ctx->opt.readings;
+        d.readings = ctx->kread;
         ctx->vols_h.push_back(d);
         for (int z = 0; z < p.nz; z++) ctx->plane_vol_h.push_back(j);
         off += round_up((long long)d.pitch * d.ny * d.nz, 64);
@@ -1270,7 +1285,7 @@ spg_status spg_certificate(spg_ctx *ctx, int vol, double *out)
     SPG_TRACE();
     if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
     if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_certificate: bad arguments");
-    if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_certificate: not available with alternative readings");
+    if (ctx->kread) return fail(ctx, SPG_EINVAL, "spg_certificate: not available with these readings");
     if (!ctx->reweighted || ctx->k_round < 1)
         return fail(ctx, SPG_ENOTREADY, "spg_certificate: needs one iteration in the current round");
     if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_certificate: not available with the Fourier-domain data term");
@@ -1423,7 +1438,7 @@ spg_status spg_unrolled(spg_ctx *ctx, int K, float *xK)
     if (!ctx || !xK || K < 0) return fail(ctx, SPG_EINVAL, "spg_unrolled: bad arguments");
     if (ctx->nvol != 1) return fail(ctx, SPG_EINVAL, "spg_unrolled: single-volume contexts only");
     if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_unrolled: not available with the Fourier-domain data term");
-    if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_unrolled: not available with alternative readings");
+    if (ctx->kread) return fail(ctx, SPG_EINVAL, "spg_unrolled: not available with these readings");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_unrolled: call spg_reweight first");
     if (K > ctx->max_iters) return fail(ctx, SPG_EINVAL, "spg_unrolled: K above max_iters_per_round");
     const VolDesc &d = ctx->vols_h[0];
@@ -1455,7 +1470,7 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
     if (!ctx || !gx || !gb || !gw || !g_scalars || K < 1) return fail(ctx, SPG_EINVAL, "spg_backward: bad arguments");
     if (ctx->nvol != 1) return fail(ctx, SPG_EINVAL, "spg_backward: single-volume contexts only");
     if (ctx->fourier) return fail(ctx, SPG_EINVAL, "spg_backward: not available with the Fourier-domain data term");
-    if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_backward: not available with alternative readings");
+    if (ctx->kread) return fail(ctx, SPG_EINVAL, "spg_backward: not available with these readings");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_backward: call spg_reweight first");
     if (K > ctx->max_iters) return fail(ctx, SPG_EINVAL, "spg_backward: K above max_iters_per_round");
     const int C = ckpt_every > 0 ? ckpt_every : 10;
@@ -1646,7 +1661,7 @@ spg_status spg_autotune(spg_ctx *ctx, int trial_iters, int info[6])
 {
     SPG_TRACE();
     if (!ctx || trial_iters < 1) return fail(ctx, SPG_EINVAL, "spg_autotune: bad arguments");
-    if (ctx->opt.readings) return fail(ctx, SPG_EINVAL, "spg_autotune: not available with alternative readings");
+    if (ctx->kread) return fail(ctx, SPG_EINVAL, "spg_autotune: not available with these readings");
     if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_autotune: call spg_reweight first");
     ctx->y_fresh = false;
     const std::string key = tune_key(ctx);

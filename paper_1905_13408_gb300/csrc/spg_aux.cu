@@ -10,6 +10,8 @@
 // deterministic. No kernel here waits on another CTA.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "spg_internal.h"
 
 namespace spg {
@@ -1245,6 +1247,46 @@ cudaError_t launch_scales(const AuxParams &a, int vol, int nz, const void *b, co
                           cudaStream_t s)
 {
     scales_kernel<<<nz * AUX_SEG, AUX_THREADS, 0, s>>>(a, vol, b, w, bf16);
+    return cudaGetLastError();
+}
+
+// In-place reversal of every axis of one pitched volume: element (z, y, x)
+// trades places with (nz-1-z, ny-1-y, nx-1-x). Element i of the unpadded
+// order pairs with element nvox-1-i, so the first half of the order visits
+// every pair once (the middle element of an odd volume stays); padding is
+// not touched.
+template <typename T>
+__global__ void __launch_bounds__(256) reverse_axes_kernel(T *v, int nx, int ny, int pitch, long long nvox)
+{
+    const long long half = nvox / 2;
+    const long long nxy = (long long)nx * ny;
+    auto at = [&](long long i) {
+        const long long z = i / nxy;
+        const long long r = i - z * nxy;
+        const long long y = r / nx;
+        return (z * ny + y) * pitch + (r - y * nx);
+    };
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < half;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long a = at(i), b = at(nvox - 1 - i);
+        const T t = v[a];
+        v[a] = v[b];
+        v[b] = t;
+    }
+}
+
+cudaError_t launch_reverse_axes(void *v, size_t es, int nx, int ny, int nz, int pitch, cudaStream_t s)
+{
+    const long long nvox = (long long)nx * ny * nz;
+    const long long half = nvox / 2;
+    if (half == 0) return cudaSuccess;
+    const int grid = (int)std::min<long long>((half + 255) / 256, 4096);
+    if (es == 4)
+        reverse_axes_kernel<uint32_t><<<grid, 256, 0, s>>>(static_cast<uint32_t *>(v), nx, ny, pitch, nvox);
+    else if (es == 2)
+        reverse_axes_kernel<uint16_t><<<grid, 256, 0, s>>>(static_cast<uint16_t *>(v), nx, ny, pitch, nvox);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -110,6 +110,7 @@ cudaError_t launch_validate(const AuxParams &a, int vol, int nz, const void *b, 
                             double *maxw_out, cudaStream_t s);
 cudaError_t launch_convert_to_bf16(const float *src, uint16_t *dst, long long n, cudaStream_t s);
 cudaError_t launch_convert_to_f32(const uint16_t *src, float *dst, long long n, cudaStream_t s);
+cudaError_t launch_reverse_axes(void *v, size_t es, int nx, int ny, int nz, int pitch, cudaStream_t s);
 cudaError_t launch_reweight(const AuxParams &a, const float *const *xbuf, float *om1, float *omtv,
                             const double *maxw, double *rstats, VolDesc *vols_rw, cudaStream_t s);
 cudaError_t launch_objective(const AuxParams &a, const float *const *xbuf, const void *b, const void *w,
