@@ -623,9 +623,10 @@ def run_adjoint(args):
 
 def run_fourier(args):
     """Fourier-domain data term of Eq. 31 at 512^3: per iteration the
-    real-to-complex transform of y_k, the residual spectrum, the inverse
-    transform and the fused step, which also writes y_{k+1} (cuFFT for the
-    transforms)."""
+    per-plane 2-D real-to-complex transforms of y_k (cuFFT), one pass along
+    z that transforms, forms the residual spectrum and transforms back, the
+    per-plane complex-to-real transforms (cuFFT) and the fused step, which
+    also writes y_{k+1}."""
     import numpy as np
     import torch
 

@@ -23,7 +23,7 @@ LIB = os.path.join(HERE, "libspg.so")
 # checker.
 LIB_CHECK = os.path.join(HERE, "libspg_check.so")
 SOURCES = ["spg_step_f32.cu", "spg_step_bf16.cu", "spg_step.cu", "spg_aux.cu", "spg_api.cu", "spg_noalloc.cu",
-           "spg_fsc.cu", "spg_cufft.cu", "spg_fourier.cu", "spg_grid.cu"]
+           "spg_fsc.cu", "spg_cufft.cu", "spg_fourier.cu", "spg_grid.cu", "spg_zfft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

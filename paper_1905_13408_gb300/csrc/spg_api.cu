@@ -113,8 +113,10 @@ struct spg_ctx {
     float *certQ = nullptr;  // 3-vector field of the certificate passes (allocated on first use)
     float *Nmax = nullptr;
     double *fpart = nullptr; // reduction partials of the Fourier data value
-    cufftHandle pr2c = 0, pc2r = 0;
+    cufftHandle pr2c = 0, pc2r = 0;  // per-plane 2-D transforms (batch nz)
     bool plans = false;
+    ZPlan zplan{};                   // the transform along z (own kernels)
+    float2 *ztw = nullptr;           // its twiddle table
     long long nhalf = 0;
 
     cudaGraphExec_t gexec = nullptr;
@@ -168,7 +170,7 @@ void free_all(spg_ctx *c)
         spg::cufft_api().destroy(c->pr2c);
         spg::cufft_api().destroy(c->pc2r);
     }
-    void *fs[] = {c->Ybuf, c->Fh, c->Yh, c->Nh, c->Ch, c->Nmax, c->fpart, c->Anc, c->Nst, c->Cst, c->certQ};
+    void *fs[] = {c->Ybuf, c->Fh, c->Yh, c->Nh, c->Ch, c->Nmax, c->fpart, c->Anc, c->Nst, c->Cst, c->certQ, c->ztw};
     for (void *p : fs)
         if (p) cudaFree(p);
     void *ps[] = {c->vols_d, c->items_d, c->sched_d, c->tmaps_d, c->plane_vol_d, c->X[0], c->X[1], c->X[2], c->X[3], c->B, c->W,
@@ -545,8 +547,8 @@ cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
         if (cf.exec_r2c(ctx->pr2c, ctx->Ybuf, reinterpret_cast<cufftComplex *>(ctx->Fh)) != CUFFT_SUCCESS)
             return cudaErrorUnknown;
         const bool anc = ctx->gamma_f > 0.f;
-        e = launch_spec_scale(ctx->Fh, anc ? ctx->Nst : ctx->Nh, anc ? ctx->Cst : ctx->Ch, ctx->nhalf, (float)(1.0 / V),
-                              ctx->stream);
+        e = launch_zfft_residual(ctx->Fh, anc ? ctx->Nst : ctx->Nh, anc ? ctx->Cst : ctx->Ch, (float)(1.0 / V),
+                                 ctx->zplan, ctx->ztw, ctx->stream);
         if (e != cudaSuccess) return e;
         if (cf.exec_c2r(ctx->pc2r, reinterpret_cast<cufftComplex *>(ctx->Fh), static_cast<float *>(ctx->B)) !=
             CUFFT_SUCCESS)
@@ -997,13 +999,22 @@ spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const
         CK(cudaMemsetAsync(ctx->Ybuf, 0, (size_t)ctx->total * sizeof(float), ctx->stream), "memset");
     }
     if (!ctx->plans) {
-        int n[3] = {d.nz, d.ny, d.nx};
-        int real_embed[3] = {d.nz, d.ny, d.pitch};
-        int cplx_embed[3] = {d.nz, d.ny, nxh};
-        const int rdist = d.nz * d.ny * d.pitch, cdist = (int)ctx->nhalf;
-        if (cf.plan_many(&ctx->pr2c, 3, n, real_embed, 1, rdist, cplx_embed, 1, cdist, CUFFT_R2C, 1) != CUFFT_SUCCESS)
+        // 3-D transforms = a batch of per-plane 2-D transforms (x, y) and the own transform along z
+        std::vector<float2> tw;
+        if (!zfft_plan(d.nz, (long long)d.ny * nxh, &ctx->zplan, &tw))
+            return fail(ctx, SPG_EINVAL, "spg_set_data_fourier: nz out of range for the transform along z");
+        CK(dalloc(&ctx->ztw, tw.size() * sizeof(float2)), "alloc");
+        CK(cudaMemcpyAsync(ctx->ztw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream),
+           "twiddles");
+        CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+        int n[2] = {d.ny, d.nx};
+        int real_embed[2] = {d.ny, d.pitch};
+        int cplx_embed[2] = {d.ny, nxh};
+        const int rdist = d.ny * d.pitch, cdist = d.ny * nxh;
+        if (cf.plan_many(&ctx->pr2c, 2, n, real_embed, 1, rdist, cplx_embed, 1, cdist, CUFFT_R2C, d.nz) != CUFFT_SUCCESS)
             return fail(ctx, SPG_ECUDA, "spg_set_data_fourier: cufft plan");
-        if (cf.plan_many(&ctx->pc2r, 3, n, cplx_embed, 1, cdist, real_embed, 1, rdist, CUFFT_C2R, 1) != CUFFT_SUCCESS) {
+        if (cf.plan_many(&ctx->pc2r, 2, n, cplx_embed, 1, cdist, real_embed, 1, rdist, CUFFT_C2R, d.nz) !=
+            CUFFT_SUCCESS) {
             cf.destroy(ctx->pr2c);
             return fail(ctx, SPG_ECUDA, "spg_set_data_fourier: cufft plan");
         }
@@ -1061,6 +1072,8 @@ spg_status spg_set_anchor(spg_ctx *ctx, int vol, float gamma, const float *x_anc
         const double V = (double)d.nx * d.ny * d.nz;
         if (spg::cufft_api().exec_r2c(ctx->pr2c, ctx->Anc, reinterpret_cast<cufftComplex *>(ctx->Fh)) != CUFFT_SUCCESS)
             return fail(ctx, SPG_ECUDA, "spg_set_anchor: transform");
+        CK(launch_zfft(ctx->Fh, ctx->zplan, ctx->ztw, ctx->stream), "transform along z");
+        ctx->launches += 1;
         CK(launch_spec_anchor(ctx->Nh, ctx->Ch, ctx->Fh, ctx->nhalf, 2.f * gamma, (float)(1.0 / V), ctx->Nst, ctx->Cst,
                               ctx->stream),
            "anchor spectrum");
@@ -1218,6 +1231,8 @@ spg_status spg_objective(spg_ctx *ctx, int vol, double out[4])
         if (spg::cufft_api().exec_r2c(ctx->pr2c, ctx->Ybuf, reinterpret_cast<cufftComplex *>(ctx->Fh)) !=
             CUFFT_SUCCESS)
             return fail(ctx, SPG_ECUDA, "spg_objective: transform");
+        CK(launch_zfft(ctx->Fh, ctx->zplan, ctx->ztw, ctx->stream), "transform along z");
+        ctx->launches += 1;
         CK(launch_spec_data_value(ctx->Fh, ctx->Yh, ctx->Nh, d.nz, d.ny, d.nx, (float)(1.0 / std::sqrt(V)),
                                   ctx->fpart, ctx->fpart + 1024, ctx->stream),
            "data value");

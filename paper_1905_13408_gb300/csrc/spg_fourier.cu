@@ -1,14 +1,16 @@
 // Kernels of the Fourier-domain data term (Sec. 2.5, Eq. 31):
 //   1/2 |y - D A x|^2, A the unitary DFT, D = diag sqrt(N),
 // whose gradient A^H (N A x - D y) is formed each iteration at the
-// extrapolated point y_k by a real-to-complex transform, a spectrum pass that
-// scales by N and subtracts the data spectrum, and a complex-to-real
-// transform (cuFFT), then consumed by the fused step. Subtracting before the
-// inverse transform keeps FP32 rounding relative to the residual rather than
-// to A^H N A y_k, which for the strongly uneven N of gridded data (many orders
-// of magnitude between low and high frequencies) is the difference between
-// errors of 1e-7 and 1e-5 after a hundred iterations.
-// Spectra use the real-to-complex half layout [nz][ny][nx/2+1].
+// extrapolated point y_k by per-plane real-to-complex transforms (cuFFT), one
+// pass along z that transforms, scales by N, subtracts the data spectrum and
+// transforms back (spg_zfft.cu), and per-plane complex-to-real transforms,
+// then consumed by the fused step. Subtracting before the inverse transform
+// keeps FP32 rounding relative to the residual rather than to A^H N A y_k,
+// which for the strongly uneven N of gridded data (many orders of magnitude
+// between low and high frequencies) is the difference between errors of 1e-7
+// and 1e-5 after a hundred iterations.
+// Spectra use the real-to-complex half layout [nz][ny][nx/2+1]; this file
+// holds the data preparation, value and scale kernels.
 #include "spg_internal.h"
 
 namespace spg {
@@ -24,20 +26,6 @@ __global__ void form_y_kernel(const DevState *st, const VolDesc *vols, const flo
     const float *d = cur == 0 ? d0 : d1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = fmaf(b, d[i], x[i]);
-}
-
-// F <- N F scale - C: the unnormalised spectrum of the residual (scale = 1/V,
-// C = sqrt(N) y / sqrt(V)), so the inverse transform gives A^H (N A y_k - D y).
-__global__ void spec_scale_kernel(float2 *F, const float *N, const float2 *C, long long n, float scale)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float m = N[i] * scale;
-        const float2 c = C[i];
-        float2 f = F[i];
-        f.x = fmaf(f.x, m, -c.x);
-        f.y = fmaf(f.y, m, -c.y);
-        F[i] = f;
-    }
 }
 
 __global__ void spec_prep_kernel(float2 *F, const float2 *Y, const float *N, long long n, float scale)
@@ -204,12 +192,6 @@ cudaError_t launch_form_y(const DevState *st, const VolDesc *vols, const float *
                           long long n, cudaStream_t s)
 {
     form_y_kernel<<<grid_for(n), 256, 0, s>>>(st, vols, beta, xbuf[0], xbuf[1], xbuf[2], xbuf[3], y, n);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_spec_scale(float2 *F, const float *N, const float2 *C, long long n, float scale, cudaStream_t s)
-{
-    spec_scale_kernel<<<grid_for(n), 256, 0, s>>>(F, N, C, n, scale);
     return cudaGetLastError();
 }
 

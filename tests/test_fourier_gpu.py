@@ -29,7 +29,11 @@ def gpu_fourier_solve(fv, hyper, rounds, iters, **kw):
     return x, obj, hist
 
 
-@pytest.mark.parametrize("shape", [(24, 28, 30), (32, 32, 32), (17, 40, 25)])
+# nz covers the z transform's radices (8 and 3, 8 and 4, a prime 17, 4 and 7,
+# the trivial nz = 1) and its narrower tiles for long lines (1024: 4 columns
+# per CTA, 2048: 2, 4096: 1)
+@pytest.mark.parametrize("shape", [(24, 28, 30), (32, 32, 32), (17, 40, 25), (28, 12, 16), (1, 24, 30),
+                                   (1024, 6, 8), (2048, 4, 4), (4096, 2, 4)])
 def test_fourier_solve_matches_oracle(shape):
     fv = synth.make_fourier_volume(shape, blobs=12, radius=6, seed=sum(shape))
     hyper = dict(HYPER, mu=0.02)
