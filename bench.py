@@ -713,11 +713,21 @@ def run_grid(args):
     kept = int((r2 <= (n / 2 - 2) ** 2).sum())
     deposits = m * kept * 27  # full-spectrum kernel deposits the scatter accounts for
     sec = ms / 1e3 / args.steps
+    # algorithmic HBM bytes of one batch: every image coefficient and CTF value
+    # read once (8 + 4 B), every accumulator point (Re, Im, N, pad: 4 x 8 B) of
+    # the half spectrum written once
+    hbm_bytes = m * n * n * 12 + n * n * (n // 2 + 1) * 32
+    peaks, kind = measured_peaks()
     print(json.dumps({"metric": "image-pose pairs gridded/s, 256x256 images into 256^3 (Gaussian kernel, h = 2)",
                       "value": m / sec, "unit": "images/s", "steps": args.steps, "ms_per_step": ms / args.steps,
                       "dtype": "f64 accumulation", "data": "synthetic",
                       "config": {"workload": "grid256", "n": n, "images": m, "coefficients_per_image": kept},
                       "kernel_deposits_per_s": deposits / sec,
+                      "roofline": {"bound": "hbm", "achieved": hbm_bytes / sec / 1e9, "peak": peaks["hbm_gbs"],
+                                   "unit": "GB/s", "frac": hbm_bytes / sec / 1e9 / peaks["hbm_gbs"], "peak_kind": kind,
+                                   "algorithmic_bytes_per_launch": hbm_bytes,
+                                   "note": "far from HBM: the scatter is limited by shared-memory atomics "
+                                           "(27 deposits of 3 sums per coefficient)"},
                       "note": "reset + scatter timed; finish (half-spectrum write) excluded"}))
     return 0
 

@@ -47,6 +47,22 @@ def test_fourier_solve_matches_oracle(shape):
     np.testing.assert_allclose(hist[:, 2:4], np.concatenate([hr[0, :, 1:3], hr[1, :, 1:3]]), rtol=1e-5)
 
 
+@pytest.mark.parametrize("shape", [(128, 24, 30), (256, 12, 20), (512, 40, 120), (512, 6, 4)])
+def test_fourier_register_resident_z_transform(shape):
+    """Lengths 128 .. 512 along z (16 columns per tile in the
+    register-resident kernel): one tile, several rows of tiles (512 x 40 x
+    120: 153 tiles) and a ragged last tile (18 columns); one round against
+    the oracle."""
+    fv = synth.make_fourier_volume(shape, blobs=12, radius=6, seed=sum(shape))
+    hyper = dict(HYPER, mu=0.02)
+    x, obj, hist = gpu_fourier_solve(fv, hyper, 1, 15)
+    p = oracle.Params(shape, **hyper)
+    xr, hr, rr = fourier.solve(fv.y, fv.N, p, 1, 15)
+    err = rel_l2(x, xr)
+    print(f"fourier z length {shape[0]} {shape}: rel-L2 {err:.3e}")
+    assert err <= 1e-5
+
+
 def test_fourier_objective_value():
     shape = (20, 22, 24)
     fv = synth.make_fourier_volume(shape, blobs=8, radius=5, seed=61)
