@@ -81,20 +81,37 @@ __global__ void spec_max_kernel(const float *N, long long n, unsigned int *out)
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
-// Half-spectrum sum of 1/2 |Y - sqrt(N) F scale|^2, coefficients 0 < h < nx/2 counted twice.
+// Half-spectrum sum of 1/2 |Y - sqrt(N) F scale|^2, coefficients 0 < h < nx/2
+// counted twice. A block walks whole rows (no index division per element);
+// sqrt(N) is the float estimate refined by one Newton step in double,
+// s <- s + r (N - s^2) / 2 with r = 1/sqrt(N) in float, which leaves a
+// relative error of the order of the float estimate's squared (the data
+// term's residual cancels Y against sqrt(N) F scale, so sqrt(N) needs more
+// than float precision, and a double square root per coefficient would
+// dominate the pass on this GPU's narrow FP64 pipe).
 __global__ void spec_value_kernel(const float2 *F, const float2 *Y, const float *N, int nz, int ny, int nx,
                                   float scale, double *partials)
 {
     __shared__ double red[32];
     const int nxh = nx / 2 + 1;
-    const long long n = (long long)nz * ny * nxh;
+    const long long rows = (long long)nz * ny;
     double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int h = (int)(i % nxh);
-        const double wgt = (h == 0 || (nx % 2 == 0 && h == nx / 2)) ? 1.0 : 2.0;
-        const double m = sqrt((double)N[i]) * scale;
-        const double rx = (double)Y[i].x - m * F[i].x, ry = (double)Y[i].y - m * F[i].y;
-        acc += wgt * 0.5 * (rx * rx + ry * ry);
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const long long o = r * nxh;
+        for (int h = threadIdx.x; h < nxh; h += blockDim.x) {
+            const float nf = N[o + h];
+            double sq = 0.0;
+            if (nf > 0.f) {
+                const float rs = rsqrtf(nf);
+                const double nd = nf, s0 = (double)nf * rs;
+                sq = s0 + 0.5 * (double)rs * (nd - s0 * s0);
+            }
+            const double m = sq * scale;
+            const float2 f = F[o + h], y = Y[o + h];
+            const double rx = (double)y.x - m * f.x, ry = (double)y.y - m * f.y;
+            const double wgt = (h == 0 || (nx % 2 == 0 && h == nx / 2)) ? 0.5 : 1.0;
+            acc += wgt * (rx * rx + ry * ry);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;

@@ -63,6 +63,16 @@ def test_fourier_register_resident_z_transform(shape):
     assert err <= 1e-5
 
 
+def test_fourier_rejects_z_lines_beyond_4096():
+    shape = (4100, 2, 2)
+    fv = synth.make_fourier_volume(shape, blobs=2, radius=1, seed=60)
+    s = spg.SPG(dict(shape=shape, **HYPER))
+    with pytest.raises(spg.SPGError):
+        s.set_data_fourier(0, synth.half_spectrum(fv.y).astype(np.complex64),
+                           synth.half_spectrum(fv.N).astype(np.float32))
+    s.close()
+
+
 def test_fourier_objective_value():
     shape = (20, 22, 24)
     fv = synth.make_fourier_volume(shape, blobs=8, radius=5, seed=61)
@@ -78,7 +88,7 @@ def test_fourier_objective_value():
     p = oracle.Params(shape, **hyper)
     om1, omtv, _ = oracle.reweight(x0, p)
     want = fourier.objective(x0.astype(np.float64), fv.y, fv.N, om1, omtv, p)
-    np.testing.assert_allclose(obj, want, rtol=1e-5)
+    np.testing.assert_allclose(obj, want, rtol=1e-6)
 
 
 def test_constant_weight_matches_real_space_solve():
