@@ -144,28 +144,59 @@ def test_vol512_first_iterations_match_oracle():
     np.testing.assert_allclose(st[0, 4:], ref.rstats[0, 4:], rtol=1e-6)
 
 
-def test_vol512_objective_at_the_gap():
-    """The benchmark's 512^3 round-1 subproblem run for the 159 iterations it
-    needs to reach a relative gap of 1e-3: the final iterate and objective
-    against the FP64 oracle run for the same 159 iterations (about 2.1e10
-    voxel-iterations of oracle work)."""
-    vol, hyper, _, _ = synth.workload("vol512")
-    shape = vol.b.shape
-    K = 159
-    s = make_solver(shape, hyper)
+def solve_512(vol, hyper, K, **kw):
+    s = make_solver(vol.b.shape, hyper, **kw)
     s.set_data(0, torch.from_numpy(vol.b).cuda(), torch.from_numpy(vol.w).cuda())
     s.reweight()
     s.iterate(K)
     x = s.get_x(0).cpu().numpy()
     obj = s.objective(0)
     s.close()
+    return x, obj
+
+
+def test_vol512_objective_at_the_gap():
+    """The benchmark's 512^3 round-1 subproblem run for the 159 iterations it
+    needs to reach a relative gap of 1e-3: the final iterate and objective
+    against the FP64 oracle run for the same 159 iterations (about 2.1e10
+    voxel-iterations of oracle work). The BF16-storage form against the same
+    oracle (FP32 inputs) shows the quantisation of b and w at that point."""
+    vol, hyper, _, _ = synth.workload("vol512")
+    shape = vol.b.shape
+    K = 159
+    x, obj = solve_512(vol, hyper, K)
+    x16, _ = solve_512(vol, hyper, K, data_dtype="bf16")
     p = oparams(shape, hyper)
     ref = oracle.solve(vol.b, vol.w, p, 1, K, with_hist=False)
     want = oracle.objective(ref.x, vol.b, vol.w, ref.om1, ref.omtv, p)
     err = rel_l2(x, ref.x)
-    print(f"512^3 after {K} iterations: rel-L2 {err:.2e}, objective rel {abs(obj[3] - want[3]) / abs(want[3]):.2e}")
+    e16 = rel_l2(x16, ref.x)
+    print(f"512^3 after {K} iterations: rel-L2 {err:.2e}, objective rel {abs(obj[3] - want[3]) / abs(want[3]):.2e}; "
+          f"BF16 storage vs the FP32-input oracle {e16:.2e}")
     assert err <= 1e-5
     np.testing.assert_allclose(obj[3], want[3], rtol=1e-6)
+    assert e16 <= 2e-2
+
+
+def test_vol512_bf16_storage_at_the_gap():
+    """BF16 b, w at 512^3 for the 159 iterations to the gap against the oracle
+    fed the BF16-rounded data (round to nearest even, as the device
+    conversion): the arithmetic gate holds for the BF16 form too."""
+    vol, hyper, _, _ = synth.workload("vol512")
+    shape = vol.b.shape
+    K = 159
+    x16, obj16 = solve_512(vol, hyper, K, data_dtype="bf16")
+    b16 = torch.from_numpy(vol.b).to(torch.bfloat16).float().numpy()
+    w16 = torch.from_numpy(vol.w).to(torch.bfloat16).float().numpy()
+    del vol
+    p = oparams(shape, hyper)
+    ref = oracle.solve(b16, w16, p, 1, K, with_hist=False)
+    want = oracle.objective(ref.x, b16, w16, ref.om1, ref.omtv, p)
+    err = rel_l2(x16, ref.x)
+    print(f"512^3 BF16 storage after {K} iterations: rel-L2 {err:.2e} vs the oracle fed BF16-rounded data, "
+          f"objective rel {abs(obj16[3] - want[3]) / abs(want[3]):.2e}")
+    assert err <= 1e-5
+    np.testing.assert_allclose(obj16[3], want[3], rtol=1e-6)
 
 
 def test_vol512_sampled_step():
