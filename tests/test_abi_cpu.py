@@ -19,6 +19,30 @@ def test_header_matches_binding_list():
     assert declared_symbols() == sorted(spg.EXPORTS)
 
 
+def test_header_is_self_contained_c_and_cxx(tmp_path):
+    """A C caller needs nothing but the header: it compiles as strict C99 and
+    as C++17 (with extern "C" linkage), and a C program calling every entry
+    point links against the library (the calls themselves are not run)."""
+    import shutil
+    import subprocess
+    hdr = os.path.join(ROOT, "include", "spg.h")
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    for lang, std in (("c", "-std=c99"), ("c++", "-std=c++17")):
+        r = subprocess.run([gcc if lang == "c" else shutil.which("g++") or gcc, "-fsyntax-only", std, "-Wall",
+                            "-Wextra", "-Werror", "-x", lang, hdr], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+    lib = spg.load()
+    calls = "\n".join(f"    (void)&{name};" for name in declared_symbols())
+    src = tmp_path / "caller.c"
+    src.write_text(f'#include "spg.h"\nint main(void)\n{{\n{calls}\n    return 0;\n}}\n')
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        str(tmp_path / "caller"), lib._name], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_library_exports_every_declared_symbol():
     lib = spg.load()
     for name in declared_symbols():
