@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--difference", default="backward", choices=["backward", "forward"])
     ap.add_argument("--boundary", default="neumann", choices=["neumann", "periodic"])
     ap.add_argument("--tv-weight", default="inside", choices=["inside", "post_div"])
+    ap.add_argument("--fourier-shape", default="512,512,512",
+                    help="nz,ny,nx of the fourier512 workload (smaller shapes for profiling captures)")
     ap.add_argument("--full-schedule", action="store_true",
                     help="with --impl reference: time the oracle on the whole volume for the workload's "
                          "rounds x iterations (one line, no warm-up)")
@@ -701,13 +703,14 @@ def run_fourier(args):
     from paper_1905_13408_gb300 import spg, synth
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    n = 512
-    fv = synth.make_fourier_volume((n, n, n), 12800, 200.0, 1102)
+    shape = tuple(int(v) for v in args.fourier_shape.split(","))
+    fv = synth.make_fourier_volume(shape, 12800 if shape == (512, 512, 512) else 1600,
+                                   200.0 if shape == (512, 512, 512) else 0.4 * min(shape), 1102)
     yh = torch.from_numpy(synth.half_spectrum(fv.y).astype(np.complex64)).cuda()
     nh = torch.from_numpy(synth.half_spectrum(fv.N).astype(np.float32)).cuda()
     del fv
     hyper = dict(synth.DEFAULT_HYPER)
-    s = spg.SPG(dict(shape=(n, n, n), **hyper), stream=stream.cuda_stream, hist_every=args.hist_every)
+    s = spg.SPG(dict(shape=shape, **hyper), stream=stream.cuda_stream, hist_every=args.hist_every)
     s.set_data_fourier(0, yh, nh)
     s.reweight()
     s.iterate(args.warmup)
@@ -722,7 +725,7 @@ def run_fourier(args):
     launches = s.launch_count() - l0
     obj = s.objective(0)
     s.close()
-    nvox = n ** 3
+    nvox = shape[0] * shape[1] * shape[2]
     peaks, kind = measured_peaks()
     # minimal bytes per voxel (a half-spectrum coefficient is half a voxel):
     # forward transform of y_k (4 + 4), residual spectrum N F / V - C
@@ -730,7 +733,7 @@ def run_fourier(args):
     # also writes the next y (28 + 4 B)
     bpv = 8 + 14 + 8 + 32
     achieved = bpv * nvox * args.steps / (ms / 1e3) / 1e9
-    print(json.dumps({"metric": "Gvoxel-iter/s, Fourier-domain data term (Eq. 31), 512^3",
+    print(json.dumps({"metric": "Gvoxel-iter/s, Fourier-domain data term (Eq. 31), %dx%dx%d" % shape,
                       "value": nvox * args.steps / (ms / 1e3) / 1e9, "unit": UNIT, "steps": args.steps,
                       "ms_per_step": ms / args.steps, "dtype": "f32", "data": "synthetic",
                       "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",

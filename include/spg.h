@@ -179,12 +179,13 @@ spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg
  * interleaved re/im) and N_half (float32, N >= 0) hold the real-to-complex
  * half spectrum [nz][ny][nx/2+1] of a Hermitian y and a centro-symmetric N;
  * host or device pointers, copied. Each iteration then transforms the
- * extrapolated point y_k (y_k is written by the previous fused step: per-plane
- * 2-D transforms by cuFFT, loaded at run time, and the library's own
- * transform along z), forms the residual spectrum N A y_k - D y inside the z
- * pass and transforms back to get the data gradient A^H (N A y_k - D y) for
- * the fused step; L = max N + 12 lambda_tv max(omtv) / mu. nz <= 4096 (else
- * SPG_EINVAL). Needs SPG_F32 data storage and
+ * extrapolated point y_k (written by the previous fused step), forms the
+ * residual spectrum N A y_k - D y and transforms back to get the data
+ * gradient A^H (N A y_k - D y) for the fused step; for power-of-two nz from 8
+ * to 4096 the transforms are per-plane 2-D ones (cuFFT, loaded at run time)
+ * and the library's own transform along z, which forms the residual inside
+ * its pass; for other nz, 3-D cuFFT transforms around a separate spectrum
+ * pass. L = max N + 12 lambda_tv max(omtv) / mu. Needs SPG_F32 data storage and
  * SPG_STORE_DELTA; certificate and adjoint are not available in this
  * mode. The objective history records the l1 and TV terms only (its data
  * column is 0); spg_objective returns all terms. spg_set_data switches back

@@ -113,10 +113,13 @@ struct spg_ctx {
     float *certQ = nullptr;  // 3-vector field of the certificate passes (allocated on first use)
     float *Nmax = nullptr;
     double *fpart = nullptr; // reduction partials of the Fourier data value
-    cufftHandle pr2c = 0, pc2r = 0;  // per-plane 2-D transforms (batch nz)
+    // zown: per-plane 2-D transforms (batch nz) and the own transform along z
+    // (power-of-two nz); otherwise 3-D transforms and a separate spectrum pass
+    cufftHandle pr2c = 0, pc2r = 0;
     bool plans = false;
-    ZPlan zplan{};                   // the transform along z (own kernels)
-    float2 *ztw = nullptr;           // its twiddle table
+    bool zown = false;
+    ZPlan zplan{};
+    float2 *ztw = nullptr;           // twiddle table of the transform along z
     long long nhalf = 0;
 
     cudaGraphExec_t gexec = nullptr;
@@ -547,8 +550,10 @@ cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
         if (cf.exec_r2c(ctx->pr2c, ctx->Ybuf, reinterpret_cast<cufftComplex *>(ctx->Fh)) != CUFFT_SUCCESS)
             return cudaErrorUnknown;
         const bool anc = ctx->gamma_f > 0.f;
-        e = launch_zfft_residual(ctx->Fh, anc ? ctx->Nst : ctx->Nh, anc ? ctx->Cst : ctx->Ch, (float)(1.0 / V),
-                                 ctx->zplan, ctx->ztw, ctx->stream);
+        const float *Nw = anc ? ctx->Nst : ctx->Nh;
+        const float2 *Cw = anc ? ctx->Cst : ctx->Ch;
+        e = ctx->zown ? launch_zfft_residual(ctx->Fh, Nw, Cw, (float)(1.0 / V), ctx->zplan, ctx->ztw, ctx->stream)
+                      : launch_spec_scale(ctx->Fh, Nw, Cw, ctx->nhalf, (float)(1.0 / V), ctx->stream);
         if (e != cudaSuccess) return e;
         if (cf.exec_c2r(ctx->pc2r, reinterpret_cast<cufftComplex *>(ctx->Fh), static_cast<float *>(ctx->B)) !=
             CUFFT_SUCCESS)
@@ -999,22 +1004,30 @@ spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const
         CK(cudaMemsetAsync(ctx->Ybuf, 0, (size_t)ctx->total * sizeof(float), ctx->stream), "memset");
     }
     if (!ctx->plans) {
-        // 3-D transforms = a batch of per-plane 2-D transforms (x, y) and the own transform along z
+        // power-of-two nz: 3-D transforms = a batch of per-plane 2-D transforms
+        // (x, y) and the own transform along z, which also forms the residual
+        // spectrum; other lengths: 3-D library transforms around a spectrum pass
         std::vector<float2> tw;
-        if (!zfft_plan(d.nz, (long long)d.ny * nxh, &ctx->zplan, &tw))
-            return fail(ctx, SPG_EINVAL, "spg_set_data_fourier: nz out of range for the transform along z");
-        CK(dalloc(&ctx->ztw, tw.size() * sizeof(float2)), "alloc");
-        CK(cudaMemcpyAsync(ctx->ztw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream),
-           "twiddles");
-        CK(cudaStreamSynchronize(ctx->stream), "synchronise");
-        int n[2] = {d.ny, d.nx};
-        int real_embed[2] = {d.ny, d.pitch};
-        int cplx_embed[2] = {d.ny, nxh};
-        const int rdist = d.ny * d.pitch, cdist = d.ny * nxh;
-        if (cf.plan_many(&ctx->pr2c, 2, n, real_embed, 1, rdist, cplx_embed, 1, cdist, CUFFT_R2C, d.nz) != CUFFT_SUCCESS)
+        ctx->zown = zfft_plan(d.nz, (long long)d.ny * nxh, &ctx->zplan, &tw);
+        if (ctx->zown) {
+            CK(dalloc(&ctx->ztw, tw.size() * sizeof(float2)), "alloc");
+            CK(cudaMemcpyAsync(ctx->ztw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                               ctx->stream),
+               "twiddles");
+            CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+        }
+        const int rank = ctx->zown ? 2 : 3;
+        int n[3] = {d.nz, d.ny, d.nx};
+        int real_embed[3] = {d.nz, d.ny, d.pitch};
+        int cplx_embed[3] = {d.nz, d.ny, nxh};
+        const int rdist = (ctx->zown ? 1 : d.nz) * d.ny * d.pitch, cdist = (ctx->zown ? 1 : d.nz) * d.ny * nxh;
+        const int batch = ctx->zown ? d.nz : 1;
+        const int o = 3 - rank;  // the 2-D plans take the last two extents
+        if (cf.plan_many(&ctx->pr2c, rank, n + o, real_embed + o, 1, rdist, cplx_embed + o, 1, cdist, CUFFT_R2C,
+                         batch) != CUFFT_SUCCESS)
             return fail(ctx, SPG_ECUDA, "spg_set_data_fourier: cufft plan");
-        if (cf.plan_many(&ctx->pc2r, 2, n, cplx_embed, 1, cdist, real_embed, 1, rdist, CUFFT_C2R, d.nz) !=
-            CUFFT_SUCCESS) {
+        if (cf.plan_many(&ctx->pc2r, rank, n + o, cplx_embed + o, 1, cdist, real_embed + o, 1, rdist, CUFFT_C2R,
+                         batch) != CUFFT_SUCCESS) {
             cf.destroy(ctx->pr2c);
             return fail(ctx, SPG_ECUDA, "spg_set_data_fourier: cufft plan");
         }
@@ -1072,8 +1085,10 @@ spg_status spg_set_anchor(spg_ctx *ctx, int vol, float gamma, const float *x_anc
         const double V = (double)d.nx * d.ny * d.nz;
         if (spg::cufft_api().exec_r2c(ctx->pr2c, ctx->Anc, reinterpret_cast<cufftComplex *>(ctx->Fh)) != CUFFT_SUCCESS)
             return fail(ctx, SPG_ECUDA, "spg_set_anchor: transform");
-        CK(launch_zfft(ctx->Fh, ctx->zplan, ctx->ztw, ctx->stream), "transform along z");
-        ctx->launches += 1;
+        if (ctx->zown) {
+            CK(launch_zfft(ctx->Fh, ctx->zplan, ctx->ztw, ctx->stream), "transform along z");
+            ctx->launches += 1;
+        }
         CK(launch_spec_anchor(ctx->Nh, ctx->Ch, ctx->Fh, ctx->nhalf, 2.f * gamma, (float)(1.0 / V), ctx->Nst, ctx->Cst,
                               ctx->stream),
            "anchor spectrum");
@@ -1231,8 +1246,10 @@ spg_status spg_objective(spg_ctx *ctx, int vol, double out[4])
         if (spg::cufft_api().exec_r2c(ctx->pr2c, ctx->Ybuf, reinterpret_cast<cufftComplex *>(ctx->Fh)) !=
             CUFFT_SUCCESS)
             return fail(ctx, SPG_ECUDA, "spg_objective: transform");
-        CK(launch_zfft(ctx->Fh, ctx->zplan, ctx->ztw, ctx->stream), "transform along z");
-        ctx->launches += 1;
+        if (ctx->zown) {
+            CK(launch_zfft(ctx->Fh, ctx->zplan, ctx->ztw, ctx->stream), "transform along z");
+            ctx->launches += 1;
+        }
         CK(launch_spec_data_value(ctx->Fh, ctx->Yh, ctx->Nh, d.nz, d.ny, d.nx, (float)(1.0 / std::sqrt(V)),
                                   ctx->fpart, ctx->fpart + 1024, ctx->stream),
            "data value");

@@ -3,8 +3,9 @@
 // whose gradient A^H (N A x - D y) is formed each iteration at the
 // extrapolated point y_k by per-plane real-to-complex transforms (cuFFT), one
 // pass along z that transforms, scales by N, subtracts the data spectrum and
-// transforms back (spg_zfft.cu), and per-plane complex-to-real transforms,
-// then consumed by the fused step. Subtracting before the inverse transform
+// transforms back (spg_zfft.cu, power-of-two nz), and per-plane
+// complex-to-real transforms; for other nz by 3-D transforms around a
+// separate spectrum pass (spec_scale_kernel). The fused step consumes it. Subtracting before the inverse transform
 // keeps FP32 rounding relative to the residual rather than to A^H N A y_k,
 // which for the strongly uneven N of gridded data (many orders of magnitude
 // between low and high frequencies) is the difference between errors of 1e-7
@@ -26,6 +27,20 @@ __global__ void form_y_kernel(const DevState *st, const VolDesc *vols, const flo
     const float *d = cur == 0 ? d0 : d1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = fmaf(b, d[i], x[i]);
+}
+
+// F <- N F scale - C: the unnormalised spectrum of the residual (scale = 1/V,
+// C = sqrt(N) y / sqrt(V)), the separate spectrum pass between 3-D transforms.
+__global__ void spec_scale_kernel(float2 *F, const float *N, const float2 *C, long long n, float scale)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float m = N[i] * scale;
+        const float2 c = C[i];
+        float2 f = F[i];
+        f.x = fmaf(f.x, m, -c.x);
+        f.y = fmaf(f.y, m, -c.y);
+        F[i] = f;
+    }
 }
 
 __global__ void spec_prep_kernel(float2 *F, const float2 *Y, const float *N, long long n, float scale)
@@ -209,6 +224,12 @@ cudaError_t launch_form_y(const DevState *st, const VolDesc *vols, const float *
                           long long n, cudaStream_t s)
 {
     form_y_kernel<<<grid_for(n), 256, 0, s>>>(st, vols, beta, xbuf[0], xbuf[1], xbuf[2], xbuf[3], y, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_scale(float2 *F, const float *N, const float2 *C, long long n, float scale, cudaStream_t s)
+{
+    spec_scale_kernel<<<grid_for(n), 256, 0, s>>>(F, N, C, n, scale);
     return cudaGetLastError();
 }
 

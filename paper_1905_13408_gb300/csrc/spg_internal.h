@@ -177,6 +177,8 @@ cudaError_t launch_spec_anchor(const float *N, const float2 *C, const float2 *FA
 // *out = sum of (x - a)^2 over the volume's voxels (pitched, n elements; partials: 1024 doubles).
 cudaError_t launch_sq_diff(const float *x, const float *a, int nx, int pitch, long long n, double *partials,
                            double *out, cudaStream_t s);
+// F <- N F scale - C over n half-spectrum coefficients.
+cudaError_t launch_spec_scale(float2 *F, const float *N, const float2 *C, long long n, float scale, cudaStream_t s);
 // F = Y * sqrt(N) * scale.
 cudaError_t launch_spec_prep(float2 *F, const float2 *Y, const float *N, long long n, float scale,
                              cudaStream_t s);
@@ -187,17 +189,16 @@ cudaError_t launch_spec_max(const float *N, long long n, float *out, cudaStream_
 cudaError_t launch_spec_data_value(const float2 *F, const float2 *Y, const float *N, int nz, int ny, int nx,
                                    float scale, double *partials, double *out, cudaStream_t s);
 
-// Transform along z of a half spectrum viewed as [n][M] (spg_zfft.cu).
-constexpr int kZMaxN = 4096, kZMaxStages = 24;
+// Transform along z of a half spectrum viewed as [n][M] (spg_zfft.cu),
+// power-of-two n from 8 to 4096.
+constexpr int kZMaxN = 4096;
 struct ZPlan {
-    int n;                     // transform length (nz)
-    int nst;                   // stages
-    int radix[kZMaxStages];    // radix of each stage (8, 4, 2 first, then odd primes)
-    int cols;                  // columns per CTA (general lengths)
-    int log2n;                 // > 0: power-of-two length 8 .. 4096, the register-resident kernel
-    long long M;               // columns (ny (nx/2 + 1))
+    int n;        // transform length (nz)
+    int log2n;    // log2 of n
+    long long M;  // columns (ny (nx/2 + 1))
 };
-// Plan and twiddle table w^m = e^(-2 pi i m / nz), m < nz; false if nz is out of range.
+// Plan and twiddle table w^m = e^(-2 pi i m / nz), m < nz; false if nz is not
+// a power of two in range (the caller then uses 3-D library transforms).
 bool zfft_plan(int nz, long long M, ZPlan *p, std::vector<float2> *table);
 // F <- A_z F (unnormalised forward transform along z of every column).
 cudaError_t launch_zfft(float2 *F, const ZPlan &p, const float2 *tw, cudaStream_t s);

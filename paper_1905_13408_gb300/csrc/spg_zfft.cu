@@ -1,19 +1,19 @@
 // Transform along z of a half spectrum, and the Fourier-domain data term's
 // spectrum pass fused between a forward and an inverse z transform (Sec. 2.5,
-// Eq. 31). The half spectrum [nz][ny][nx/2+1] is viewed as [nz][M] with
-// M = ny (nx/2+1) columns, each a line along z; a CTA takes kC consecutive
-// columns, so every z row of its tile is one contiguous run of kC complex
+// Eq. 31), for power-of-two nz from 8 to 4096. The half spectrum
+// [nz][ny][nx/2+1] is viewed as [nz][M] with M = ny (nx/2+1) columns, each a
+// line along z; a CTA takes C consecutive columns (16 where 1024 threads
+// allow it), so every z row of its tile is one contiguous run of C complex
 // values in HBM.
 //
-// In shared memory each tile goes through a Stockham auto-sort FFT (the
-// formulation of Govindaraju et al., SC 2008): for a stage of radix R over
-// sub-transforms of span Ns, butterfly j takes the R inputs j + r n/R,
-// multiplies input r by w^(r k n/(Ns R)) (k = j mod Ns, w = e^(-2 pi i/n)),
-// transforms them with an R-point DFT and writes output q to
-// (j - k) R + k + q Ns of the other buffer; after the last stage the line is
-// in natural order. Radices 8, 4 and 2 have hand-written butterflies; any
-// other prime factor takes a direct R-point DFT. The twiddle table w^m
-// (m < n) is computed on the host in double precision.
+// Each line goes through a Stockham auto-sort FFT (the formulation of
+// Govindaraju et al., SC 2008): for a stage of radix R over sub-transforms of
+// span Ns, butterfly j takes the R inputs j + r n/R, multiplies input r by
+// w^(r k n/(Ns R)) (k = j mod Ns, w = e^(-2 pi i/n)), transforms them with an
+// R-point DFT and writes output q to (j - k) R + k + q Ns; after the last
+// stage the line is in natural order. Stages are radix 8 and one final radix
+// 2 or 4. The twiddle table w^m (m < n) is computed on the host in double
+// precision.
 //
 // Fused mode: F <- A_z^-1 ( (A_z F) N s - C ) per column, which together with
 // the per-plane 2-D transforms on either side gives the residual spectrum of
@@ -81,126 +81,6 @@ __device__ __forceinline__ void dft8(float2 *v)
     v[6] = csub(e2, o2);
     v[3] = cadd(e3, o3);
     v[7] = csub(e3, o3);
-}
-
-// One butterfly of a hand-written radix R in {2, 4, 8}.
-template <int R, int S, int C>
-__device__ __forceinline__ void butterfly(const float2 *src, float2 *dst, const float2 *T, int n, int Ns, int j, int c)
-{
-    const int nR = n / R;
-    const int k = j % Ns;
-    const int tstep = n / (Ns * R);
-    float2 v[R];
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        v[r] = src[(j + r * nR) * C + c];
-        if (r > 0 && k > 0) v[r] = cmul(v[r], twiddle<S>(T, r * k * tstep));
-    }
-    if (R == 2) {
-        const float2 a = v[0];
-        v[0] = cadd(a, v[1]);
-        v[1] = csub(a, v[1]);
-    } else if (R == 4) {
-        dft4<S>(v[0], v[1], v[2], v[3]);
-    } else {
-        dft8<S>(v);
-    }
-    const int base = (j - k) * R + k;
-#pragma unroll
-    for (int q = 0; q < R; q++) dst[(base + q * Ns) * C + c] = v[q];
-}
-
-// One butterfly of any other radix R: a direct R-point DFT, each output
-// summed from the inputs in shared memory (the R-th roots of unity are the
-// table entries m n/R).
-template <int S, int C>
-__device__ void butterfly_any(const float2 *src, float2 *dst, const float2 *T, int n, int R, int Ns, int j, int c)
-{
-    const int nR = n / R;
-    const int k = j % Ns;
-    const int tstep = n / (Ns * R);
-    const int base = (j - k) * R + k;
-    for (int q = 0; q < R; q++) {
-        float2 acc = make_float2(0.f, 0.f);
-        for (int r = 0; r < R; r++) {
-            float2 x = src[(j + r * nR) * C + c];
-            if (r > 0 && k > 0) x = cmul(x, twiddle<S>(T, r * k * tstep));
-            acc = cadd(acc, cmul(x, twiddle<S>(T, ((r * q) % R) * nR)));
-        }
-        dst[(base + q * Ns) * C + c] = acc;
-    }
-}
-
-// All stages of one transform of sign S over the CTA's kC lines; the result
-// ends in *src (the buffers swap after every stage).
-template <int S, int C>
-__device__ void stages(float2 *&src, float2 *&dst, const float2 *T, const ZPlan &p)
-{
-    const int n = p.n;
-    int Ns = 1;
-    for (int s = 0; s < p.nst; s++) {
-        const int R = p.radix[s];
-        const int nb = (n / R) * C;
-        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-            const int c = t % C, j = t / C;
-            if (R == 8)
-                butterfly<8, S, C>(src, dst, T, n, Ns, j, c);
-            else if (R == 4)
-                butterfly<4, S, C>(src, dst, T, n, Ns, j, c);
-            else if (R == 2)
-                butterfly<2, S, C>(src, dst, T, n, Ns, j, c);
-            else
-                butterfly_any<S, C>(src, dst, T, n, R, Ns, j, c);
-        }
-        __syncthreads();
-        float2 *t = src;
-        src = dst;
-        dst = t;
-        Ns *= R;
-    }
-}
-
-constexpr int kZThreads = 256;
-constexpr int kZMaxSmem = 100 * 1024;  // two tile buffers and the twiddle table
-
-// FUSED = false: F <- A_z F (unnormalised forward transform along z).
-// FUSED = true:  F <- A_z^-1 ((A_z F) N scale - Cd) (inverse unnormalised).
-template <int C, bool FUSED>
-__global__ void __launch_bounds__(kZThreads) zfft_kernel(float2 *F, const float *N, const float2 *Cd, float scale,
-                                                         const __grid_constant__ ZPlan p,
-                                                         const float2 *tw)
-{
-    extern __shared__ float2 zsm[];
-    const int n = p.n;
-    float2 *src = zsm, *dst = zsm + (size_t)n * C;
-    float2 *T = zsm + (size_t)2 * n * C;
-    const long long M = p.M;
-    const long long q0 = (long long)blockIdx.x * C;
-    const int ncol = (int)(M - q0 < C ? M - q0 : C);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) T[i] = tw[i];
-    for (int i = threadIdx.x; i < n * C; i += blockDim.x) {
-        const int z = i / C, c = i % C;
-        src[i] = c < ncol ? F[z * M + q0 + c] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    stages<-1, C>(src, dst, T, p);
-    if (FUSED) {
-        for (int i = threadIdx.x; i < n * C; i += blockDim.x) {
-            const int z = i / C, c = i % C;
-            if (c >= ncol) continue;
-            const long long g = z * M + q0 + c;
-            const float m = N[g] * scale;
-            const float2 cd = Cd[g];
-            const float2 f = src[i];
-            src[i] = make_float2(fmaf(f.x, m, -cd.x), fmaf(f.y, m, -cd.y));
-        }
-        __syncthreads();
-        stages<1, C>(src, dst, T, p);
-    }
-    for (int i = threadIdx.x; i < n * C; i += blockDim.x) {
-        const int z = i / C, c = i % C;
-        if (c < ncol) F[z * M + q0 + c] = src[i];
-    }
 }
 
 // Power-of-two lengths 8 .. 4096: a register-resident form of the same
@@ -352,50 +232,17 @@ cudaError_t set_pow2_limits()
     return e;
 }
 
-template <int C>
-size_t zfft_smem(int n)
-{
-    return ((size_t)2 * n * C + n) * sizeof(float2);
-}
-
-template <int C, bool FUSED>
-cudaError_t launch_c(float2 *F, const float *N, const float2 *Cd, float scale, const ZPlan &p, const float2 *tw,
-                     cudaStream_t s)
-{
-    const size_t smem = zfft_smem<C>(p.n);
-    if (smem > (size_t)kZMaxSmem) return cudaErrorInvalidValue;
-    const long long grid = (p.M + C - 1) / C;
-    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-    zfft_kernel<C, FUSED><<<(unsigned)grid, kZThreads, smem, s>>>(F, N, Cd, scale, p, tw);
-    return cudaGetLastError();
-}
-
 template <bool FUSED>
 cudaError_t launch_any(float2 *F, const float *N, const float2 *Cd, float scale, const ZPlan &p, const float2 *tw,
                        cudaStream_t s)
 {
-    if (p.log2n > 0) return launch_pow2_any<FUSED>(F, N, Cd, scale, p, tw, s);
-    switch (p.cols) {
-    case 8: return launch_c<8, FUSED>(F, N, Cd, scale, p, tw, s);
-    case 4: return launch_c<4, FUSED>(F, N, Cd, scale, p, tw, s);
-    case 2: return launch_c<2, FUSED>(F, N, Cd, scale, p, tw, s);
-    case 1: return launch_c<1, FUSED>(F, N, Cd, scale, p, tw, s);
-    default: return cudaErrorInvalidValue;
-    }
+    return launch_pow2_any<FUSED>(F, N, Cd, scale, p, tw, s);
 }
 
 // The opt-in shared-memory limit of every instance, set when a plan is made
 // (before any launch, so never inside a graph capture).
 cudaError_t set_smem_limits()
 {
-    const void *fns[] = {(const void *)zfft_kernel<8, false>, (const void *)zfft_kernel<4, false>,
-                         (const void *)zfft_kernel<2, false>, (const void *)zfft_kernel<1, false>,
-                         (const void *)zfft_kernel<8, true>,  (const void *)zfft_kernel<4, true>,
-                         (const void *)zfft_kernel<2, true>,  (const void *)zfft_kernel<1, true>};
-    for (const void *f : fns) {
-        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kZMaxSmem);
-        if (e != cudaSuccess) return e;
-    }
     const cudaError_t es[] = {set_pow2_limits<3>(), set_pow2_limits<4>(),  set_pow2_limits<5>(),
                               set_pow2_limits<6>(), set_pow2_limits<7>(),  set_pow2_limits<8>(),
                               set_pow2_limits<9>(), set_pow2_limits<10>(), set_pow2_limits<11>(),
@@ -409,32 +256,13 @@ cudaError_t set_smem_limits()
 
 bool zfft_plan(int nz, long long M, ZPlan *p, std::vector<float2> *table)
 {
-    if (nz < 1 || nz > kZMaxN || M < 1) return false;
+    if (nz < 8 || nz > kZMaxN || (nz & (nz - 1)) != 0 || M < 1) return false;
     static const cudaError_t limits = set_smem_limits();
     if (limits != cudaSuccess) return false;
     ZPlan q{};
     q.n = nz;
     q.M = M;
-    q.log2n = 0;
-    if (nz >= 8 && (nz & (nz - 1)) == 0)
-        while ((1 << q.log2n) < nz) q.log2n++;
-    int m = nz;
-    while (m % 8 == 0) q.radix[q.nst++] = 8, m /= 8;
-    while (m % 4 == 0) q.radix[q.nst++] = 4, m /= 4;
-    while (m % 2 == 0) q.radix[q.nst++] = 2, m /= 2;
-    for (int f = 3; m > 1; f += 2)
-        while (m % f == 0) {
-            if (q.nst >= kZMaxStages) return false;
-            q.radix[q.nst++] = f;
-            m /= f;
-        }
-    // columns per CTA: the widest tile whose two buffers and table fit the limit
-    q.cols = 1;
-    for (int c : {8, 4, 2})
-        if (((size_t)2 * nz * c + nz) * sizeof(float2) <= (size_t)kZMaxSmem) {
-            q.cols = c;
-            break;
-        }
+    while ((1 << q.log2n) < nz) q.log2n++;
     table->resize(nz);
     const double pi = 3.14159265358979323846;
     for (int j = 0; j < nz; j++) {
