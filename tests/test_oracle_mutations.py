@@ -57,6 +57,10 @@ MUTATIONS = {
                                          "if (p->restart && restart_dot(p, x, xprev, xnext, beta[km]) < 0.0)"),
     "Lipschitz bound with |D|^2 <= 4": ("return m + 12.0 * p->lambda_tv * max_omtv / p->mu",
                                          "return m + 4.0 * p->lambda_tv * max_omtv / p->mu"),
+    "certificate with grad f(y) - grad f(x+)": ("double r = gx[v] - gy[v] + (y[v] - xplus[v]) / tau;",
+                                               "double r = gy[v] - gx[v] + (y[v] - xplus[v]) / tau;"),
+    "certificate without the 1/tau": ("double r = gx[v] - gy[v] + (y[v] - xplus[v]) / tau;",
+                                      "double r = gx[v] - gy[v] + (y[v] - xplus[v]);"),
     "gamma term without its factor 2 in the gradient": ("out[v] += 2.0 * p->gamma * (x[v] - p->anchor[v]);",
                                                         "out[v] += p->gamma * (x[v] - p->anchor[v]);"),
 }
@@ -84,6 +88,7 @@ QUICK = [
     pins.test_adjoint_matches_central_differences,
     pins.test_gradient_restart_converges_faster,
     pins.test_gamma_term_folds_into_data_and_weight,
+    pins.test_certificate_is_the_norm_of_a_subgradient,
     lambda o: readings.test_div_is_the_adjoint_of_grad("forward", "neumann", (5, 7, 9)),
     lambda o: readings.test_div_is_the_adjoint_of_grad("backward", "periodic", (5, 7, 9)),
     lambda o: readings.test_div_is_the_adjoint_of_grad("forward", "periodic", (5, 7, 9)),

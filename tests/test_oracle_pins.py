@@ -359,6 +359,33 @@ def test_certificate_bounds_gap(orc):
     assert 0 <= gap <= cert / (2 * w.min()) * (1 + 1e-9) + 1e-14
 
 
+def test_certificate_is_the_norm_of_a_subgradient(orc):
+    """The certificate is |r|^2 for the r that the prox step makes a
+    subgradient of F at x+: r - grad f(x+) = grad f(y) -> (y - x+)/tau - grad
+    f(y) lies in lambda_l1 om1 d|x+| (equal to lambda_l1 om1 sign x+ where x+
+    is non-zero, within that bound where it is zero), from the soft-threshold's
+    optimality condition (Eq. 21), with grad f pinned on its own by finite
+    differences. A random y (not a fixed point) keeps r far from zero; a large
+    lambda_l1 makes the threshold zero a part of the voxels."""
+    b, w, p = _tiny_problem(orc, mu=0.01, lam_l1=30.0)
+    rng = np.random.default_rng(23)
+    y = rng.standard_normal(b.shape)
+    om1 = rng.uniform(0.3, 1.0, b.shape)
+    omtv = rng.uniform(0.3, 1.0, b.shape)
+    tau = 1.0 / orc.lipschitz(w, omtv.max(), p)
+    xplus = orc.step(y, y, 0.0, tau, b, w, om1, omtv, p)
+    assert np.count_nonzero(xplus) > 5 and np.count_nonzero(xplus == 0) > 5
+    s = (y - xplus) / tau - orc.grad_f(y, b, w, omtv, p)   # the l1 part of r
+    t = p.lambda_l1 * om1
+    nz = xplus != 0
+    np.testing.assert_allclose(s[nz], t[nz] * np.sign(xplus[nz]), rtol=1e-9, atol=1e-9)
+    assert np.all(np.abs(s[~nz]) <= t[~nz] * (1 + 1e-9) + 1e-12)
+    r = orc.grad_f(xplus, b, w, omtv, p) + s
+    cert = orc.certificate(y, xplus, tau, b, w, omtv, p)
+    assert cert == pytest.approx(float((r * r).sum()), rel=1e-12)
+    assert cert > 1e-3
+
+
 def test_reweighting_majorises_log_penalty(orc):
     """Sec. 2.1 (tangent majoriser of the log penalty, Eq. 9/11): with the TV
     term off, each fully solved round does not increase
