@@ -494,7 +494,7 @@ def run_spg(args):
     return 0
 
 
-def measure_e2e(vol, hyper, args, stream, iters=100, reps=3, world=1):
+def measure_e2e(vol, hyper, args, stream, iters=100, reps=5, world=1):
     """Through the public API with host buffers. Each step uploads b and w from
     pinned host memory (with the device validation), re-weights, runs `iters`
     fused iterations, reads the objective and downloads x to pinned host
