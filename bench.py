@@ -19,6 +19,7 @@ on a bounded z-slab of the same workload.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -528,6 +529,12 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=5, world=1):
             import torch.distributed as dist
             dist.barrier()
 
+    # Host-timed loops: Python's cyclic garbage collector is paused for them
+    # (a full collection over the interpreter's objects stalled single steps
+    # by tens of milliseconds), as a serving loop would keep it out of its
+    # steps; it runs once before.
+    gc.collect()
+    gc.disable()
     # one context, steps back to back
     s = ctxs[0]
     phases = {"upload_validate": 0.0, "reweight_iterate_objective": 0.0, "download": 0.0}
@@ -579,6 +586,7 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=5, world=1):
         streams[i % 2].synchronize()
         step_ms.append(1e3 * (time.perf_counter() - ts))
     dt = max_over_ranks(time.perf_counter() - t0, world)
+    gc.enable()
     for c in ctxs:
         c.close()
     return {"value": world * nvox * iters * steps / dt / 1e9, "unit": UNIT,
