@@ -258,8 +258,9 @@ def run_reference(args):
         xp, x = x, xn
     dt = time.perf_counter() - t0
     value = b.size * args.steps / dt / 1e9
+    nz, ny, nx = vol.b.shape
     sample = (f"each step: one FP64 oracle iteration (objective + step) on a {b.shape[2]}x{b.shape[1]}x{nz_slab} "
-              f"z-slab of the 512^3 workload")
+              f"z-slab of the {nx}x{ny}x{nz} workload")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
