@@ -472,7 +472,7 @@ def run_spg(args):
     if not args.no_e2e:
         e2e = measure_e2e(vol, hyper, args, stream, world=world)
     gap = None
-    if not args.no_gap and rank == 0:
+    if not args.no_gap and rank == 0 and world == 1:  # a single-GPU figure; other GPUs are not held for it
         gap = time_to_gap(vol, hyper, args, stream)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
