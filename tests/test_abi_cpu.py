@@ -86,3 +86,31 @@ def test_grid_bad_arguments_rejected_before_device_use():
     assert lib.spg_grid_finish(None, None, None) == spg.SPG_EINVAL
     assert lib.spg_grid_count(None) == 0
     lib.spg_grid_destroy(None)
+
+
+def test_every_handle_entry_point_rejects_a_null_handle():
+    """Each entry point that takes a context or accumulator handle returns
+    SPG_EINVAL for a null one (or, for the void, count and message calls,
+    returns without touching it), before any device work; run in a child
+    process so that a crash would show as a failure here."""
+    import subprocess
+    import sys
+    code = r'''
+import ctypes
+from paper_1905_13408_gb300 import spg
+lib = spg.load()
+bad = []
+for name in spg.EXPORTS:
+    f = getattr(lib, name)
+    if not f.argtypes or f.argtypes[0] is not ctypes.c_void_p:
+        continue
+    args = [None if t in (ctypes.c_void_p,) or isinstance(t, type) and issubclass(t, ctypes._Pointer) else 0
+            for t in f.argtypes]
+    r = f(*args)
+    if f.restype is ctypes.c_int and r != spg.SPG_EINVAL:
+        bad.append((name, r))
+print("BAD", bad)
+'''
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "BAD []" in r.stdout, r.stdout
