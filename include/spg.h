@@ -185,7 +185,8 @@ spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg
  * to 4096 the transforms are per-plane 2-D ones (cuFFT, loaded at run time)
  * and the library's own transform along z, which forms the residual inside
  * its pass; for other nz, 3-D cuFFT transforms around a separate spectrum
- * pass. L = max N + 12 lambda_tv max(omtv) / mu. Needs SPG_F32 data storage and
+ * pass (volumes of fewer than 2^31 voxels; larger ones need a power-of-two
+ * nz, else SPG_EINVAL). L = max N + 12 lambda_tv max(omtv) / mu. Needs SPG_F32 data storage and
  * SPG_STORE_DELTA; certificate and adjoint are not available in this
  * mode. The objective history records the l1 and TV terms only (its data
  * column is 0); spg_objective returns all terms. spg_set_data switches back

@@ -7,6 +7,7 @@
 #include <functional>
 #include <numeric>
 #include <queue>
+#include <climits>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -1020,7 +1021,12 @@ spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const
         int n[3] = {d.nz, d.ny, d.nx};
         int real_embed[3] = {d.nz, d.ny, d.pitch};
         int cplx_embed[3] = {d.nz, d.ny, nxh};
-        const int rdist = (ctx->zown ? 1 : d.nz) * d.ny * d.pitch, cdist = (ctx->zown ? 1 : d.nz) * d.ny * nxh;
+        const long long rdist64 = (long long)(ctx->zown ? 1 : d.nz) * d.ny * d.pitch;
+        const long long cdist64 = (long long)(ctx->zown ? 1 : d.nz) * d.ny * nxh;
+        if (rdist64 > INT_MAX || cdist64 > INT_MAX)
+            return fail(ctx, SPG_EINVAL,
+                        "spg_set_data_fourier: a transform of more than 2^31 elements needs a power-of-two nz");
+        const int rdist = (int)rdist64, cdist = (int)cdist64;
         const int batch = ctx->zown ? d.nz : 1;
         const int o = 3 - rank;  // the 2-D plans take the last two extents
         if (cf.plan_many(&ctx->pr2c, rank, n + o, real_embed + o, 1, rdist, cplx_embed + o, 1, cdist, CUFFT_R2C,
