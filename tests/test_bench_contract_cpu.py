@@ -27,3 +27,17 @@ def test_reference_arm_json_line():
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_byte_model_and_rates():
+    """The roofline's algorithmic bytes per voxel-iteration (each array of the
+    fused step read or written once) and the whole-job rate."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.bytes_per_voxel("f32", "delta") == 32  # x, d, b, w, om1, omtv read; x, d written
+    assert bench.bytes_per_voxel("f32", "prev") == 28   # x_k, x_{k-1}, b, w, om1, omtv read; x written
+    assert bench.bytes_per_voxel("bf16", "delta") == 28
+    assert bench.bytes_per_voxel("bf16", "prev") == 24
+    # 2 ranks x 1e9 voxel-iterations in 500 ms of the slowest rank: 4 Gvoxel-iter/s for the job
+    assert abs(bench.whole_job_rate(1e8, 10, 2, 500.0) - 4.0) < 1e-12
+    assert bench.max_over_ranks(12.5, 1) == 12.5
