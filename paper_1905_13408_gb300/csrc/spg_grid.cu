@@ -39,7 +39,6 @@ thread_local std::string g_grid_err = "no error";
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 152 * 16;
 
-__device__ __forceinline__ int fidx(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
 __device__ __forceinline__ int wrap(int i, int n) { return ((i % n) + n) % n; }
 
 // Add (re, im, w) at full-spectrum point (x, y, z) (any integers), and, unless
