@@ -121,6 +121,8 @@ struct spg_ctx {
     bool zown = false;
     ZPlan zplan{};
     float2 *ztw = nullptr;           // twiddle table of the transform along z
+    ZMaps zmaps[2]{};                // TMA maps of the z pass: with (N, C), with (N + 2 gamma, C + ...)
+    bool zmaps_ok[2] = {false, false};
     long long nhalf = 0;
 
     cudaGraphExec_t gexec = nullptr;
@@ -244,6 +246,29 @@ cudaError_t encode_map(CUtensorMap *m, CUtensorMapDataType dt, void *base, const
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Tensor maps of the TMA-fed z pass over the half spectrum viewed as [n][M]:
+// F and C as rows of 2M floats, N as rows of M floats; boxes of 16 columns by
+// min(n, 256) rows.
+bool encode_zmaps(const ZPlan &p, float2 *F, const float *N, const float2 *C, ZMaps *m)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint32_t rows = (cuuint32_t)(p.n < 256 ? p.n : 256);
+    cuuint32_t estr[2] = {1, 1};
+    auto one = [&](CUtensorMap *map, const void *base, long long inner, size_t row_bytes, cuuint32_t box_inner) {
+        cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)p.n};
+        cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+        cuuint32_t box[2] = {box_inner, rows};
+        return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    std::memset(m, 0, sizeof(*m));
+    return one(&m->f, F, 2 * p.M, (size_t)p.M * sizeof(float2), 32) &&
+           one(&m->n, N, p.M, (size_t)p.M * sizeof(float), 16) &&
+           one(&m->c, C, 2 * p.M, (size_t)p.M * sizeof(float2), 32);
 }
 
 // Tensor maps of one volume for variant v: the iterate boxes of the given
@@ -553,8 +578,13 @@ cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
         const bool anc = ctx->gamma_f > 0.f;
         const float *Nw = anc ? ctx->Nst : ctx->Nh;
         const float2 *Cw = anc ? ctx->Cst : ctx->Ch;
-        e = ctx->zown ? launch_zfft_residual(ctx->Fh, Nw, Cw, (float)(1.0 / V), ctx->zplan, ctx->ztw, ctx->stream)
-                      : launch_spec_scale(ctx->Fh, Nw, Cw, ctx->nhalf, (float)(1.0 / V), ctx->stream);
+        if (!ctx->zown)
+            e = launch_spec_scale(ctx->Fh, Nw, Cw, ctx->nhalf, (float)(1.0 / V), ctx->stream);
+        else if (ctx->zmaps_ok[anc ? 1 : 0])
+            e = launch_zfft_residual_tma(ctx->Fh, (float)(1.0 / V), ctx->zplan, ctx->ztw, ctx->zmaps[anc ? 1 : 0],
+                                         &ctx->st_d->err, ctx->stream);
+        else
+            e = launch_zfft_residual(ctx->Fh, Nw, Cw, (float)(1.0 / V), ctx->zplan, ctx->ztw, ctx->stream);
         if (e != cudaSuccess) return e;
         if (cf.exec_c2r(ctx->pc2r, reinterpret_cast<cufftComplex *>(ctx->Fh), static_cast<float *>(ctx->B)) !=
             CUFFT_SUCCESS)
@@ -1040,6 +1070,8 @@ spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const
         cf.set_stream(ctx->pr2c, ctx->stream);
         cf.set_stream(ctx->pc2r, ctx->stream);
         ctx->plans = true;
+        ctx->zmaps_ok[0] = ctx->zown && zfft_tma_ok(ctx->zplan) &&
+                           encode_zmaps(ctx->zplan, ctx->Fh, ctx->Nh, ctx->Ch, &ctx->zmaps[0]);
     }
     CK(cudaMemcpyAsync(ctx->Yh, y_half, (size_t)ctx->nhalf * sizeof(float2), cudaMemcpyDefault, ctx->stream),
        "copy y");
@@ -1085,6 +1117,7 @@ spg_status spg_set_anchor(spg_ctx *ctx, int vol, float gamma, const float *x_anc
             CK(dalloc(&ctx->Nst, (size_t)ctx->nhalf * sizeof(float)), "alloc");
             CK(dalloc(&ctx->Cst, (size_t)ctx->nhalf * sizeof(float2)), "alloc");
             CK(cudaMemsetAsync(ctx->Anc, 0, (size_t)ctx->total * sizeof(float), ctx->stream), "memset");
+            ctx->zmaps_ok[1] = ctx->zmaps_ok[0] && encode_zmaps(ctx->zplan, ctx->Fh, ctx->Nst, ctx->Cst, &ctx->zmaps[1]);
         }
         spg_status s = copy_volume_in(ctx, ctx->Anc, 4, d, x_anchor);
         if (s != SPG_OK) return s;

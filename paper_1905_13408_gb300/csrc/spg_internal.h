@@ -200,6 +200,17 @@ struct ZPlan {
 // Plan and twiddle table w^m = e^(-2 pi i m / nz), m < nz; false if nz is not
 // a power of two in range (the caller then uses 3-D library transforms).
 bool zfft_plan(int nz, long long M, ZPlan *p, std::vector<float2> *table);
+// Tensor maps of the TMA-fed fused z pass: the spectrum F and the C data as
+// [n][2M] float rows, N as [n][M], boxes of 16 columns by min(n, 256) rows.
+struct ZMaps {
+    CUtensorMap f, n, c;
+};
+// The TMA-fed form applies: n from 128 to 512 and M a multiple of 4 (row strides of 16-byte multiples).
+bool zfft_tma_ok(const ZPlan &p);
+// The fused z pass (as launch_zfft_residual) fed by TMA; a copy that never
+// arrives within 2 s sets *err = SPG_ETIMEOUT.
+cudaError_t launch_zfft_residual_tma(float2 *F, float scale, const ZPlan &p, const float2 *tw, const ZMaps &maps,
+                                     int *err, cudaStream_t s);
 // F <- A_z F (unnormalised forward transform along z of every column).
 cudaError_t launch_zfft(float2 *F, const ZPlan &p, const float2 *tw, cudaStream_t s);
 // F <- A_z^-1 ((A_z F) N scale - Cd), A_z^-1 the unnormalised inverse.

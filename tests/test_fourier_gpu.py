@@ -116,11 +116,12 @@ def test_fourier_param_scales():
     np.testing.assert_allclose(got, want, rtol=2e-5)
 
 
-def test_fourier_anchor_matches_oracle():
+@pytest.mark.parametrize("shape", [(20, 24, 28), (128, 20, 22)])
+def test_fourier_anchor_matches_oracle(shape):
     """The implicit-gradient term gamma |x - a|^2 with the Fourier-domain data
     term (Eq. 31): the spectrum pass uses N + 2 gamma and the anchor's
-    transform; iterate and data-plus-anchor value against the oracle."""
-    shape = (20, 24, 28)
+    transform; iterate and data-plus-anchor value against the oracle, on the
+    library's 3-D transforms (nz = 20) and on the TMA-fed z pass (nz = 128)."""
     fv = synth.make_fourier_volume(shape, blobs=10, radius=5, seed=65)
     hyper = dict(HYPER, mu=0.02)
     anchor = (0.2 * np.random.default_rng(66).standard_normal(shape)).astype(np.float32)
@@ -136,7 +137,7 @@ def test_fourier_anchor_matches_oracle():
     p = oracle.Params(shape, **hyper, gamma=gamma, anchor=anchor.astype(np.float64))
     xr, hr, rr = fourier.solve(fv.y, fv.N, p, 2, 40, with_hist=False)
     err = rel_l2(x, xr)
-    print(f"fourier + anchor: rel-L2 {err:.3e}")
+    print(f"fourier + anchor {shape}: rel-L2 {err:.3e}")
     assert err <= 1e-5
     np.testing.assert_allclose(st[4], rr[1, 4], rtol=1e-6)  # L of round 2 includes 2 gamma
     want = fourier.data_value(x, fv.y, fv.N) + gamma * float(((x - anchor) ** 2).sum())
