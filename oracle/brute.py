@@ -68,6 +68,19 @@ class Problem:
         grad = self.w * r + self.tv * (self.D.T @ (self.omtv[None, :] * hg).ravel())
         return f, grad
 
+    def parts(self, x):
+        """(data, l1, tv) of the round objective (Eq. 11 with the data term of
+        Eq. 28/31 and the smoothed norm of Eq. 14), each with its lambda, each
+        summed on its own: a dot product of the weights with the per-voxel
+        terms, with |Dx| taken from the sparse D above."""
+        x = np.asarray(x, dtype=np.float64).ravel()
+        g3 = (self.D @ x).reshape(3, self.n)
+        hv, _ = huber_vec(g3, self.mu)
+        r = x - self.b
+        return (0.5 * np.dot(self.w, r * r),
+                self.l1 * np.dot(self.om1, np.abs(x)),
+                self.tv * np.dot(self.omtv, hv))
+
     def F(self, x):
         x = np.asarray(x, dtype=np.float64).ravel()
         f, _ = self.smooth(x)

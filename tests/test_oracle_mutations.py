@@ -42,6 +42,11 @@ MUTATIONS = {
     "lambda_tv dropped from grad f": ("out[v] = w[v] * (x[v] - b[v]) + p->lambda_tv * out[v];",
                                       "out[v] = w[v] * (x[v] - b[v]) + out[v];"),
     "data term without the 1/2": ("sd += 0.5 * w[v] * r * r;", "sd += w[v] * r * r;"),
+    "om1 ignored in the objective's l1 sum": ("sl += (om1 ? om1[v] : 1.0) * fabs(x[v]);",
+                                              "sl += fabs(x[v]);"),
+    "omtv ignored in the objective's TV sum": ("st += (omtv ? omtv[v] : 1.0) * orc_huber(",
+                                               "st += 1.0 * orc_huber("),
+    "lambda_l1 dropped from the objective": ("out[1] = p->lambda_l1 * sl;", "out[1] = sl;"),
     "TV weight built from eps instead of eps_tv": ("omtv[v] = p->eps_tv / (gn + p->eps_tv);",
                                                    "omtv[v] = p->eps / (gn + p->eps);"),
     "l1 weight ignored in the prox": ("tau * p->lambda_l1 * (om1 ? om1[v] : 1.0));\n    free(y);",
@@ -73,6 +78,8 @@ QUICK = [
     lambda o: pins.test_adjoint_identity(o, (5, 7, 9)),
     pins.test_constant_has_zero_gradient_and_tv,
     pins.test_tv_of_ramp_and_spike,
+    pins.test_objective_hand_example,
+    lambda o: pins.test_objective_parts_match_sparse_evaluation(o, (4, 5, 6)),
     pins.test_reweight_spike,
     pins.test_lipschitz_bound_holds,
     pins.test_lipschitz_bound_is_valid_and_tight,

@@ -130,6 +130,45 @@ def test_tv_of_ramp_and_spike(orc):
     assert tv == pytest.approx((h * math.sqrt(3) - mu / 2) + 3 * (h - mu / 2), rel=1e-14)
 
 
+def test_objective_hand_example(orc):
+    """Eq. 11 objective (data term of Eq. 28/31, weighted l1, weighted smoothed
+    TV of Eq. 14) with non-uniform om1 and omtv on a 2x1x2 volume worked by
+    hand (tests/golden/objective_2x1x2.txt)."""
+    rows = golden("objective_2x1x2.txt")
+    vox = [r for r in rows if len(r) == 8]
+    (lam1, lamtv, mu, data, l1, tv, total), = [r for r in rows if len(r) == 7]
+    shape = (2, 1, 2)
+    x, b, w, om1, omtv = (np.zeros(shape) for _ in range(5))
+    for z, y, xx, xv, bv, wv, o1, ot in vox:
+        q = (int(z), int(y), int(xx))
+        x[q], b[q], w[q], om1[q], omtv[q] = xv, bv, wv, o1, ot
+    p = P(orc, shape, lambda_l1=lam1, lambda_tv=lamtv, mu=mu)
+    got = orc.objective(x, b, w, om1, omtv, p)
+    np.testing.assert_allclose(got, [data, l1, tv, total], rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("shape", [(4, 5, 6), (7, 3, 2), (1, 9, 4)])
+def test_objective_parts_match_sparse_evaluation(orc, shape):
+    """Each part of the Eq. 11 objective (data, om1-weighted l1, omtv-weighted
+    smoothed TV) against a separate evaluation from the Kronecker-assembled D,
+    on random x straddling mu and random non-uniform weights (as in rounds
+    2 and 3, where Eq. 11's weights come from the previous round's iterate)."""
+    rng = np.random.default_rng(sum(shape))
+    x = rng.standard_normal(shape) * 10 ** rng.uniform(-3.5, 0, shape)
+    b = rng.standard_normal(shape)
+    w = rng.uniform(0.3, 4, shape)
+    om1 = rng.uniform(0.01, 1, shape)
+    omtv = rng.uniform(0.01, 1, shape)
+    p = P(orc, shape, lambda_l1=0.07, lambda_tv=0.13, mu=1e-3)
+    got = orc.objective(x, b, w, om1, omtv, p)
+    want = brute.Problem(b, w, om1, omtv, p.lambda_l1, p.lambda_tv, p.mu).parts(x)
+    np.testing.assert_allclose(got[:3], want, rtol=1e-12, atol=0)
+    assert got[3] == pytest.approx(sum(want), rel=1e-12)
+    # the weights matter: dropping either one changes its part
+    unw = brute.Problem(b, w, None, None, p.lambda_l1, p.lambda_tv, p.mu).parts(x)
+    assert abs(unw[1] - got[1]) > 1e-3 * got[1] and abs(unw[2] - got[2]) > 1e-3 * got[2]
+
+
 def test_reweight_spike(orc):
     """Eq. 11 weights scaled by eps (Sec. 2.5) on a single spike."""
     eps, eps_tv, h = 1e-3, 2e-3, 0.7
