@@ -369,21 +369,29 @@ spg_status spg_plan_info(const spg_ctx *ctx, int info[6]);
  * pool or a fixed arena sized at start-up, and latency-critical paths that
  * must not trigger the device-wide synchronisation cudaMalloc can cause).
  *
- * Computes out = {data, l1, tv, total} of F at x exactly as spg_objective
- * does, from caller-provided device arrays x, b, w, om1, omtv (float32,
- * contiguous [nz][ny][nx], no padding) and the volume's lambda_l1, lambda_tv
- * and mu; out is a device pointer to 4 doubles; stream is a cudaStream_t or
- * NULL. Asynchronous. It calls no cudaMalloc, cudaFree or allocating routine:
- * its scratch (one partial sum per z-plane and a counter) is a static device
- * array of SPG_NOALLOC_MAX_PLANES planes (about 128 KiB) inside this library,
- * which every GPU that loads the library holds until the process exits.
+ * Computes out = {data, l1, tv, total} of F at x, from caller-provided device
+ * arrays x, b, w, om1, omtv (float32, contiguous [nz][ny][nx], no padding)
+ * and the volume's lambda_l1, lambda_tv and mu; out is a device pointer to 4
+ * doubles; stream is a cudaStream_t or NULL. Asynchronous. It covers the
+ * default form only: the adopted readings (backward differences, the Neumann
+ * edge, the TV weight inside the divergence), float32 b and w, and the
+ * real-space data term of Eq. 28; for such a context it agrees with
+ * spg_objective to a relative 1e-6 (same float32 per-voxel terms and
+ * compensated sums, summed in another order).
+ * It calls no cudaMalloc, cudaFree or allocating routine: its scratch (one
+ * partial sum per z-plane and a counter) is a static device array of
+ * SPG_NOALLOC_MAX_PLANES planes (about 128 KiB) inside this library, which
+ * every GPU that loads the library holds until the process exits.
  * nz > SPG_NOALLOC_MAX_PLANES is rejected with SPG_EINVAL.
- * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * The first call in each CUDA context (a device's primary context, or a
+ * context the caller created with the driver API and made current) looks up
+ * the array's device address in that context; make that first call before
+ * any stream capture.
  * Every call shares the array, which keeps the previous call's contents (the
  * counter is cleared at the start of each call): calls that overlap on the
  * GPU, from other streams or threads, race and must be serialised by the
- * caller. Errors: SPG_EINVAL, SPG_ECUDA; message in spg_noalloc_last_error(). */
+ * caller. Errors: SPG_EINVAL, SPG_ECUDA; message in spg_noalloc_last_error()
+ * ("no error" after a successful call on the calling thread). */
 #define SPG_NOALLOC_MAX_PLANES 4096
 spg_status spg_objective_noalloc(int nx, int ny, int nz, float lambda_l1, float lambda_tv, float mu,
                                  const float *x, const float *b, const float *w, const float *om1,

@@ -5,6 +5,7 @@
 // this library keeps until the process exits.
 #include <cuda_runtime.h>
 
+#include <cstdio>
 #include <mutex>
 
 #include "spg.h"
@@ -90,72 +91,142 @@ __global__ void objective_noalloc_kernel(int nx, int ny, int nz, float lambda_l1
     *counter = 0u;
 }
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double *g_scratch_ptr[kMaxDevices] = {nullptr};
+// The scratch array's device address belongs to one CUDA context: the primary
+// context of a device, or a context the caller created with the driver API
+// and made current. It is looked up once per context and cached under the
+// context's ID, which the driver never reuses within a process, so a context
+// created after another was destroyed (or after cudaDeviceReset) gets a fresh
+// lookup.
+typedef int (*PfnCtxGetCurrent)(void **ctx);
+typedef int (*PfnCtxGetId)(void *ctx, unsigned long long *id);
 
-// Device address of the scratch array for the current device (set up once per
-// device, with that device current).
-cudaError_t scratch_for_current_device(double **ptr, int *dev_out)
+struct DriverFns {
+    PfnCtxGetCurrent get_current = nullptr;
+    PfnCtxGetId get_id = nullptr;
+};
+
+const DriverFns &driver_fns()
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    static DriverFns f = [] {
+        DriverFns d;
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<double *>(p);
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            d.get_current = reinterpret_cast<PfnCtxGetCurrent>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            d.get_id = reinterpret_cast<PfnCtxGetId>(p);
+        return d;
+    }();
+    return f;
+}
+
+constexpr int kMaxContexts = 64;
+std::mutex g_mu;
+struct CacheEntry {
+    unsigned long long ctx_id;
+    double *ptr;
+};
+CacheEntry g_cache[kMaxContexts];
+int g_cache_n = 0;
+
+// Device address of the scratch array in the calling thread's current context
+// (the current device's primary context unless the caller made another one
+// current). `msg` names the step that failed.
+cudaError_t scratch_for_current_context(double **ptr, const char **msg)
+{
+    const DriverFns &f = driver_fns();
+    if (!f.get_current || !f.get_id) {
+        *msg = "driver entry points cuCtxGetCurrent/cuCtxGetId unavailable";
+        return cudaErrorNotSupported;
     }
-    *ptr = g_scratch_ptr[dev];
-    *dev_out = dev;
+    void *ctx = nullptr;
+    if (f.get_current(&ctx) != 0) {
+        *msg = "cuCtxGetCurrent failed";
+        return cudaErrorDeviceUninitialized;
+    }
+    if (!ctx) {
+        // no context yet on this thread: bind the current device's primary one
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaSetDevice(dev);
+        if (e != cudaSuccess) {
+            *msg = "no usable CUDA device";
+            return e;
+        }
+        if (f.get_current(&ctx) != 0 || !ctx) {
+            *msg = "no current CUDA context";
+            return cudaErrorDeviceUninitialized;
+        }
+    }
+    unsigned long long id = 0;
+    if (f.get_id(ctx, &id) != 0) {
+        *msg = "cuCtxGetId failed";
+        return cudaErrorDeviceUninitialized;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int i = 0; i < g_cache_n; i++)
+        if (g_cache[i].ctx_id == id) {
+            *ptr = g_cache[i].ptr;
+            return cudaSuccess;
+        }
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        *msg = "cudaGetSymbolAddress of the scratch array failed";
+        return e;
+    }
+    // a full table drops its oldest entry (contexts that old are rarely alive)
+    if (g_cache_n == kMaxContexts) {
+        for (int i = 1; i < kMaxContexts; i++) g_cache[i - 1] = g_cache[i];
+        g_cache_n--;
+    }
+    g_cache[g_cache_n++] = CacheEntry{id, static_cast<double *>(p)};
+    *ptr = static_cast<double *>(p);
     return cudaSuccess;
 }
 
-thread_local const char *g_noalloc_err = "no error";
+thread_local char g_noalloc_msg[256] = "no error";
+
+spg_status noalloc_fail(spg_status st, const char *what, cudaError_t e)
+{
+    if (e != cudaSuccess)
+        snprintf(g_noalloc_msg, sizeof(g_noalloc_msg), "spg_objective_noalloc: %s (%s)", what, cudaGetErrorString(e));
+    else
+        snprintf(g_noalloc_msg, sizeof(g_noalloc_msg), "spg_objective_noalloc: %s", what);
+    return st;
+}
 
 }  // namespace
 
-extern "C" const char *spg_noalloc_last_error(void) { return g_noalloc_err; }
+extern "C" const char *spg_noalloc_last_error(void) { return g_noalloc_msg; }
 
 extern "C" spg_status spg_objective_noalloc(int nx, int ny, int nz, float lambda_l1, float lambda_tv, float mu,
                                             const float *x, const float *b, const float *w, const float *om1,
                                             const float *omtv, double *out, void *stream)
 {
     SPG_TRACE();
-    if (nx <= 0 || ny <= 0 || nz <= 0 || !x || !b || !w || !om1 || !omtv || !out || !(mu > 0.f)) {
-        g_noalloc_err = "spg_objective_noalloc: bad arguments";
-        return SPG_EINVAL;
-    }
-    if (nz > kMaxPlanes) {
-        g_noalloc_err = "spg_objective_noalloc: nz exceeds SPG_NOALLOC_MAX_PLANES (4096)";
-        return SPG_EINVAL;
-    }
-    if ((long long)nx * ny > (1LL << 30)) {
-        g_noalloc_err = "spg_objective_noalloc: plane too large";
-        return SPG_EINVAL;
-    }
+    if (nx <= 0 || ny <= 0 || nz <= 0 || !x || !b || !w || !om1 || !omtv || !out || !(mu > 0.f))
+        return noalloc_fail(SPG_EINVAL, "bad arguments", cudaSuccess);
+    if (nz > kMaxPlanes)
+        return noalloc_fail(SPG_EINVAL, "nz exceeds SPG_NOALLOC_MAX_PLANES (4096)", cudaSuccess);
+    if ((long long)nx * ny > (1LL << 30)) return noalloc_fail(SPG_EINVAL, "plane too large", cudaSuccess);
     double *scratch = nullptr;
-    int dev = 0;
-    cudaError_t e = scratch_for_current_device(&scratch, &dev);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        g_noalloc_err = "spg_objective_noalloc: scratch set-up failed (no usable CUDA device?)";
-        return SPG_ECUDA;
-    }
+    const char *what = "scratch set-up failed";
+    cudaError_t e = scratch_for_current_context(&scratch, &what);
+    if (e != cudaSuccess) return noalloc_fail(SPG_ECUDA, what, e);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the arrival counter must start at zero on every call
     e = cudaMemsetAsync(scratch + 4 * kMaxPlanes, 0, sizeof(unsigned int), s);
-    if (e == cudaSuccess) {
-        objective_noalloc_kernel<<<nz, kThreads, 0, s>>>(nx, ny, nz, lambda_l1, lambda_tv, mu, x, b, w, om1, omtv,
-                                                         out, scratch);
-        e = cudaGetLastError();
-    }
-    if (e != cudaSuccess) {
-        g_noalloc_err = "spg_objective_noalloc: launch failed";
-        return SPG_ECUDA;
-    }
+    if (e != cudaSuccess) return noalloc_fail(SPG_ECUDA, "clearing the scratch counter failed", e);
+    // cudaLaunchKernel reports this launch's own error (no stale error of
+    // earlier, unrelated work is picked up from the runtime's last-error slot)
+    void *args[] = {&nx, &ny, &nz, &lambda_l1, &lambda_tv, &mu, &x, &b, &w, &om1, &omtv, &out, &scratch};
+    e = cudaLaunchKernel(reinterpret_cast<const void *>(objective_noalloc_kernel), dim3(nz), dim3(kThreads), args,
+                         0, s);
+    if (e != cudaSuccess) return noalloc_fail(SPG_ECUDA, "kernel launch failed", e);
+    snprintf(g_noalloc_msg, sizeof(g_noalloc_msg), "no error");
     return SPG_OK;
 }

@@ -38,6 +38,31 @@ def test_byte_model_and_rates():
     assert bench.bytes_per_voxel("f32", "prev") == 28   # x_k, x_{k-1}, b, w, om1, omtv read; x written
     assert bench.bytes_per_voxel("bf16", "delta") == 28
     assert bench.bytes_per_voxel("bf16", "prev") == 24
+    # the method's own bytes (x_k, x_{k-1}, b, w, om1, omtv read once, x_{k+1}
+    # written once): what the roofline fraction counts, whatever the storage
+    assert bench.method_bytes_per_voxel("f32") == 28
+    assert bench.method_bytes_per_voxel("bf16") == 24
     # 2 ranks x 1e9 voxel-iterations in 500 ms of the slowest rank: 4 Gvoxel-iter/s for the job
     assert abs(bench.whole_job_rate(1e8, 10, 2, 500.0) - 4.0) < 1e-12
     assert bench.max_over_ranks(12.5, 1) == 12.5
+
+
+def test_roofline_counts_the_method_bytes():
+    """frac = method bytes / launch time / peak; the increment write of the
+    increment storage form is reported beside it, not inside it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    nvox = 512 ** 3
+    r = bench.roofline_block("f32", "delta", nvox, 0.6508e-3, 6689.5, "measured", traffic=4.313e9)
+    assert r["algorithmic_bytes_per_launch"] == 28 * nvox
+    assert r["storage_overhead_bytes_per_launch"] == 4 * nvox
+    assert r["moved_bytes_per_launch"] == 32 * nvox
+    assert abs(r["achieved"] - 28 * nvox / 0.6508e-3 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / 6689.5) < 1e-12
+    assert abs(r["frac"] - 0.863) < 0.001          # 206.2 Gvoxel-iter/s on 28 B
+    assert abs(r["moved_frac"] - 0.986) < 0.001    # the same launch on the 32 B it moves
+    assert abs(r["traffic_over_algorithmic"] - 4.313e9 / (28 * nvox)) < 1e-12
+    assert abs(r["frac_nominal"] - r["achieved"] / bench.NOMINAL_HBM_GBS) < 1e-12
+    r = bench.roofline_block("bf16", "prev", nvox, 1e-3, 6791.0, "measured")
+    assert r["algorithmic_bytes_per_launch"] == r["moved_bytes_per_launch"] == 24 * nvox
+    assert r["storage_overhead_bytes_per_launch"] == 0 and r["traffic"] is None
