@@ -317,7 +317,11 @@ def test_certificate_matches_oracle(shape, storage):
     beta = float(np.float32(oracle.beta_table(31)[30]))
     y = xk + beta * (xk - xkm1)
     want = oracle.certificate(y, x1, tau, vol.b, vol.w, omtv, oparams(shape))
-    np.testing.assert_allclose(cert, want, rtol=1e-3)
+    print(f"certificate {shape} {storage}: {cert:.9e} vs oracle {want:.9e}, rel {abs(cert / want - 1):.2e}")
+    # both sides take the same stored float32 iterates; the GPU forms y - x+ as
+    # (x_k - x+) + beta d (no cancellation against a rounded y) and sums r^2
+    # compensated: measured within 7.4e-8 of the oracle
+    np.testing.assert_allclose(cert, want, rtol=1e-6)
 
 
 def test_batch_equals_single_volumes():
@@ -336,9 +340,16 @@ def test_batch_equals_single_volumes():
     for i, (sh, v, h) in enumerate(zip(shapes, vols, hypers)):
         x1, h1, _, _ = gpu_solve(v.b, v.w, h, 2, 25)
         ref = oracle.solve(v.b, v.w, oparams(sh, h), 2, 25)
+        print(f"batch vs single {sh}: x rel-L2 {rel_l2(xb[i], x1):.2e} (max abs {np.abs(xb[i] - x1).max():.2e}), "
+              f"objective max rel {np.abs(hb[i][:, 4] / h1[:, 4] - 1).max():.2e}")
         assert rel_l2(xb[i], ref.x) <= 1e-6
-        assert rel_l2(xb[i], x1) <= 1e-6
-        np.testing.assert_allclose(hb[i][:, 4], h1[:, 4], rtol=1e-7)
+        # the per-voxel arithmetic is the same, so the iterates are bitwise
+        # equal; the objective sums differ only in grouping (the batch plan
+        # cuts each volume into other z-chunks than a single-volume plan, so
+        # each thread's compensated float32 sums cover other voxels):
+        # measured within 1.2e-9
+        np.testing.assert_array_equal(xb[i], x1)
+        np.testing.assert_allclose(hb[i][:, 4], h1[:, 4], rtol=1e-8)
 
 
 def test_bf16_storage():
@@ -504,19 +515,40 @@ def test_adjoint_differentiation_workload():
     np.testing.assert_allclose(gs, rs, rtol=1e-4)
 
 
-def test_autograd_function():
+@pytest.mark.parametrize("K,ckpt", [(8, 10), (23, 5)])
+def test_autograd_function(K, ckpt):
+    """UnrolledSPG (torch.autograd.Function over spg_unrolled/spg_backward):
+    x_K against the oracle's K steps, and the gradients of
+    L = |x_K - phantom|^2 w.r.t. b, w, lambda_l1 and lambda_tv, as autograd
+    delivers them, against the oracle's FP64 adjoint (rel-L2 <= 1e-4, the
+    scalars each to rel 1e-4)."""
     shape = (10, 12, 16)
     vol = synth.make_volume(shape, blobs=5, radius=3, seed=80)
+    hyper = dict(HYPER, mu=0.02)
     b = torch.from_numpy(vol.b).cuda().requires_grad_(True)
     w = torch.from_numpy(vol.w).cuda().requires_grad_(True)
-    l1 = torch.tensor(0.05, requires_grad=True)
-    tv = torch.tensor(0.1, requires_grad=True)
-    x = spg.UnrolledSPG.apply(b, w, l1, tv, 8, mu=0.02)
+    l1 = torch.tensor(hyper["lambda_l1"], dtype=torch.float64, requires_grad=True)
+    tv = torch.tensor(hyper["lambda_tv"], dtype=torch.float64, requires_grad=True)
+    x = spg.UnrolledSPG.apply(b, w, l1, tv, K, mu=hyper["mu"], ckpt_every=ckpt)
     loss = ((x - torch.from_numpy(vol.phantom).cuda()) ** 2).sum()
     loss.backward()
-    assert b.grad is not None and w.grad is not None
-    assert torch.isfinite(b.grad).all() and torch.isfinite(w.grad).all()
-    assert l1.grad is not None and tv.grad is not None
+    p = oparams(shape, hyper)
+    tau = 1.0 / oracle.lipschitz(vol.w, 1.0, p)
+    x0 = np.zeros(shape)
+    ref_xK = oracle.unrolled(vol.b, vol.w, None, None, tau, K, x0, p)
+    assert rel_l2(x.detach().cpu().numpy(), ref_xK) <= 1e-6
+    rb, rw, rs = oracle.backward(vol.b, vol.w, None, None, tau, K, x0, 2 * (ref_xK - vol.phantom), p)
+    assert rel_l2(b.grad.cpu().numpy(), rb) <= 1e-4
+    assert rel_l2(w.grad.cpu().numpy(), rw) <= 1e-4
+    assert float(l1.grad) == pytest.approx(rs[0], rel=1e-4)
+    assert float(tv.grad) == pytest.approx(rs[1], rel=1e-4)
+    # the loss scaled by -3 scales every gradient by -3 (the cotangent reaches
+    # the adjoint as given, not only its sign or norm)
+    b2 = torch.from_numpy(vol.b).cuda().requires_grad_(True)
+    w2 = torch.from_numpy(vol.w).cuda().requires_grad_(True)
+    x2 = spg.UnrolledSPG.apply(b2, w2, hyper["lambda_l1"], hyper["lambda_tv"], K, mu=hyper["mu"], ckpt_every=ckpt)
+    (-3 * ((x2 - torch.from_numpy(vol.phantom).cuda()) ** 2).sum()).backward()
+    assert rel_l2(b2.grad.cpu().numpy(), -3 * rb) <= 1e-4
 
 
 def test_autotune_keeps_the_solve():
