@@ -136,6 +136,180 @@ struct KSum {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// Packed float32 pairs (sm_100 and later issue one instruction for two
+// lanes' worth of add, multiply or fused multiply-add). Each lane rounds to
+// nearest exactly as the scalar operation does, so the results are bitwise
+// those of the scalar code; only the issue slots are halved.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b rounded once: the product b * (-1) is exact
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// Two compensated (Kahan) float32 accumulators advanced together.
+struct KSum2 {
+    float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add(float2 v)
+    {
+        const float2 y = sub2(v, c);
+        const float2 t = add2(s, y);
+        c = sub2(sub2(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value_x() const { return (double)s.x - (double)c.x; }
+    __device__ __forceinline__ double value_y() const { return (double)s.y - (double)c.y; }
+};
+
+// Phase A of one z-step at a thread's VX voxels of plane z: the weighted
+// clipped gradient p = omtv (Dy) / max(mu, |Dy|) (Eq. 12, 16) and, with REC,
+// the weighted smoothed norm omtv h_mu(D x_k) (Eq. 14) summed into *tsum.
+// xl, ld: x_k and d at the voxel left of the first one; xu, du: the row
+// above; xz, dz: the plane below. Pairs of voxels go through the packed
+// operations; the differences along x (operands one register apart) stay
+// scalar.
+template <int VX, bool REC>
+__device__ __forceinline__ void phase_a(const float (&xc)[VX], const float (&dc)[VX], const float (&xu)[VX],
+                                        const float (&du)[VX], const float (&xz)[VX], const float (&dz)[VX],
+                                        const float (&om)[VX], float xl, float ld, float beta, float inv_mu,
+                                        float half_inv_mu, float half_mu, float mu2, float (&pc)[3][VX],
+                                        float *tsum)
+{
+    if constexpr (VX % 2 == 0) {
+        float ex[VX], exd[VX];
+#pragma unroll
+        for (int i = 0; i < VX; i++) {
+            ex[i] = xc[i] - (i ? xc[i - 1] : xl);
+            exd[i] = dc[i] - (i ? dc[i - 1] : ld);
+        }
+        const float2 B = dup2(beta);
+        float2 ts = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < VX / 2; q++) {
+            const int i = 2 * q;
+            const float2 X = make_float2(xc[i], xc[i + 1]), D = make_float2(dc[i], dc[i + 1]);
+            const float2 EX = make_float2(ex[i], ex[i + 1]);
+            const float2 EY = sub2(X, make_float2(xu[i], xu[i + 1]));
+            const float2 EZ = sub2(X, make_float2(xz[i], xz[i + 1]));
+            const float2 AX = fma2(B, make_float2(exd[i], exd[i + 1]), EX);
+            const float2 AY = fma2(B, sub2(D, make_float2(du[i], du[i + 1])), EY);
+            const float2 AZ = fma2(B, sub2(D, make_float2(dz[i], dz[i + 1])), EZ);
+            const float2 S2 = fma2(AX, AX, fma2(AY, AY, mul2(AZ, AZ)));
+            const float2 SC = mul2(make_float2(om[i], om[i + 1]),
+                                   make_float2(fminf(inv_mu, rsqrtf(S2.x)), fminf(inv_mu, rsqrtf(S2.y))));
+            const float2 P0 = mul2(AX, SC), P1 = mul2(AY, SC), P2 = mul2(AZ, SC);
+            pc[0][i] = P0.x; pc[0][i + 1] = P0.y;
+            pc[1][i] = P1.x; pc[1][i + 1] = P1.y;
+            pc[2][i] = P2.x; pc[2][i + 1] = P2.y;
+            if constexpr (REC) {
+                const float2 Q = fma2(EX, EX, fma2(EY, EY, mul2(EZ, EZ)));
+                const float2 HQ = mul2(Q, dup2(half_inv_mu));
+                const float2 HL = fma2(Q, make_float2(rsqrtf(Q.x), rsqrtf(Q.y)), dup2(-half_mu));
+                const float2 H = make_float2(Q.x <= mu2 ? HQ.x : HL.x, Q.y <= mu2 ? HQ.y : HL.y);
+                ts = fma2(make_float2(om[i], om[i + 1]), H, ts);
+            }
+        }
+        if constexpr (REC) *tsum = ts.x + ts.y;
+    } else {
+        float t = 0.f;
+#pragma unroll
+        for (int i = 0; i < VX; i++) {
+            const float lx = i ? xc[i - 1] : xl;
+            const float l_d = i ? dc[i - 1] : ld;
+            const float ex = xc[i] - lx, ey = xc[i] - xu[i], ez = xc[i] - xz[i];
+            const float ax = fmaf(beta, dc[i] - l_d, ex);
+            const float ay = fmaf(beta, dc[i] - du[i], ey);
+            const float az = fmaf(beta, dc[i] - dz[i], ez);
+            const float s2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
+            const float sc = om[i] * fminf(inv_mu, rsqrtf(s2));
+            pc[0][i] = ax * sc;
+            pc[1][i] = ay * sc;
+            pc[2][i] = az * sc;
+            if constexpr (REC) {
+                const float q = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                const float h = q <= mu2 ? q * half_inv_mu : fmaf(q, rsqrtf(q), -half_mu);
+                t = fmaf(om[i], h, t);
+            }
+        }
+        if constexpr (REC) *tsum = t;
+    }
+}
+
+// Phase B at a thread's VX voxels of plane z-1: divergence (Eq. 17), data
+// gradient, gradient step and weighted soft-threshold (Eq. 20-21). Writes the
+// new iterate `out` and the increment `inc`; with REC adds the data and l1
+// terms of F(x_k) into dl (x: data, y: l1), with DOT the restart product
+// (y - x+).(x+ - x) into *rsum. pxr: p_x of the voxel right of the last one.
+template <int VX, bool REC, bool DOT, bool FOURIER>
+__device__ __forceinline__ void phase_b(const float (&pp)[3][VX], float pxn, const float (&pyd)[VX],
+                                        const float (&pz)[VX], const float (&xz)[VX], const float (&dz)[VX],
+                                        const float (&bb)[VX], const float (&ww)[VX], const float (&oo)[VX],
+                                        float beta, float tau, float lam_tv, float tl1, float (&out)[VX],
+                                        float (&inc)[VX], float2 *dl, float *rsum)
+{
+    if constexpr (VX % 2 == 0) {
+        float dxx[VX];
+#pragma unroll
+        for (int i = 0; i < VX; i++) dxx[i] = pp[0][i] - (i < VX - 1 ? pp[0][i + 1] : pxn);
+        const float2 B = dup2(beta), NT = dup2(-tau), LT = dup2(lam_tv), TL = dup2(tl1);
+        float2 d2 = make_float2(0.f, 0.f), l2 = make_float2(0.f, 0.f);
+        float r = 0.f;
+#pragma unroll
+        for (int q = 0; q < VX / 2; q++) {
+            const int i = 2 * q;
+            const float2 XZ = make_float2(xz[i], xz[i + 1]), DZ = make_float2(dz[i], dz[i + 1]);
+            const float2 DIV = add2(add2(make_float2(dxx[i], dxx[i + 1]),
+                                         sub2(make_float2(pp[1][i], pp[1][i + 1]), make_float2(pyd[i], pyd[i + 1]))),
+                                    sub2(make_float2(pp[2][i], pp[2][i + 1]), make_float2(pz[i], pz[i + 1])));
+            const float2 BB = make_float2(bb[i], bb[i + 1]);
+            const float2 RES = sub2(XZ, BB);
+            const float2 GD = FOURIER ? BB : mul2(make_float2(ww[i], ww[i + 1]), fma2(B, DZ, RES));
+            const float2 G = fma2(LT, DIV, GD);
+            const float2 DL = fma2(B, DZ, mul2(NT, G));
+            const float2 ZZ = add2(XZ, DL);
+            const float2 T = mul2(TL, make_float2(oo[i], oo[i + 1]));
+            const float2 CS = make_float2(copysignf(T.x, ZZ.x), copysignf(T.y, ZZ.y));
+            const float2 IN0 = sub2(DL, CS);
+            const float2 IN = make_float2(fabsf(ZZ.x) < T.x ? -XZ.x : IN0.x, fabsf(ZZ.y) < T.y ? -XZ.y : IN0.y);
+            const float2 OUT = add2(XZ, IN);
+            out[i] = OUT.x; out[i + 1] = OUT.y;
+            inc[i] = IN.x; inc[i + 1] = IN.y;
+            if constexpr (DOT) {
+                r = fmaf(fmaf(beta, DZ.x, -IN.x), IN.x, r);
+                r = fmaf(fmaf(beta, DZ.y, -IN.y), IN.y, r);
+            }
+            if constexpr (REC) {
+                if constexpr (!FOURIER) d2 = fma2(mul2(make_float2(ww[i], ww[i + 1]), RES), RES, d2);
+                l2 = fma2(make_float2(oo[i], oo[i + 1]), make_float2(fabsf(XZ.x), fabsf(XZ.y)), l2);
+            }
+        }
+        if constexpr (REC) *dl = make_float2(d2.x + d2.y, l2.x + l2.y);
+        if constexpr (DOT) *rsum = r;
+    } else {
+        float dsum = 0.f, lsum = 0.f, r = 0.f;
+#pragma unroll
+        for (int i = 0; i < VX; i++) {
+            const float pxr = (i < VX - 1) ? pp[0][i + 1] : pxn;
+            const float div = (pp[0][i] - pxr) + (pp[1][i] - pyd[i]) + (pp[2][i] - pz[i]);
+            const float res = xz[i] - bb[i];
+            const float gdat = FOURIER ? bb[i] : ww[i] * fmaf(beta, dz[i], res);
+            const float g = fmaf(lam_tv, div, gdat);
+            const float delta = fmaf(beta, dz[i], -tau * g);
+            const float zz = xz[i] + delta;
+            const float t = tl1 * oo[i];
+            inc[i] = fabsf(zz) < t ? -xz[i] : delta - copysignf(t, zz);
+            out[i] = xz[i] + inc[i];
+            if constexpr (DOT) r = fmaf(fmaf(beta, dz[i], -inc[i]), inc[i], r);
+            if constexpr (REC) {
+                if constexpr (!FOURIER) dsum = fmaf(ww[i] * res, res, dsum);
+                lsum = fmaf(oo[i], fabsf(xz[i]), lsum);
+            }
+        }
+        if constexpr (REC) *dl = make_float2(dsum, lsum);
+        if constexpr (DOT) *rsum = r;
+    }
+}
+
 template <int VX>
 __device__ __forceinline__ void ld_vec(const float *p, float (&v)[VX])
 {
@@ -221,9 +395,9 @@ struct Cfg {
 // what they do not consume.
 template <class C, int S, bool LOADW>
 __device__ __forceinline__ void issue_stage(unsigned char *sm, uint64_t *bars, const TmapSet *tm,
-                                            const WorkItem &W, int ia, int ib, long long gstep, int j)
+                                            const WorkItem &W, int ia, int ib, unsigned gstep, int j)
 {
-    const int s = (int)((gstep + j) % S);
+    const int s = (int)((gstep + (unsigned)j) % S);
     unsigned char *base = sm + s * C::STAGE;
     const int z = W.z0 - 1 + j;
     const bool need_om = j >= 1, need_bwo = j >= 2;
@@ -258,9 +432,9 @@ struct Smem {
 
 // Pipeline bookkeeping of one CTA (owned by thread 0 where noted).
 struct Pipe {
-    long long gstep;        // steps consumed so far
-    long long issued_upto;  // steps issued so far (thread 0)
-    long long drain_from;   // first step that may be pending after an abort
+    unsigned gstep;         // steps consumed so far
+    unsigned issued_upto;   // steps issued so far (thread 0)
+    unsigned drain_from;    // first step that may be pending after an abort
 };
 
 // One work item: plane-by-plane march over [z0, z1) of one x-y tile.
@@ -284,7 +458,7 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
     const float tau = V.tau, lam_tv = V.lambda_tv, tl1 = V.tau * V.lambda_l1;
     const float inv_mu = 1.0f / V.mu, half_inv_mu = 0.5f / V.mu, half_mu = 0.5f * V.mu;
     const float mu2 = V.mu * V.mu;
-    const long long g0 = pp_.gstep;
+    const unsigned g0 = pp_.gstep;
 
     // the TMA producer is lane 0 of the halo warp, which has no write phase
     const bool producer = (warp == TY) && (lane == 0);
@@ -304,7 +478,8 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
         dz[i] = 0.f;
         pp[0][i] = pp[1][i] = pp[2][i] = 0.f;
     }
-    KSum kd, kl, kt, kr;  // objective sums and (DOT) the restart test <y - x+, x+ - x>
+    KSum2 kdl;            // objective sums: data (x) and l1 (y)
+    KSum kt, kr;          // TV sum and (DOT) the restart test <y - x+, x+ - x>
 
     const int gy = W.y0 + r;
     const int gx0 = W.x0 + VX * lane;
@@ -316,6 +491,10 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
     // The zero differences on the first column, row and plane (Eq. 12) are
     // made by substituting the voxel itself for its missing neighbour.
     bool aborted = false;
+    // output offset of plane z-1 = W.z0 - 2 + j, advanced by one plane per step
+    const long long plane_elems = (long long)V.ny * V.pitch;
+    long long o = V.off + ((long long)(W.z0 - 2) * V.ny + gy) * V.pitch + gx0;
+    int slot = 0, slot_prev = 2;  // j % 3 and (j - 1) % 3 (p_y and p_x halo rings)
 #pragma unroll 2
     for (int j = 0; j < nsteps; j++) {
         const int s = (int)((g0 + j) % S);
@@ -364,25 +543,11 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
                 }
             }
             float tsum = 0.f;
+            float dup_[VX];
 #pragma unroll
-            for (int i = 0; i < VX; i++) {
-                const float lx = i ? xc[i - 1] : xl;
-                const float ld = i ? dc[i - 1] : (XD ? ml : xl - ml);
-                const float ex = xc[i] - lx, ey = xc[i] - xu[i], ez = xc[i] - xz[i];
-                const float ax = fmaf(beta, dc[i] - ld, ex);
-                const float ay = fmaf(beta, dc[i] - (XD ? mu_[i] : xu[i] - mu_[i]), ey);
-                const float az = fmaf(beta, dc[i] - dz[i], ez);
-                const float s2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
-                const float sc = om[i] * fminf(inv_mu, rsqrtf(s2));
-                pc[0][i] = ax * sc;
-                pc[1][i] = ay * sc;
-                pc[2][i] = az * sc;
-                if constexpr (REC) {
-                    const float q = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                    const float h = q <= mu2 ? q * half_inv_mu : q * rsqrtf(q) - half_mu;
-                    tsum = fmaf(om[i], h, tsum);
-                }
-            }
+            for (int i = 0; i < VX; i++) dup_[i] = XD ? mu_[i] : xu[i] - mu_[i];
+            phase_a<VX, REC>(xc, dc, xu, dup_, xz, dz, om, xl, XD ? ml : xl - ml, beta, inv_mu, half_inv_mu,
+                             half_mu, mu2, pc, &tsum);
             if constexpr (REC) {
                 if (main_warp && z < W.z1) kt.add(tsum);
             }
@@ -400,10 +565,10 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
                 const float s2 = ax * ax + ay * ay + az * az;
                 const bool in = hx < V.nx && hy < V.ny && z < V.nz;
                 const float sc = in ? OM[lane * OW + TX] * fminf(inv_mu, rsqrtf(s2)) : 0.f;
-                sh.hx_ring[(j % 3) * 32 + lane] = ax * sc;
+                sh.hx_ring[slot * 32 + lane] = ax * sc;
             }
-            if (SPG_GUARD(P.st, r <= TY && ((j % 3) * (TY + 1) + r) * TX + VX * (lane + 1) <= 3 * (TY + 1) * TX, 6u))
-                st_vec<VX>(sh.py_ring + ((j % 3) * (TY + 1) + r) * TX + VX * lane, pc[1]);
+            if (SPG_GUARD(P.st, r <= TY && slot == j % 3 && (slot * (TY + 1) + r) * TX + VX * (lane + 1) <= 3 * (TY + 1) * TX, 6u))
+                st_vec<VX>(sh.py_ring + (slot * (TY + 1) + r) * TX + VX * lane, pc[1]);
         } else {
 #pragma unroll
             for (int i = 0; i < VX; i++) pc[0][i] = pc[1][i] = pc[2][i] = 0.f;
@@ -434,40 +599,20 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
                 ld_data<VX, BF16>(base + C::OFF_B, r * TX + VX * lane, bb);
                 if constexpr (!FOURIER) ld_data<VX, BF16>(base + C::OFF_W, r * TX + VX * lane, ww);
                 ld_vec<VX>(reinterpret_cast<const float *>(base + C::OFF_O1) + r * TX + VX * lane, oo);
-                ld_vec<VX>(sh.py_ring + (((j - 1) % 3) * (TY + 1) + r + 1) * TX + VX * lane, pyd);
+                ld_vec<VX>(sh.py_ring + ((slot_prev * (TY + 1)) + r + 1) * TX + VX * lane, pyd);
             }
             float pxn = __shfl_down_sync(FULL, pp[0][0], 1);
-            if (lane == 31) pxn = sh.hx_ring[((j - 1) % 3) * 32 + r];
+            if (lane == 31) pxn = sh.hx_ring[slot_prev * 32 + r];
             float out[VX], inc[VX];
-            float dsum = 0.f, lsum = 0.f, rsum = 0.f;
-#pragma unroll
-            for (int i = 0; i < VX; i++) {
-                const float pxr = (i < VX - 1) ? pp[0][(i + 1) % VX] : pxn;
-                const float div = (pp[0][i] - pxr) + (pp[1][i] - pyd[i]) + (pp[2][i] - pc[2][i]);
-                const float res = xz[i] - bb[i];
-                // data gradient: w (y - b) (Eq. 28 form) or, for the Fourier-domain term of
-                // Eq. 31, A^H (N A y - D y) formed by the transforms in the b tile (no w tile)
-                const float gdat = FOURIER ? bb[i] : ww[i] * fmaf(beta, dz[i], res);
-                const float g = fmaf(lam_tv, div, gdat);
-                const float delta = fmaf(beta, dz[i], -tau * g);
-                const float zz = xz[i] + delta;
-                const float t = tl1 * oo[i];
-                inc[i] = fabsf(zz) < t ? -xz[i] : delta - copysignf(t, zz);
-                out[i] = xz[i] + inc[i];
-                if constexpr (DOT) rsum = fmaf(fmaf(beta, dz[i], -inc[i]), inc[i], rsum);  // (y - x+).(x+ - x)
-                if constexpr (REC) {
-                    if constexpr (!FOURIER) dsum = fmaf(ww[i] * res, res, dsum);  // halved once per item
-                    lsum = fmaf(oo[i], fabsf(xz[i]), lsum);
-                }
-            }
-            if constexpr (REC) {
-                kd.add(dsum);
-                kl.add(lsum);
-            }
+            float2 dl = make_float2(0.f, 0.f);
+            float rsum = 0.f;
+            phase_b<VX, REC, DOT, FOURIER>(pp, pxn, pyd, pc[2], xz, dz, bb, ww, oo, beta, tau, lam_tv, tl1, out, inc,
+                                           &dl, &rsum);
+            if constexpr (REC) kdl.add(dl);
             if constexpr (DOT) kr.add(rsum);
-            const long long o = V.off + ((long long)zo * V.ny + gy) * V.pitch + gx0;
             if (gy_in && gx0 < V.pitch &&
-                SPG_GUARD(P.st, zo >= 0 && zo < V.nz && gx0 + VX <= V.pitch, 8u)) {
+                SPG_GUARD(P.st, zo >= 0 && zo < V.nz && gx0 + VX <= V.pitch &&
+                          o == V.off + ((long long)zo * V.ny + gy) * V.pitch + gx0, 8u)) {
                 st_vec<VX>(xout_base + o, out);
                 if constexpr (XD) st_vec<VX>(dout_base + o, inc);
                 if constexpr (FOURIER) {
@@ -489,11 +634,14 @@ __device__ __forceinline__ bool run_item(const StepParams &P, const Smem &sh, Pi
             pp[1][i] = pc[1][i];
             pp[2][i] = pc[2][i];
         }
+        o += plane_elems;
+        slot_prev = slot;
+        slot = slot == 2 ? 0 : slot + 1;
     }
 
     if (!aborted && (REC || DOT)) {
         // block reduction of the item's sums, fixed order
-        double v[4] = {0.5 * kd.value(), kl.value(), kt.value(), kr.value()};
+        double v[4] = {0.5 * kdl.value_x(), kdl.value_y(), kt.value(), kr.value()};
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -521,7 +669,9 @@ __global__ void __launch_bounds__(32 * (TY + 1), MINB)
     using C = Cfg<VX, TY, S, BF16>;
     extern __shared__ unsigned char smem_raw[];
     Smem sh;
-    sh.sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    // 128-byte aligned start, kept as an offset into the shared array so the
+    // compiler addresses every tile as shared memory
+    sh.sm = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     sh.bars = reinterpret_cast<uint64_t *>(sh.sm + C::OFF_BAR);
     sh.py_ring = reinterpret_cast<float *>(sh.sm + C::OFF_PY);
     sh.hx_ring = reinterpret_cast<float *>(sh.sm + C::OFF_HX);
@@ -597,7 +747,7 @@ __global__ void __launch_bounds__(32 * (TY + 1), MINB)
     if (aborted && warp == TY && lane == 0) {
         // record the timeout, then wait (bounded) for copies still in flight
         atomicCAS(&P.st->err, 0, (int)SPG_ETIMEOUT);
-        for (long long q = pipe.drain_from; q < pipe.issued_upto; q++) {
+        for (unsigned q = pipe.drain_from; q < pipe.issued_upto; q++) {
             const int s = (int)(q % S);
             (void)mbar_wait(&sh.bars[s], (uint32_t)((q / S) & 1), P.timeout_ns);
         }
