@@ -108,6 +108,8 @@ def _bind(path):
         "orc_solve": (ctypes.c_int, [PP, _D, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D]),
         "orc_unrolled": (None, [PP, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D]),
         "orc_certificate": (ctypes.c_double, [PP, _D, _D, ctypes.c_double, _D, _D, _D]),
+        "orc_unrolled_counts": (None, [PP, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D,
+                                       ctypes.POINTER(ctypes.c_longlong)]),
         "orc_unrolled_active": (ctypes.c_longlong, [PP, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D]),
         "orc_step_sampled": (None, [PP, _D, _D, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D,
                                     ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _D]),
@@ -301,6 +303,18 @@ def unrolled_active(b, w, om1, omtv, tau, iters, x0, p: Params):
     n = _load().orc_unrolled_active(ctypes.byref(p.c()), _ptr(b), _ptr(w), _ptr(o1), _ptr(ot), float(tau),
                                     int(iters), _ptr(x0), _ptr(out))
     return out, int(n)
+
+
+def unrolled_counts(b, w, om1, omtv, tau, iters, x0, p: Params):
+    """(x_K, (soft-threshold passes, voxel-steps on the quadratic branch of the
+    smoothed norm)): the two kinds of kink of the unrolled map."""
+    b, w, x0 = _a(b, p.shape), _a(w, p.shape), _a(x0, p.shape)
+    o1, ot = _opt(om1, p.shape), _opt(omtv, p.shape)
+    out = np.empty(p.shape)
+    cnt = (ctypes.c_longlong * 2)()
+    _load().orc_unrolled_counts(ctypes.byref(p.c()), _ptr(b), _ptr(w), _ptr(o1), _ptr(ot), float(tau),
+                                int(iters), _ptr(x0), _ptr(out), cnt)
+    return out, (int(cnt[0]), int(cnt[1]))
 
 
 def certificate(y, xplus, tau, b, w, omtv, p: Params):

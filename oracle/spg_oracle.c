@@ -479,6 +479,54 @@ long long orc_unrolled_active(const orc_params *p, const double *b, const double
     return active;
 }
 
+/* K steps as orc_unrolled, counting the two places where the unrolled map has
+ * a kink: soft-threshold passes (Eq. 21: |z| > t) and voxel-steps on the
+ * quadratic branch of the smoothed norm (Eq. 14/16: |Dy| < mu, where the
+ * second derivative of h_mu jumps). counts = {passes, quadratic-branch
+ * voxel-steps}. Two runs with equal counts take the same branches unless
+ * entries and exits cancel. */
+void orc_unrolled_counts(const orc_params *p, const double *b, const double *w, const double *om1,
+                         const double *omtv, double tau, int iters, const double *x0, double *xK,
+                         long long counts[2])
+{
+    const size_t n = NVOX(p);
+    double *xc = (double *)malloc(n * sizeof(double));
+    double *xp = (double *)malloc(n * sizeof(double));
+    double *y = (double *)malloc(n * sizeof(double));
+    double *g = (double *)malloc(n * sizeof(double));
+    double *dy = (double *)malloc(3 * n * sizeof(double));
+    double *beta = (double *)malloc((size_t)(iters > 0 ? iters : 1) * sizeof(double));
+    orc_beta_table(p->momentum, iters, beta);
+    memcpy(xc, x0, n * sizeof(double));
+    memcpy(xp, x0, n * sizeof(double));
+    long long passes = 0, quad = 0;
+    for (int k = 0; k < iters; k++) {
+        for (size_t v = 0; v < n; v++) y[v] = xc[v] + beta[k] * (xc[v] - xp[v]);
+        orc_grad(p, y, dy);
+        for (size_t v = 0; v < n; v++) {
+            const double s2 = dy[v] * dy[v] + dy[n + v] * dy[n + v] + dy[2 * n + v] * dy[2 * n + v];
+            if (sqrt(s2) < p->mu) quad++;
+        }
+        orc_grad_f(p, y, b, w, omtv, g);
+        for (size_t v = 0; v < n; v++) {
+            double z = y[v] - tau * g[v];
+            double t = tau * p->lambda_l1 * (om1 ? om1[v] : 1.0);
+            if (fabs(z) > t || t <= 0.0) passes++;
+            xp[v] = xc[v];
+            xc[v] = orc_soft(z, t);
+        }
+    }
+    memcpy(xK, xc, n * sizeof(double));
+    counts[0] = passes;
+    counts[1] = quad;
+    free(xc);
+    free(xp);
+    free(y);
+    free(g);
+    free(dy);
+    free(beta);
+}
+
 /* ---------- strong-convexity certificate ---------- */
 
 /* |r|^2 with r = grad f(x+) - grad f(y) + (y - x+)/tau, an element of the

@@ -535,6 +535,23 @@ def test_adjoint_matches_central_differences(orc):
         assert done, name
 
 
+def test_unrolled_kink_counts(orc):
+    """The counting run used to exclude kink-crossing directions: same x_K and
+    threshold count as the plain unrolled run; on a constant problem every
+    difference is 0, so every voxel-step is on the quadratic branch of the
+    smoothed norm (Eq. 14/16), and with a large threshold none passes."""
+    vol, b, w, p, tau, x0, K = _adjoint_case(orc)
+    xa, act = orc.unrolled_active(b, w, None, None, tau, K, x0, p)
+    xc, (passes, quad) = orc.unrolled_counts(b, w, None, None, tau, K, x0, p)
+    np.testing.assert_array_equal(xa, xc)
+    assert passes == act and 0 < quad < b.size * K
+    shape = b.shape
+    pc = P(orc, shape, mu=0.02, lambda_tv=0.1, lambda_l1=10.0)
+    _, (passes, quad) = orc.unrolled_counts(np.full(shape, 0.7), np.full(shape, 2.0), None, None, 0.1, K,
+                                            x0, pc)
+    assert quad == b.size * K and passes == 0
+
+
 def test_adjoint_identity_of_one_linear_step(orc):
     """With lambda_l1 = 0 and every |Dy| below mu one step is linear in
     (x_k, x_{k-1}, b): the adjoint's b-gradient equals tau w g for a loss
