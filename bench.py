@@ -533,7 +533,7 @@ def run_spg(args):
     return 0
 
 
-def measure_e2e(vol, hyper, args, stream, iters=100, reps=5, world=1):
+def measure_e2e(vol, hyper, args, stream, iters=100, reps=10, world=1):
     """Through the public API with host buffers. Each step uploads b and w from
     pinned host memory (with the device validation), re-weights, runs `iters`
     fused iterations, reads the objective and downloads x to pinned host
@@ -652,7 +652,7 @@ def run_batch(args):
     params = [dict(shape=v.b.shape, **h) for v, h in vols]
     nvox = sum(v.b.size for v, _ in vols)
     s = spg.SPG(params, stream=stream.cuda_stream, hist_every=args.hist_every, storage=args.storage,
-                data_dtype=args.dtype)
+                data_dtype=args.dtype, tile=args.tile)
     for i, (v, _) in enumerate(vols):
         s.set_data(i, *dev_inputs(v, args.dtype))
     s.reweight()
