@@ -116,12 +116,13 @@ def test_fourier_param_scales():
     np.testing.assert_allclose(got, want, rtol=2e-5)
 
 
-@pytest.mark.parametrize("shape", [(20, 24, 28), (128, 20, 22)])
+@pytest.mark.parametrize("shape", [(20, 24, 28), (128, 20, 22), (16, 128, 128)])
 def test_fourier_anchor_matches_oracle(shape):
     """The implicit-gradient term gamma |x - a|^2 with the Fourier-domain data
     term (Eq. 31): the spectrum pass uses N + 2 gamma and the anchor's
     transform; iterate and data-plus-anchor value against the oracle, on the
-    library's 3-D transforms (nz = 20) and on the TMA-fed z pass (nz = 128)."""
+    library's 3-D transforms (nz = 20) and on the TMA-fed z pass (nz = 128,
+    with narrow and with square 128 x 128 planes)."""
     fv = synth.make_fourier_volume(shape, blobs=10, radius=5, seed=65)
     hyper = dict(HYPER, mu=0.02)
     anchor = (0.2 * np.random.default_rng(66).standard_normal(shape)).astype(np.float32)
@@ -163,3 +164,19 @@ def test_fourier_checkpoint_resume_bitwise():
     x2 = s.get_x(0).cpu().numpy()
     s.close()
     np.testing.assert_array_equal(x1, x2)
+
+
+
+# square power-of-two planes (128, 256, 512; the benchmark's planes are 512 x
+# 512) with power-of-two nz: per-plane 2-D transforms around the own z pass
+@pytest.mark.parametrize("shape", [(16, 128, 128), (128, 128, 128), (8, 256, 256), (32, 256, 256), (8, 512, 512)])
+def test_fourier_square_planes_match_oracle(shape):
+    fv = synth.make_fourier_volume(shape, blobs=12, radius=6, seed=sum(shape) + 1)
+    hyper = dict(HYPER, mu=0.02)
+    x, obj, hist = gpu_fourier_solve(fv, hyper, 2, 15)
+    p = oracle.Params(shape, **hyper)
+    xr, hr, rr = fourier.solve(fv.y, fv.N, p, 2, 15)
+    err = rel_l2(x, xr)
+    print(f"fourier square planes {shape}: rel-L2 {err:.3e}")
+    assert err <= 1e-5
+    np.testing.assert_allclose(hist[:, 2:4], np.concatenate([hr[0, :, 1:3], hr[1, :, 1:3]]), rtol=1e-5)
