@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-gap", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the other storage forms, the batch, the adjoint and the Fourier-domain lines that the "
+                         "default run appends under 'secondary'")
     ap.add_argument("--difference", default="backward", choices=["backward", "forward"])
     ap.add_argument("--boundary", default="neumann", choices=["neumann", "periodic"])
     ap.add_argument("--tv-weight", default="inside", choices=["inside", "post_div"])
@@ -511,6 +514,9 @@ def run_spg(args):
     gap = None
     if not args.no_gap and rank == 0 and world == 1:  # a single-GPU figure; other GPUs are not held for it
         gap = time_to_gap(vol, hyper, args, stream)
+    secondary = None
+    if not args.no_secondary and adopted and rank == 0 and world == 1:
+        secondary = measure_secondary(vol, hyper, args, stream)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(vol, hyper)
@@ -526,21 +532,69 @@ def run_spg(args):
                           "iterate_storage": args.storage,
                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                "roofline": roof, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
-               "cpu_baseline": cpu, "time_to_gap": gap, "final_objective": float(obj[3])}
+               "cpu_baseline": cpu, "time_to_gap": gap, "final_objective": float(obj[3]),
+               "secondary": secondary}
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
     return 0
 
 
+def measure_forms(vol, hyper, args, stream, steps=50, warmup=5):
+    """The other storage forms of the fused step on the same 512^3 volume, the
+    objective fused into every step: FP32 previous-iterate storage, BF16 b,w
+    with increment and with previous-iterate storage."""
+    import torch
+
+    from paper_1905_13408_gb300 import spg
+    peaks, kind = measured_peaks()
+    out = {}
+    nvox = vol.b.size
+    for dtype, storage in (("f32", "prev"), ("bf16", "delta"), ("bf16", "prev")):
+        s = spg.SPG(dict(shape=vol.b.shape, **hyper), data_dtype=dtype, stream=stream.cuda_stream, storage=storage,
+                    max_iters=100000)
+        s.set_data(0, *dev_inputs(vol, dtype))
+        s.reweight()
+        s.iterate(warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.iterate(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.close()
+        sec = e0.elapsed_time(e1) / 1e3 / steps
+        out[f"{dtype}_{storage}"] = {"value": nvox / sec / 1e9, "unit": UNIT, "ms_per_step": sec * 1e3,
+                                     "steps": steps,
+                                     "roofline": roofline_block(dtype, storage, nvox, sec, peaks["hbm_gbs"], kind,
+                                                                profiled_traffic(args.workload, dtype, storage))}
+    return out
+
+
+def measure_secondary(vol, hyper, args, stream):
+    """Lines of the other workloads, appended to the default run so that one
+    run of bench.py measures every figure the design notes quote: the other
+    storage forms at 512^3, the 24-volume batch, the unrolled adjoint at
+    128^3 and the Fourier-domain data term at 512^3 (each its own workload
+    and timing, 20 timed steps after 5 warm-up steps)."""
+    import copy
+
+    sub = copy.copy(args)
+    sub.steps, sub.warmup, sub.tile, sub.zchunk, sub.hist_every = 20, 5, "auto", 0, 1
+    sub.dtype, sub.storage = "f32", "delta"
+    sub.fourier_shape = "512,512,512"
+    return {"forms_512": measure_forms(vol, hyper, args, stream), "batch24": measure_batch(sub),
+            "adjoint128": measure_adjoint(sub), "fourier512": measure_fourier(sub)}
+
+
 def measure_e2e(vol, hyper, args, stream, iters=100, reps=10, world=1):
     """Through the public API with host buffers. Each step uploads b and w from
     pinned host memory (with the device validation), re-weights, runs `iters`
     fused iterations, reads the objective and downloads x to pinned host
-    memory. Two contexts on two streams alternate between steps, so a step's
-    upload and the previous step's objective and download overlap iterations
-    (the serving pattern); the same steps run back to back on one context are
-    reported beside it. With several ranks every rank runs its own volume;
+    memory. Three contexts on three streams take the steps in rotation, so a
+    step's upload and the previous step's objective and download overlap
+    iterations (the serving pattern); the same steps run back to back on one
+    context are reported beside it. With several ranks every rank runs its own volume;
     the times are taken between barriers, their maximum over ranks is the
     job's time and the rate counts all ranks' voxels."""
     import torch
@@ -549,7 +603,7 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=10, world=1):
     b_h = torch.from_numpy(vol.b).pin_memory()
     w_h = torch.from_numpy(vol.w).pin_memory()
     x_h = torch.empty(vol.b.shape, dtype=torch.float32).pin_memory()
-    streams = [stream, torch.cuda.Stream()]
+    streams = [stream, torch.cuda.Stream(), torch.cuda.Stream()]
     ctxs = [spg.SPG(dict(shape=vol.b.shape, **hyper), data_dtype=args.dtype, tile=args.tile, zchunk=args.zchunk,
                     stream=st.cuda_stream, storage=args.storage, hist_every=args.hist_every) for st in streams]
     for _ in range(2):
@@ -597,31 +651,40 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=10, world=1):
     t_seq = max_over_ranks(time.perf_counter() - t0, world)
     seq = world * nvox * iters * reps / t_seq / 1e9
 
-    # two contexts: step i+1 is uploaded and enqueued while step i iterates,
-    # and step i's objective and download overlap step i+1's iterations
+    # three contexts in rotation: steps i+1 and i+2 are uploaded and enqueued
+    # while step i iterates, and step i's objective and download overlap their
+    # iterations; the fused launches of consecutive steps are ordered by an
+    # event, so they never share the GPU. Two steps of queued GPU work (about
+    # 0.12 s) ride out a stall of the host thread
     steps = 2 * reps
+    nq = len(ctxs)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    ctxs[0].set_data(0, b_h, w_h)
-    ctxs[0].reweight()
-    ctxs[0].iterate(iters)
-    done = torch.cuda.Event()
+    last = [None]
+
+    def enqueue(i):
+        c, st = ctxs[i % nq], streams[i % nq]
+        c.set_data(0, b_h, w_h)  # copies and validates on its own stream
+        if last[0] is not None:
+            st.wait_event(last[0])
+        c.reweight()
+        c.iterate(iters)  # asynchronous on its stream
+        ev = torch.cuda.Event()
+        ev.record(st)
+        last[0] = ev
+
+    for i in range(min(nq - 1, steps)):
+        enqueue(i)
     step_ms = []
     for i in range(steps):
         ts = time.perf_counter()
-        cur, nxt = ctxs[i % 2], ctxs[(i + 1) % 2]
-        done.record(streams[i % 2])    # cur's iterations are queued before this point
-        if i + 1 < steps:
-            nxt.set_data(0, b_h, w_h)  # copies and validates on nxt's stream
-            # nxt's iterations start when cur's are done: the fused launches of the
-            # two contexts never share the GPU, only copies and small kernels overlap
-            streams[(i + 1) % 2].wait_event(done)
-            nxt.reweight()
-            nxt.iterate(iters)         # asynchronous on nxt's stream
-        cur.objective(0)               # synchronises cur's stream
+        if i + nq - 1 < steps:
+            enqueue(i + nq - 1)
+        cur = ctxs[i % nq]
+        cur.objective(0)  # synchronises cur's stream
         cur.get_x(0, x_h)
-        streams[i % 2].synchronize()
+        streams[i % nq].synchronize()
         step_ms.append(1e3 * (time.perf_counter() - ts))
     dt = max_over_ranks(time.perf_counter() - t0, world)
     gc.enable()
@@ -631,14 +694,19 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=10, world=1):
             "h2d_bytes_per_step": int(world * (b_h.numel() * 4 + w_h.numel() * 4)),
             "d2h_bytes_per_step": int(world * (x_h.numel() * 4 + 4 * 8)),
             "step": f"upload b,w from pinned host (validated), re-weight, {iters} fused iterations, objective, "
-                    f"download x; two contexts on two streams alternate, so a step's upload and the previous "
-                    f"step's objective and download overlap iterations",
+                    f"download x; three contexts on three streams take the steps in rotation, so a step's "
+                    f"upload and the previous step's objective and download overlap iterations",
             "host_ms_per_step": [round(v, 2) for v in step_ms],
             "back_to_back_one_context": {"value": seq, "ms_per_phase": {k: 1e3 * v / reps for k, v in phases.items()},
                                          "upload_validate_ms_per_rep": [round(v, 2) for v in uploads]}}
 
 
 def run_batch(args):
+    print(json.dumps(measure_batch(args)))
+    return 0
+
+
+def measure_batch(args):
     """24 independent volumes of uneven sizes (6 each of 96^3, 128^3, 192^3,
     256^3, lambda_tv ~ U(0.05, 0.2)) advanced by one fused launch per
     iteration (replayed from a CUDA graph, tile shape from the autotuner),
@@ -701,11 +769,15 @@ def run_batch(args):
            "sequential": {"value": nvox * args.steps / (ms_seq / 1e3) / 1e9, "ms_per_step": ms_seq / args.steps,
                           "launches_per_step": len(vols)},
            "speedup_vs_sequential": ms_seq / ms_batch, "gpu_launches": launches}
-    print(json.dumps(out))
-    return 0
+    return out
 
 
 def run_adjoint(args):
+    print(json.dumps(measure_adjoint(args)))
+    return 0
+
+
+def measure_adjoint(args):
     """128^3 volume, 50 unrolled iterations (weights 1, tau fixed), forward
     and hand-written adjoint with checkpoints every 10 iterations."""
     import torch
@@ -731,13 +803,17 @@ def run_adjoint(args):
         b.grad = None
         w.grad = None
     fwd, bwd = min(t[0] for t in times), min(t[1] for t in times)
-    print(json.dumps({"metric": "unrolled forward + adjoint, 128^3, 50 iterations, checkpoints every 10",
-                      "forward_ms": fwd * 1e3, "backward_ms": bwd * 1e3, "unit": "ms",
-                      "voxel_iterations_per_s_backward": vol.b.size * K / bwd / 1e9}))
-    return 0
+    return {"metric": "unrolled forward + adjoint, 128^3, 50 iterations, checkpoints every 10",
+            "forward_ms": fwd * 1e3, "backward_ms": bwd * 1e3, "unit": "ms",
+            "voxel_iterations_per_s_backward": vol.b.size * K / bwd / 1e9}
 
 
 def run_fourier(args):
+    print(json.dumps(measure_fourier(args)))
+    return 0
+
+
+def measure_fourier(args):
     """Fourier-domain data term of Eq. 31 at 512^3: per iteration the
     per-plane 2-D real-to-complex transforms of y_k (cuFFT), one pass along
     z that transforms, forms the residual spectrum and transforms back, the
@@ -779,14 +855,12 @@ def run_fourier(args):
     # also writes the next y (28 + 4 B)
     bpv = 8 + 14 + 8 + 32
     achieved = bpv * nvox * args.steps / (ms / 1e3) / 1e9
-    print(json.dumps({"metric": "Gvoxel-iter/s, Fourier-domain data term (Eq. 31), %dx%dx%d" % shape,
-                      "value": nvox * args.steps / (ms / 1e3) / 1e9, "unit": UNIT, "steps": args.steps,
-                      "ms_per_step": ms / args.steps, "dtype": "f32", "data": "synthetic",
-                      "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                                   "frac": achieved / peaks["hbm_gbs"], "peak_kind": kind,
-                                   "bytes_per_voxel_model": bpv},
-                      "gpu_launches": launches, "final_objective": float(obj[3])}))
-    return 0
+    return {"metric": "Gvoxel-iter/s, Fourier-domain data term (Eq. 31), %dx%dx%d" % shape,
+            "value": nvox * args.steps / (ms / 1e3) / 1e9, "unit": UNIT, "steps": args.steps,
+            "ms_per_step": ms / args.steps, "dtype": "f32", "data": "synthetic",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "peak_kind": kind, "bytes_per_voxel_model": bpv},
+            "gpu_launches": launches, "final_objective": float(obj[3])}
 
 
 def run_grid(args):
