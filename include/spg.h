@@ -306,6 +306,49 @@ spg_status spg_history(spg_ctx *ctx, int vol, double *host, int max_entries, int
  * out = {max omtv, nnz(x), sum om1, sum omtv, L, tau}. Synchronises. */
 spg_status spg_round_stats(spg_ctx *ctx, int vol, double out[6]);
 
+/* z-slab decomposition of one volume over several contexts (one per GPU in a
+ * multi-GPU run; no counterpart in the paper, whose solver runs on one GPU).
+ * A volume of nz planes is cut into slabs of consecutive planes; each
+ * context holds its slab plus a one-plane halo: the plane just below it
+ * (halo_lo = 1, absent for the first slab) and the plane just above it
+ * (halo_hi = 1, absent for the last slab). A halo plane is read by the fused
+ * step (its x_k and pair enter the differences of Eq. 12 and the divergence
+ * of Eq. 17 at the slab's edge) but never written, and is left out of the
+ * objective sums and of the re-weighting statistics, so each context's
+ * history and statistics cover its own planes only. After every iteration
+ * the halo planes are refreshed with the neighbours' new values
+ * (spg_get_planes / spg_set_planes: the exchange a multi-GPU run makes with
+ * send/receive), and after every spg_reweight all slabs take one step size
+ * from the maxima over all slabs (spg_step_bound, then spg_set_step_bound).
+ * With these exchanges the slabs together compute bitwise the iterates of
+ * one context holding the whole volume; the objective is the sum of the
+ * slabs' histories.
+ *
+ * spg_set_halo marks the first (lo = 1) and/or last (hi = 1) plane of volume
+ * `vol` as halo planes (0 or 1 each; nz - lo - hi >= 1) and re-plans the
+ * fused step; call it before spg_autotune. Needs the adopted readings, no
+ * gradient restart and the real-space data term. Synchronises. */
+spg_status spg_set_halo(spg_ctx *ctx, int vol, int lo, int hi);
+
+/* out = {max w, max omtv} of volume `vol` in the current round (after
+ * spg_reweight; halo planes excluded from max omtv). Synchronises. */
+spg_status spg_step_bound(spg_ctx *ctx, int vol, double out[2]);
+
+/* Sets volume `vol`'s step of the current round to tau = 1/L with
+ * L = max_w + 12 lambda_tv max_omtv / mu, the expression spg_reweight uses,
+ * from maxima supplied by the caller (the maxima over all slabs); call after
+ * spg_reweight and before the round's first iteration. spg_round_stats then
+ * reports that L and tau. Errors: SPG_EINVAL, SPG_ENOTREADY. Synchronises. */
+spg_status spg_set_step_bound(spg_ctx *ctx, int vol, double max_w, double max_omtv);
+
+/* Copy planes [z0, z0 + n) of volume `vol`'s current iterate x_k (into x) and
+ * of its pair (into pair: the increment d_k with SPG_STORE_DELTA, x_{k-1}
+ * with SPG_STORE_PREV) out of the context, or into it. x and pair (either may
+ * be NULL) are contiguous float32 [n][ny][nx] arrays, host or device; the
+ * caller keeps ownership. Needs the adopted readings. Synchronises. */
+spg_status spg_get_planes(spg_ctx *ctx, int vol, int z0, int n, float *x, float *pair);
+spg_status spg_set_planes(spg_ctx *ctx, int vol, int z0, int n, const float *x, const float *pair);
+
 /* Strong-convexity certificate of the last iteration of volume `vol`:
  * out = |r|^2 with r = grad f(x_{k+1}) - grad f(y_k) + (y_k - x_{k+1})/tau, an
  * element of the subdifferential of F at x_{k+1}; F(x_{k+1}) - F* <=

@@ -341,7 +341,7 @@ spg_status build_plan(spg_ctx *ctx, const StepVariant &v, int zchunk_opt)
     for (const auto &d : ctx->vols_h) {
         const long long cols = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY);
         columns += cols;
-        plane_tiles += cols * d.nz;
+        plane_tiles += cols * (d.nz - d.halo_lo - d.halo_hi);
     }
     // Planes per work item: the z-chunk whose items, scheduled longest first
     // over the resident CTAs, give the shortest makespan (one wave of equal
@@ -350,9 +350,10 @@ spg_status build_plan(spg_ctx *ctx, const StepVariant &v, int zchunk_opt)
         std::vector<long long> c;
         for (const auto &d : ctx->vols_h) {
             const long long cols = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY);
-            const int nch = (d.nz + chunk - 1) / chunk;
+            const int nzi = d.nz - d.halo_lo - d.halo_hi;  // planes written (halo planes are only read)
+            const int nch = (nzi + chunk - 1) / chunk;
             for (int q = 0; q < nch; q++) {
-                const int z0 = (int)((long long)d.nz * q / nch), z1 = (int)((long long)d.nz * (q + 1) / nch);
+                const int z0 = (int)((long long)nzi * q / nch), z1 = (int)((long long)nzi * (q + 1) / nch);
                 if (z1 > z0) c.insert(c.end(), cols, item_cost(z0, z1));
             }
         }
@@ -388,9 +389,11 @@ spg_status build_plan(spg_ctx *ctx, const StepVariant &v, int zchunk_opt)
     for (int j = 0; j < ctx->nvol; j++) {
         VolDesc &d = ctx->vols_h[j];
         d.item_begin = (int)items.size();
-        const int nch = (d.nz + chunk - 1) / chunk;
+        const int nzi = d.nz - d.halo_lo - d.halo_hi;
+        const int nch = (nzi + chunk - 1) / chunk;
         for (int c = 0; c < nch; c++) {
-            const int z0 = (int)((long long)d.nz * c / nch), z1 = (int)((long long)d.nz * (c + 1) / nch);
+            const int z0 = d.halo_lo + (int)((long long)nzi * c / nch);
+            const int z1 = d.halo_lo + (int)((long long)nzi * (c + 1) / nch);
             if (z1 <= z0) continue;
             for (int ty = 0; ty < (d.ny + TY - 1) / TY; ty++)
                 for (int tx = 0; tx < (d.nx + TX - 1) / TX; tx++)
@@ -1349,6 +1352,108 @@ spg_status spg_round_stats(spg_ctx *ctx, int vol, double out[6])
     CK(cudaMemcpyAsync(out, ctx->rstats_d + (size_t)vol * 6, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
        "read round stats");
     return device_status(ctx);
+}
+
+// ---------------- z-slab decomposition of one volume ----------------
+
+spg_status spg_set_halo(spg_ctx *ctx, int vol, int lo, int hi)
+{
+    SPG_TRACE();
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || (lo != 0 && lo != 1) || (hi != 0 && hi != 1))
+        return fail(ctx, SPG_EINVAL, "spg_set_halo: bad arguments");
+    if (ctx->kread || ctx->opt.restart || ctx->fourier)
+        return fail(ctx, SPG_EINVAL,
+                    "spg_set_halo: needs the adopted readings, no gradient restart and the real-space data term");
+    VolDesc &d = ctx->vols_h[vol];
+    if (d.nz - lo - hi < 1) return fail(ctx, SPG_EINVAL, "spg_set_halo: no interior plane left");
+    d.halo_lo = lo;
+    d.halo_hi = hi;
+    return build_plan(ctx, ctx->var, ctx->opt.zchunk);  // items over the interior; descriptors uploaded
+}
+
+spg_status spg_step_bound(spg_ctx *ctx, int vol, double out[2])
+{
+    SPG_TRACE();
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || !out) return fail(ctx, SPG_EINVAL, "spg_step_bound: bad arguments");
+    if (!ctx->reweighted) return fail(ctx, SPG_ENOTREADY, "spg_step_bound: call spg_reweight first");
+    double mw = 0.0, st[6];
+    CK(cudaMemcpyAsync(&mw, ctx->maxw_d + vol, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "read max w");
+    CK(cudaMemcpyAsync(st, ctx->rstats_d + (size_t)vol * 6, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+       "read round stats");
+    spg_status s = device_status(ctx);
+    if (s != SPG_OK) return s;
+    out[0] = mw;
+    out[1] = st[0];
+    return SPG_OK;
+}
+
+spg_status spg_set_step_bound(spg_ctx *ctx, int vol, double max_w, double max_omtv)
+{
+    SPG_TRACE();
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || !std::isfinite(max_w) || !std::isfinite(max_omtv) || !(max_w > 0.0) ||
+        !(max_omtv >= 0.0))
+        return fail(ctx, SPG_EINVAL, "spg_set_step_bound: bad arguments");
+    if (!ctx->reweighted || ctx->k_round != 0)
+        return fail(ctx, SPG_ENOTREADY, "spg_set_step_bound: call it after spg_reweight, before the round's first step");
+    const VolDesc &d = ctx->vols_h[vol];
+    // the re-weighting kernel's expression, evaluated in the same order
+    const double L = max_w + 12.0 * (double)d.lambda_tv * max_omtv / (double)d.mu;
+    const double tau = 1.0 / L;
+    const float tf = (float)tau;
+    const double lt[2] = {L, tau};
+    CK(cudaMemcpyAsync(reinterpret_cast<char *>(ctx->vols_d + vol) + offsetof(VolDesc, tau), &tf, sizeof(float),
+                       cudaMemcpyHostToDevice, ctx->stream),
+       "write step");
+    CK(cudaMemcpyAsync(ctx->rstats_d + (size_t)vol * 6 + 4, lt, 2 * sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->stream),
+       "write round stats");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    ctx->vols_h[vol].tau = tf;
+    return SPG_OK;
+}
+
+// planes [z0, z0 + n) of the current iterate x_k and of its pair (d_k or
+// x_{k-1}) between the context and a caller's contiguous [n][ny][nx] arrays
+static spg_status copy_planes(spg_ctx *ctx, int vol, int z0, int n, float *x, float *pair, bool in, const char *who)
+{
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || n < 1 || z0 < 0 || (!x && !pair))
+        return fail(ctx, SPG_EINVAL, std::string(who) + ": bad arguments");
+    const VolDesc &d = ctx->vols_h[vol];
+    if ((long long)z0 + n > d.nz) return fail(ctx, SPG_EINVAL, std::string(who) + ": planes outside the volume");
+    if (ctx->reversed || ctx->kread) return fail(ctx, SPG_EINVAL, std::string(who) + ": needs the adopted readings");
+    const int c = ctx->cur();
+    float *bufs[2] = {ctx->X[c], ctx->X[ctx->aux_of(c)]};
+    float *user[2] = {x, pair};
+    for (int q = 0; q < 2; q++) {
+        if (!user[q]) continue;
+        float *dev = bufs[q] + d.off + (size_t)z0 * d.ny * d.pitch;
+        const size_t dp = (size_t)d.pitch * sizeof(float), up = (size_t)d.nx * sizeof(float);
+        if (in)
+            CK(cudaMemcpy2DAsync(dev, dp, user[q], up, up, (size_t)d.ny * n, cudaMemcpyDefault, ctx->stream),
+               "copy planes in");
+        else
+            CK(cudaMemcpy2DAsync(user[q], up, dev, dp, up, (size_t)d.ny * n, cudaMemcpyDefault, ctx->stream),
+               "copy planes out");
+    }
+    if (in) ctx->y_fresh = false;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    return SPG_OK;
+}
+
+spg_status spg_get_planes(spg_ctx *ctx, int vol, int z0, int n, float *x, float *pair)
+{
+    SPG_TRACE();
+    return copy_planes(ctx, vol, z0, n, x, pair, false, "spg_get_planes");
+}
+
+spg_status spg_set_planes(spg_ctx *ctx, int vol, int z0, int n, const float *x, const float *pair)
+{
+    SPG_TRACE();
+    return copy_planes(ctx, vol, z0, n, const_cast<float *>(x), const_cast<float *>(pair), true, "spg_set_planes");
 }
 
 spg_status spg_certificate(spg_ctx *ctx, int vol, double *out)

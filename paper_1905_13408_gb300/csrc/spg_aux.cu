@@ -451,7 +451,7 @@ __device__ void reweight_finish(const AuxParams &a, const double *maxw, double *
     for (int v = 0; v < a.nvol; v++) {
         const VolDesc W = a.vols[v];
         double m = 0, c3[3] = {0, 0, 0};
-        for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG; q += blockDim.x) {
+        for (int q = (W.plane_begin + W.halo_lo) * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz - W.halo_hi) * AUX_SEG; q += blockDim.x) {
             const double *pp = a.plane_part + (long long)q * 4;
             m = fmax(m, __ldcg(pp + 0));
             c3[0] += __ldcg(pp + 1);
@@ -490,7 +490,7 @@ __device__ void objective_finish(const AuxParams &a, double *scratch)
     for (int v = 0; v < a.nvol; v++) {
         const VolDesc W = a.vols[v];
         double c3[3] = {0, 0, 0};
-        for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG; q += blockDim.x) {
+        for (int q = (W.plane_begin + W.halo_lo) * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz - W.halo_hi) * AUX_SEG; q += blockDim.x) {
             const double *pp = a.plane_part + (long long)q * 4;
             c3[0] += __ldcg(pp + 0);
             c3[1] += __ldcg(pp + 1);
@@ -791,7 +791,7 @@ __global__ void generic_step_kernel(GenericParams g)
         const VolDesc W = g.vols[v];
         if (rec) {
             double c3[3] = {0, 0, 0};
-            for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG;
+            for (int q = (W.plane_begin + W.halo_lo) * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz - W.halo_hi) * AUX_SEG;
                  q += blockDim.x) {
                 const double *pp = g.plane_part + (long long)q * 4;
                 c3[0] += __ldcg(pp + 0);
@@ -1215,7 +1215,7 @@ __global__ void certificate_r_kernel(AuxParams a, const float *xplus, const floa
     for (int v = 0; v < a.nvol; v++) {
         const VolDesc W = a.vols[v];
         double accv[1] = {0};
-        for (int q = W.plane_begin * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz) * AUX_SEG; q += blockDim.x)
+        for (int q = (W.plane_begin + W.halo_lo) * AUX_SEG + threadIdx.x; q < (W.plane_begin + W.nz - W.halo_hi) * AUX_SEG; q += blockDim.x)
             accv[0] += __ldcg(a.plane_part + (long long)q * 4);
         block_sum<1>(accv, scratch);
         if (threadIdx.x == 0) a.vol_out[(long long)v * 8 + 4] = accv[0];

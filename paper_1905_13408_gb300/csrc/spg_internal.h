@@ -34,6 +34,7 @@ struct VolDesc {
     int kmom;                    // index of the next step's extrapolation weight in the beta table
     float beta_last;             // extrapolation weight used by the last step
     int readings;                // SPG_READ_* flags (0: the adopted readings, the fused path)
+    int halo_lo, halo_hi;        // first / last z-plane is a neighbour's plane (read, never written or summed)
 };
 
 // One work item of the fused step: an x-y tile [x0, x0+TX) x [y0, y0+TY) of

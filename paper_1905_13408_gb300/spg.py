@@ -41,7 +41,8 @@ EXPORTS = ["spg_create", "spg_create_batch", "spg_set_data", "spg_set_x", "spg_g
            "spg_objective_noalloc", "spg_noalloc_last_error", "spg_set_anchor", "spg_param_scales",
            "spg_fsc", "spg_fsc_last_error", "spg_set_data_fourier", "spg_backproject",
            "spg_backproject_last_error", "spg_grid_create", "spg_grid_add", "spg_grid_finish", "spg_grid_reset",
-           "spg_grid_count", "spg_grid_last_error", "spg_grid_destroy"]
+           "spg_grid_count", "spg_grid_last_error", "spg_grid_destroy", "spg_set_halo", "spg_step_bound",
+           "spg_set_step_bound", "spg_get_planes", "spg_set_planes"]
 
 
 class SPGError(RuntimeError):
@@ -136,6 +137,11 @@ def load():
             "spg_grid_last_error": (ctypes.c_char_p, [P]),
             "spg_grid_destroy": (None, [P]),
             "spg_param_scales": (I, [P, I, ctypes.POINTER(D)]),
+            "spg_set_halo": (I, [P, I, I, I]),
+            "spg_step_bound": (I, [P, I, ctypes.POINTER(D)]),
+            "spg_set_step_bound": (I, [P, I, D, D]),
+            "spg_get_planes": (I, [P, I, I, I, V, V]),
+            "spg_set_planes": (I, [P, I, I, I, V, V]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -378,6 +384,36 @@ def spg_round_stats(h, vol=0):
     return np.array(out[:])
 
 
+def spg_set_halo(h, vol, lo, hi):
+    _check(load().spg_set_halo(h, int(vol), int(lo), int(hi)), h)
+
+
+def spg_step_bound(h, vol=0):
+    out = (ctypes.c_double * 2)()
+    _check(load().spg_step_bound(h, int(vol), out), h)
+    return float(out[0]), float(out[1])
+
+
+def spg_set_step_bound(h, vol, max_w, max_omtv):
+    _check(load().spg_set_step_bound(h, int(vol), float(max_w), float(max_omtv)), h)
+
+
+def _opt_ptr(a):
+    return (None, None) if a is None else _ptr(a)
+
+
+def spg_get_planes(h, vol, z0, n, x, pair):
+    px, kx = _opt_ptr(x)
+    pp, kp = _opt_ptr(pair)
+    _check(load().spg_get_planes(h, int(vol), int(z0), int(n), px, pp), h)
+
+
+def spg_set_planes(h, vol, z0, n, x, pair):
+    px, kx = _opt_ptr(x)
+    pp, kp = _opt_ptr(pair)
+    _check(load().spg_set_planes(h, int(vol), int(z0), int(n), px, pp), h)
+
+
 def spg_certificate(h, vol=0):
     out = ctypes.c_double()
     _check(load().spg_certificate(h, vol, ctypes.byref(out)), h)
@@ -552,6 +588,27 @@ class SPG:
 
     def certificate(self, vol=0):
         return spg_certificate(self.handle, vol)
+
+    def set_halo(self, vol, lo, hi):
+        spg_set_halo(self.handle, vol, lo, hi)
+
+    def step_bound(self, vol=0):
+        return spg_step_bound(self.handle, vol)
+
+    def set_step_bound(self, vol, max_w, max_omtv):
+        spg_set_step_bound(self.handle, vol, max_w, max_omtv)
+
+    def get_planes(self, vol, z0, n):
+        """(x, pair) planes [z0, z0 + n) of the current iterate pair, as CUDA tensors."""
+        import torch
+        nz, ny, nx = self.shapes[vol]
+        x = torch.empty((n, ny, nx), dtype=torch.float32, device="cuda")
+        p = torch.empty_like(x)
+        spg_get_planes(self.handle, vol, z0, n, x, p)
+        return x, p
+
+    def set_planes(self, vol, z0, x, pair):
+        spg_set_planes(self.handle, vol, z0, x.shape[0], x.contiguous(), pair.contiguous())
 
     def counters(self):
         return spg_counters(self.handle)
