@@ -49,3 +49,17 @@ def test_half_maps_regularised_vs_raw():
     print(f"half-maps 64^3: FSC=0.143 at shell {kr} (raw) vs {ks} (regularised)")
     mid = slice(4, n // 4)
     assert sol[mid].mean() > raw[mid].mean()
+
+
+def test_fsc_repeats_within_rounding():
+    """Shell sums are accumulated with shared-memory double atomics, so their
+    order, and the last bits of the result, can change between runs; two runs
+    on the same maps agree far below the float32 inputs' precision."""
+    rng = np.random.default_rng(9)
+    n = 48
+    a = torch.from_numpy(rng.standard_normal((n, n, n)).astype(np.float32)).cuda()
+    b = torch.from_numpy(rng.standard_normal((n, n, n)).astype(np.float32)).cuda()
+    f1, c1 = spg.spg_fsc(a, b)
+    f2, c2 = spg.spg_fsc(a, b)
+    np.testing.assert_array_equal(c1, c2)
+    np.testing.assert_allclose(f1, f2, rtol=0, atol=1e-12)
