@@ -315,7 +315,7 @@ def run_reference(args):
     return 0
 
 
-def time_to_gap(vol, hyper, args, stream):
+def time_to_gap(vol, hyper, args, stream, later_rounds=True):
     """Round-1 subproblem from x_0 = 0: iterations and wall time (CUDA events)
     until F(x_k) <= F* (1 + 1e-3), then rounds 2 and 3 the same way from the
     previous round's point at the gap. F* is the best objective of 1500-iteration
@@ -386,6 +386,8 @@ def time_to_gap(vol, hyper, args, stream):
     # runs of both variants; both variants are timed.
     later = []
     start = x_gap if out["fixed_schedule"].get("iterations_to_gap") is not None else None
+    if not later_rounds:
+        start = None
     for r in (2, 3):
         if start is None:
             break
@@ -583,8 +585,13 @@ def measure_secondary(vol, hyper, args, stream):
     sub.steps, sub.warmup, sub.tile, sub.zchunk, sub.hist_every = 20, 5, "auto", 0, 1
     sub.dtype, sub.storage = "f32", "delta"
     sub.fourier_shape = "512,512,512"
-    return {"forms_512": measure_forms(vol, hyper, args, stream), "batch24": measure_batch(sub),
-            "adjoint128": measure_adjoint(sub), "fourier512": measure_fourier(sub)}
+    bf = copy.copy(args)
+    bf.dtype, bf.storage, bf.tile, bf.zchunk = "bf16", "delta", "auto", 0
+    gap_bf16 = time_to_gap(vol, hyper, bf, stream, later_rounds=False)
+    gap_bf16["note"] = ("round-1 subproblem with b, w stored in bfloat16 (its own F*: the problem of the rounded "
+                        "data); compare with the FP32 line's time_to_gap")
+    return {"forms_512": measure_forms(vol, hyper, args, stream), "time_to_gap_bf16": gap_bf16,
+            "batch24": measure_batch(sub), "adjoint128": measure_adjoint(sub), "fourier512": measure_fourier(sub)}
 
 
 def measure_e2e(vol, hyper, args, stream, iters=100, reps=10, world=1):
