@@ -182,11 +182,14 @@ spg_status spg_set_data(spg_ctx *ctx, int vol, const void *b, const void *w, spg
  * extrapolated point y_k (written by the previous fused step), forms the
  * residual spectrum N A y_k - D y and transforms back to get the data
  * gradient A^H (N A y_k - D y) for the fused step; for power-of-two nz from 8
- * to 4096 the transforms are per-plane 2-D ones (cuFFT, loaded at run time)
- * and the library's own transform along z, which forms the residual inside
- * its pass; for other nz, 3-D cuFFT transforms around a separate spectrum
- * pass (volumes of fewer than 2^31 voxels; larger ones need a power-of-two
- * nz, else SPG_EINVAL). L = max N + 12 lambda_tv max(omtv) / mu. Needs SPG_F32 data storage and
+ * to 4096 the transforms are per-plane ones and the library's own transform
+ * along z, which forms the residual inside its pass: with power-of-two nx
+ * from 128 to 1024 an own pass along the rows (the spectrum held kx-major in
+ * between) and cuFFT along y over contiguous lines, otherwise cuFFT's
+ * per-plane 2-D transforms (also chosen by SPG_ROW_PASS=0 in the
+ * environment when the data are set); for other nz, 3-D cuFFT transforms
+ * around a separate spectrum pass (volumes of fewer than 2^31 voxels; larger
+ * ones need a power-of-two nz, else SPG_EINVAL). cuFFT is loaded at run time. L = max N + 12 lambda_tv max(omtv) / mu. Needs SPG_F32 data storage and
  * SPG_STORE_DELTA; certificate and adjoint are not available in this
  * mode. The objective history records the l1 and TV terms only (its data
  * column is 0); spg_objective returns all terms. spg_set_data switches back

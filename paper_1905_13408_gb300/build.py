@@ -23,7 +23,7 @@ LIB = os.path.join(HERE, "libspg.so")
 # checker.
 LIB_CHECK = os.path.join(HERE, "libspg_check.so")
 SOURCES = ["spg_step_f32.cu", "spg_step_bf16.cu", "spg_step.cu", "spg_aux.cu", "spg_api.cu", "spg_noalloc.cu",
-           "spg_fsc.cu", "spg_cufft.cu", "spg_fourier.cu", "spg_grid.cu", "spg_zfft.cu"]
+           "spg_fsc.cu", "spg_cufft.cu", "spg_fourier.cu", "spg_grid.cu", "spg_zfft.cu", "spg_xpass.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -50,7 +50,7 @@ def _stale(lib=LIB):
     t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, s) for s in SOURCES]
     deps += [os.path.join(CSRC, "spg_internal.h"), os.path.join(CSRC, "spg_step_kernel.cuh"),
-             os.path.join(CSRC, "spg_cufft.h"), os.path.join(CSRC, "spg_trace.h"),
+             os.path.join(CSRC, "spg_cufft.h"), os.path.join(CSRC, "spg_trace.h"), os.path.join(CSRC, "spg_fft.cuh"),
              os.path.join(INCLUDE, "spg.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps)
 

@@ -123,6 +123,19 @@ struct spg_ctx {
     float2 *ztw = nullptr;           // twiddle table of the transform along z
     ZMaps zmaps[2]{};                // TMA maps of the z pass: with (N, C), with (N + 2 gamma, C + ...)
     bool zmaps_ok[2] = {false, false};
+    // xown: each iteration's in-plane transforms are the own row pass
+    // (power-of-two nx 128 .. 1024) and the library's transform along y over
+    // the contiguous lines of the kx-major spectrum [nz][nx/2+1][ny]; the z
+    // pass then reads N and C (and their anchor variants) in that order
+    bool xown = false;
+    float2 *xtw = nullptr;           // twiddle table of the row pass
+    cufftHandle pyc = 0;             // complex transform along y, nz (nx/2+1) contiguous lines
+    float *Nx = nullptr;             // N, C, N + 2 gamma, C + ... held kx-major
+    float2 *Cx = nullptr;
+    float *Nstx = nullptr;
+    float2 *Cstx = nullptr;
+    ZMaps zmapsx[2]{};
+    bool zmapsx_ok[2] = {false, false};
     long long nhalf = 0;
 
     cudaGraphExec_t gexec = nullptr;
@@ -176,7 +189,9 @@ void free_all(spg_ctx *c)
         spg::cufft_api().destroy(c->pr2c);
         spg::cufft_api().destroy(c->pc2r);
     }
-    void *fs[] = {c->Ybuf, c->Fh, c->Yh, c->Nh, c->Ch, c->Nmax, c->fpart, c->Anc, c->Nst, c->Cst, c->certQ, c->ztw};
+    if (c->xown) spg::cufft_api().destroy(c->pyc);
+    void *fs[] = {c->Ybuf, c->Fh, c->Yh, c->Nh, c->Ch, c->Nmax, c->fpart, c->Anc, c->Nst, c->Cst, c->certQ, c->ztw, c->xtw, c->Nx,
+                  c->Cx, c->Nstx, c->Cstx};
     for (void *p : fs)
         if (p) cudaFree(p);
     void *ps[] = {c->vols_d, c->items_d, c->sched_d, c->tmaps_d, c->plane_vol_d, c->X[0], c->X[1], c->X[2], c->X[3], c->B, c->W,
@@ -576,23 +591,42 @@ cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
         const double V = (double)d.nx * d.ny * d.nz;
         cudaError_t e = cudaSuccess;
         const spg::CufftApi &cf = spg::cufft_api();
-        if (cf.exec_r2c(ctx->pr2c, ctx->Ybuf, reinterpret_cast<cufftComplex *>(ctx->Fh)) != CUFFT_SUCCESS)
-            return cudaErrorUnknown;
         const bool anc = ctx->gamma_f > 0.f;
-        const float *Nw = anc ? ctx->Nst : ctx->Nh;
-        const float2 *Cw = anc ? ctx->Cst : ctx->Ch;
-        if (!ctx->zown)
-            e = launch_spec_scale(ctx->Fh, Nw, Cw, ctx->nhalf, (float)(1.0 / V), ctx->stream);
-        else if (ctx->zmaps_ok[anc ? 1 : 0])
-            e = launch_zfft_residual_tma(ctx->Fh, (float)(1.0 / V), ctx->zplan, ctx->ztw, ctx->zmaps[anc ? 1 : 0],
-                                         &ctx->st_d->err, ctx->stream);
-        else
-            e = launch_zfft_residual(ctx->Fh, Nw, Cw, (float)(1.0 / V), ctx->zplan, ctx->ztw, ctx->stream);
-        if (e != cudaSuccess) return e;
-        if (cf.exec_c2r(ctx->pc2r, reinterpret_cast<cufftComplex *>(ctx->Fh), static_cast<float *>(ctx->B)) !=
-            CUFFT_SUCCESS)
-            return cudaErrorUnknown;
-        ctx->launches += 1;
+        if (ctx->xown) {
+            cufftComplex *Fc = reinterpret_cast<cufftComplex *>(ctx->Fh);
+            e = launch_xpass_r2c(d.nx, ctx->Ybuf, d.pitch, d.ny, d.nz, ctx->Fh, ctx->xtw, ctx->stream);
+            if (e != cudaSuccess) return e;
+            if (cf.exec_c2c(ctx->pyc, Fc, Fc, CUFFT_FORWARD) != CUFFT_SUCCESS) return cudaErrorUnknown;
+            if (ctx->zmapsx_ok[anc ? 1 : 0])
+                e = launch_zfft_residual_tma(ctx->Fh, (float)(1.0 / V), ctx->zplan, ctx->ztw, ctx->zmapsx[anc ? 1 : 0],
+                                             &ctx->st_d->err, ctx->stream);
+            else
+                e = launch_zfft_residual(ctx->Fh, anc ? ctx->Nstx : ctx->Nx, anc ? ctx->Cstx : ctx->Cx,
+                                         (float)(1.0 / V), ctx->zplan, ctx->ztw, ctx->stream);
+            if (e != cudaSuccess) return e;
+            if (cf.exec_c2c(ctx->pyc, Fc, Fc, CUFFT_INVERSE) != CUFFT_SUCCESS) return cudaErrorUnknown;
+            e = launch_xpass_c2r(d.nx, ctx->Fh, d.ny, d.nz, static_cast<float *>(ctx->B), d.pitch, ctx->xtw,
+                                 ctx->stream);
+            if (e != cudaSuccess) return e;
+            ctx->launches += 3;
+        } else {
+            if (cf.exec_r2c(ctx->pr2c, ctx->Ybuf, reinterpret_cast<cufftComplex *>(ctx->Fh)) != CUFFT_SUCCESS)
+                return cudaErrorUnknown;
+            const float *Nw = anc ? ctx->Nst : ctx->Nh;
+            const float2 *Cw = anc ? ctx->Cst : ctx->Ch;
+            if (!ctx->zown)
+                e = launch_spec_scale(ctx->Fh, Nw, Cw, ctx->nhalf, (float)(1.0 / V), ctx->stream);
+            else if (ctx->zmaps_ok[anc ? 1 : 0])
+                e = launch_zfft_residual_tma(ctx->Fh, (float)(1.0 / V), ctx->zplan, ctx->ztw, ctx->zmaps[anc ? 1 : 0],
+                                             &ctx->st_d->err, ctx->stream);
+            else
+                e = launch_zfft_residual(ctx->Fh, Nw, Cw, (float)(1.0 / V), ctx->zplan, ctx->ztw, ctx->stream);
+            if (e != cudaSuccess) return e;
+            if (cf.exec_c2r(ctx->pc2r, reinterpret_cast<cufftComplex *>(ctx->Fh), static_cast<float *>(ctx->B)) !=
+                CUFFT_SUCCESS)
+                return cudaErrorUnknown;
+            ctx->launches += 1;
+        }
     }
     if (ctx->kread) {
         GenericParams g;
@@ -620,7 +654,8 @@ cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
 spg_status launch_steps(spg_ctx *ctx, int k)
 {
     const StepParams p = step_params(ctx);
-    const long long per_iter = ctx->fourier ? 2 : 1;  // kernels of this library per iteration
+    // kernels of this library per iteration
+    const long long per_iter = ctx->fourier ? (ctx->xown ? 4 : 2) : 1;
     if (ctx->fourier && k > 0 && !ctx->y_fresh) {
         // y_k of the first step; every fused step then writes the next one
         CK(launch_form_y(ctx->st_d, ctx->vols_d, ctx->beta_d, ctx->X, ctx->Ybuf, ctx->total, ctx->stream), "form y");
@@ -1075,6 +1110,30 @@ spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const
         ctx->plans = true;
         ctx->zmaps_ok[0] = ctx->zown && zfft_tma_ok(ctx->zplan) &&
                            encode_zmaps(ctx->zplan, ctx->Fh, ctx->Nh, ctx->Ch, &ctx->zmaps[0]);
+        // power-of-two nx 128 .. 1024: the own row pass and the library's
+        // transform along y over contiguous lines (SPG_ROW_PASS=0 in the
+        // environment keeps the library's per-plane 2-D transforms)
+        const char *rp = std::getenv("SPG_ROW_PASS");
+        const long long ylines = (long long)d.nz * nxh;
+        if (ctx->zown && xpass_supported(d.nx, d.nz) && !(rp && std::strcmp(rp, "0") == 0) &&
+            ylines * d.ny <= INT_MAX) {
+            int ny1[1] = {d.ny};
+            if (cf.plan_many(&ctx->pyc, 1, ny1, ny1, 1, d.ny, ny1, 1, d.ny, CUFFT_C2C, (int)ylines) == CUFFT_SUCCESS) {
+                ctx->xown = true;  // the plan exists from here on (destroyed with the context)
+                cf.set_stream(ctx->pyc, ctx->stream);
+                std::vector<float2> xt;
+                xpass_twiddles(d.nx, &xt);
+                CK(dalloc(&ctx->xtw, xt.size() * sizeof(float2)), "alloc");
+                CK(cudaMemcpyAsync(ctx->xtw, xt.data(), xt.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                                   ctx->stream),
+                   "twiddles");
+                CK(dalloc(&ctx->Nx, (size_t)ctx->nhalf * sizeof(float)), "alloc");
+                CK(dalloc(&ctx->Cx, (size_t)ctx->nhalf * sizeof(float2)), "alloc");
+                CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+                ctx->zmapsx_ok[0] = zfft_tma_ok(ctx->zplan) &&
+                                    encode_zmaps(ctx->zplan, ctx->Fh, ctx->Nx, ctx->Cx, &ctx->zmapsx[0]);
+            }
+        }
     }
     CK(cudaMemcpyAsync(ctx->Yh, y_half, (size_t)ctx->nhalf * sizeof(float2), cudaMemcpyDefault, ctx->stream),
        "copy y");
@@ -1083,6 +1142,11 @@ spg_status spg_set_data_fourier(spg_ctx *ctx, int vol, const void *y_half, const
     // data spectrum sqrt(N) y / sqrt(V), subtracted from N F / V each iteration; b starts at 0
     const double V = (double)d.nx * d.ny * d.nz;
     CK(launch_spec_prep(ctx->Ch, ctx->Yh, ctx->Nh, ctx->nhalf, (float)(1.0 / std::sqrt(V)), ctx->stream), "prep");
+    if (ctx->xown) {
+        CK(launch_kx_major(ctx->Nh, ctx->Nx, d.ny, nxh, d.nz, ctx->stream), "N kx-major");
+        CK(launch_kx_major(ctx->Ch, ctx->Cx, d.ny, nxh, d.nz, ctx->stream), "C kx-major");
+        ctx->launches += 2;
+    }
     CK(cudaMemsetAsync(ctx->B, 0, (size_t)ctx->total * sizeof(float), ctx->stream), "memset");
     CK(launch_spec_max(ctx->Nh, ctx->nhalf, ctx->Nmax, ctx->stream), "max N");
     ctx->launches += 2;  // prep and max
@@ -1121,6 +1185,12 @@ spg_status spg_set_anchor(spg_ctx *ctx, int vol, float gamma, const float *x_anc
             CK(dalloc(&ctx->Cst, (size_t)ctx->nhalf * sizeof(float2)), "alloc");
             CK(cudaMemsetAsync(ctx->Anc, 0, (size_t)ctx->total * sizeof(float), ctx->stream), "memset");
             ctx->zmaps_ok[1] = ctx->zmaps_ok[0] && encode_zmaps(ctx->zplan, ctx->Fh, ctx->Nst, ctx->Cst, &ctx->zmaps[1]);
+            if (ctx->xown) {
+                CK(dalloc(&ctx->Nstx, (size_t)ctx->nhalf * sizeof(float)), "alloc");
+                CK(dalloc(&ctx->Cstx, (size_t)ctx->nhalf * sizeof(float2)), "alloc");
+                ctx->zmapsx_ok[1] =
+                    ctx->zmapsx_ok[0] && encode_zmaps(ctx->zplan, ctx->Fh, ctx->Nstx, ctx->Cstx, &ctx->zmapsx[1]);
+            }
         }
         spg_status s = copy_volume_in(ctx, ctx->Anc, 4, d, x_anchor);
         if (s != SPG_OK) return s;
@@ -1135,6 +1205,12 @@ spg_status spg_set_anchor(spg_ctx *ctx, int vol, float gamma, const float *x_anc
                               ctx->stream),
            "anchor spectrum");
         ctx->launches += 1;
+        if (ctx->xown) {
+            const int nxh = d.nx / 2 + 1;
+            CK(launch_kx_major(ctx->Nst, ctx->Nstx, d.ny, nxh, d.nz, ctx->stream), "N kx-major");
+            CK(launch_kx_major(ctx->Cst, ctx->Cstx, d.ny, nxh, d.nz, ctx->stream), "C kx-major");
+            ctx->launches += 2;
+        }
         float nmax = 0.f;
         CK(launch_spec_max(ctx->Nh, ctx->nhalf, ctx->Nmax, ctx->stream), "max N");
         ctx->launches += 1;

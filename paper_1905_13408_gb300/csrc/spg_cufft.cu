@@ -21,8 +21,9 @@ const CufftApi &cufft_api()
         c.set_stream = reinterpret_cast<decltype(c.set_stream)>(dlsym(h, "cufftSetStream"));
         c.exec_r2c = reinterpret_cast<decltype(c.exec_r2c)>(dlsym(h, "cufftExecR2C"));
         c.exec_c2r = reinterpret_cast<decltype(c.exec_c2r)>(dlsym(h, "cufftExecC2R"));
+        c.exec_c2c = reinterpret_cast<decltype(c.exec_c2c)>(dlsym(h, "cufftExecC2C"));
         c.destroy = reinterpret_cast<decltype(c.destroy)>(dlsym(h, "cufftDestroy"));
-        c.ok = c.plan3d && c.plan_many && c.set_stream && c.exec_r2c && c.exec_c2r && c.destroy;
+        c.ok = c.plan3d && c.plan_many && c.set_stream && c.exec_r2c && c.exec_c2r && c.exec_c2c && c.destroy;
     });
     return c;
 }

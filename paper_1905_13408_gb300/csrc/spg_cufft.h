@@ -15,6 +15,7 @@ struct CufftApi {
     cufftResult (*set_stream)(cufftHandle, cudaStream_t) = nullptr;
     cufftResult (*exec_r2c)(cufftHandle, cufftReal *, cufftComplex *) = nullptr;
     cufftResult (*exec_c2r)(cufftHandle, cufftComplex *, cufftReal *) = nullptr;
+    cufftResult (*exec_c2c)(cufftHandle, cufftComplex *, cufftComplex *, int) = nullptr;
     cufftResult (*destroy)(cufftHandle) = nullptr;
     bool ok = false;
 };

@@ -214,6 +214,19 @@ cudaError_t launch_zfft_residual_tma(float2 *F, float scale, const ZPlan &p, con
                                      int *err, cudaStream_t s);
 // F <- A_z F (unnormalised forward transform along z of every column).
 cudaError_t launch_zfft(float2 *F, const ZPlan &p, const float2 *tw, cudaStream_t s);
+
+// Row pass of the Fourier-domain term for power-of-two nx = 128 .. 1024
+// (spg_xpass.cu): real rows [nz][ny][pitch] <-> half spectrum held kx-major,
+// [nz][nx/2+1][ny], unnormalised; and the transposes that put arrays of the
+// standard half layout [nz][ny][nx/2+1] into that order.
+bool xpass_supported(int nx, int nz);
+void xpass_twiddles(int nx, std::vector<float2> *table);
+cudaError_t launch_xpass_r2c(int nx, const float *Y, int pitch, int ny, int nz, float2 *F, const float2 *tw,
+                             cudaStream_t s);
+cudaError_t launch_xpass_c2r(int nx, const float2 *F, int ny, int nz, float *Y, int pitch, const float2 *tw,
+                             cudaStream_t s);
+cudaError_t launch_kx_major(const float *in, float *out, int ny, int nxh, int nz, cudaStream_t s);
+cudaError_t launch_kx_major(const float2 *in, float2 *out, int ny, int nxh, int nz, cudaStream_t s);
 // F <- A_z^-1 ((A_z F) N scale - Cd), A_z^-1 the unnormalised inverse.
 cudaError_t launch_zfft_residual(float2 *F, const float *N, const float2 *Cd, float scale, const ZPlan &p,
                                  const float2 *tw, cudaStream_t s);

@@ -180,3 +180,21 @@ def test_fourier_square_planes_match_oracle(shape):
     print(f"fourier square planes {shape}: rel-L2 {err:.3e}")
     assert err <= 1e-5
     np.testing.assert_allclose(hist[:, 2:4], np.concatenate([hr[0, :, 1:3], hr[1, :, 1:3]]), rtol=1e-5)
+
+
+@pytest.mark.parametrize("shape", [(16, 128, 128), (8, 40, 256), (8, 512, 512), (8, 24, 1024)])
+def test_row_pass_equals_library_transforms(shape, monkeypatch):
+    """The own row pass (power-of-two nx, the spectrum held kx-major between
+    it and the transform along y) against the library's per-plane 2-D
+    transforms (SPG_ROW_PASS=0) on the same solve: the same arithmetic up to
+    the transforms' rounding; ny not a multiple of the rows per CTA (40)
+    leaves a ragged last group of rows."""
+    fv = synth.make_fourier_volume(shape, blobs=12, radius=min(shape) / 3, seed=sum(shape) + 2)
+    hyper = dict(HYPER, mu=0.02)
+    x_own, _, h_own = gpu_fourier_solve(fv, hyper, 1, 20)
+    monkeypatch.setenv("SPG_ROW_PASS", "0")
+    x_lib, _, h_lib = gpu_fourier_solve(fv, hyper, 1, 20)
+    err = rel_l2(x_own, x_lib)
+    print(f"row pass vs library in-plane transforms {shape}: rel-L2 {err:.3e}")
+    assert err <= 1e-6
+    np.testing.assert_allclose(h_own[:, 2:4], h_lib[:, 2:4], rtol=1e-6)
