@@ -42,10 +42,11 @@ struct Rows {
     static constexpr int T = H / 8;             // threads per row transform
     static constexpr int THREADS = 512;
     static constexpr int R = THREADS / T;       // rows per CTA
-    // a row's slots in shared memory: at least the padded length (and n/2 + 1),
-    // rounded to 1 modulo 16 so that one column read across 16 rows (the
-    // kx-major runs) falls on 16 different bank pairs
-    static constexpr int LP = (H + H / 8 + 14) / 16 * 16 + 1;
+    // a row's slots in shared memory: n/2 + 1 (the exchanges of the row
+    // transform are swizzled in place, see swz), which is 1 modulo 16, so that
+    // one column read across 16 rows (the kx-major runs) falls on 16
+    // different bank pairs
+    static constexpr int LP = H + 1;
     static constexpr int L = H;                 // length of a row transform
     // per-stage twiddle tables of the row transform (see stage_table_size)
     static constexpr int NS8 = (LOG2N - 1) / 3, REM = (LOG2N - 1) % 3;
@@ -56,6 +57,13 @@ struct Rows {
     static_assert(LOG2N >= 7 && LOG2N <= 10, "rows of 128 .. 1024");
     static_assert(LP >= NXH, "a row's slots hold its half spectrum");
 };
+
+// Slot of position z of a row during the transform's exchanges: bits 0-3 of z
+// XORed with bits 3-6 (a bijection within each aligned run of 128, so the row
+// needs no padding). The writes of a stage (8 consecutive positions of a
+// thread, Ns apart) and the reads (t + i L/8, consecutive over t) then each
+// take the minimum of two wavefronts per warp for L = 128 .. 512.
+__device__ __forceinline__ int swz(int z) { return z ^ ((z >> 3) & 15); }
 
 // In-register Stockham transform of length L = 2^LOG2L (L >= 64) and sign S;
 // row r's thread t holds positions t + i L/8 before and after. The threads of
@@ -85,10 +93,10 @@ __device__ __forceinline__ void row_fft(float2 (&v)[8], const float2 *stw, float
             const int base = (t - k) * 8 + k;
             __syncthreads();  // the previous exchange's (or the caller's) reads are done
 #pragma unroll
-            for (int q = 0; q < 8; q++) row[padded(base + q * Ns)] = v[q];
+            for (int q = 0; q < 8; q++) row[swz(base + q * Ns)] = v[q];
             __syncthreads();
 #pragma unroll
-            for (int i = 0; i < 8; i++) v[i] = row[padded(t + i * T)];
+            for (int i = 0; i < 8; i++) v[i] = row[swz(t + i * T)];
         }
     }
     if (REM == 1) {  // radix 2, span L/2: butterfly t + m L/8 on slots m, m + 4
@@ -138,22 +146,46 @@ __global__ void __launch_bounds__(Rows<LOG2N>::THREADS, 4)
     for (int i = 0; i < 8; i++) v[i] = in ? __ldg(row + t + i * P::T) : make_float2(0.f, 0.f);
     row_fft<LOG2N - 1, P::LP, -1>(v, tws + P::N, buf, t, r);
     float2 *u = buf + r * P::LP;
-    __syncthreads();  // the transform's last exchange is read
+    if constexpr (P::T <= 32) {
+        // U[n/2 - k] of k = t + i T is held by thread T - t of the row at slot
+        // 7 - i (thread 0: its own slot 8 - i), within the row's lanes
+        const int lane = threadIdx.x & 31;
+        const int partner = (lane & ~(P::T - 1)) | ((P::T - t) & (P::T - 1));
+        __syncthreads();  // the transform's last exchange is read
 #pragma unroll
-    for (int i = 0; i < 8; i++) u[t + i * P::T] = v[i];
-    __syncthreads();
-    for (int k = t; k <= P::H / 2; k += P::T) {
-        const float2 uk = u[k];
-        if (k == 0) {
-            u[0] = make_float2(uk.x + uk.y, 0.f);
-            u[P::H] = make_float2(uk.x - uk.y, 0.f);
-        } else {
-            const float2 um = conjf2(u[P::H - k]);
-            const float2 e = scale2(cadd(uk, um), 0.5f);
-            const float2 o = scale2(mul_mi(csub(uk, um)), 0.5f);
-            const float2 wo = cmul(tws[k], o);
-            u[k] = cadd(e, wo);
-            if (k != P::H - k) u[P::H - k] = conjf2(csub(e, wo));
+        for (int i = 0; i < 8; i++) {
+            const float2 got = make_float2(__shfl_sync(0xffffffffu, v[7 - i].x, partner),
+                                           __shfl_sync(0xffffffffu, v[7 - i].y, partner));
+            const float2 uk = v[i];
+            const int k = t + i * P::T;
+            if (k == 0) {
+                u[0] = make_float2(uk.x + uk.y, 0.f);
+                u[P::H] = make_float2(uk.x - uk.y, 0.f);
+            } else {
+                const float2 um = conjf2(t == 0 ? v[(8 - i) & 7] : got);
+                const float2 e = scale2(cadd(uk, um), 0.5f);
+                const float2 o = scale2(mul_mi(csub(uk, um)), 0.5f);
+                u[k] = cadd(e, cmul(tws[k], o));
+            }
+        }
+    } else {
+        __syncthreads();  // the transform's last exchange is read
+#pragma unroll
+        for (int i = 0; i < 8; i++) u[t + i * P::T] = v[i];
+        __syncthreads();
+        for (int k = t; k <= P::H / 2; k += P::T) {
+            const float2 uk = u[k];
+            if (k == 0) {
+                u[0] = make_float2(uk.x + uk.y, 0.f);
+                u[P::H] = make_float2(uk.x - uk.y, 0.f);
+            } else {
+                const float2 um = conjf2(u[P::H - k]);
+                const float2 e = scale2(cadd(uk, um), 0.5f);
+                const float2 o = scale2(mul_mi(csub(uk, um)), 0.5f);
+                const float2 wo = cmul(tws[k], o);
+                u[k] = cadd(e, wo);
+                if (k != P::H - k) u[P::H - k] = conjf2(csub(e, wo));
+            }
         }
     }
     __syncthreads();
