@@ -21,10 +21,10 @@
 // A CTA takes R consecutive rows of one plane; each row's length-n/2
 // transform is the register-resident Stockham form of spg_zfft.cu (n/16
 // threads per row, each holding 8 values), with exchanges through shared
-// memory laid out row by row, which keeps a warp (the threads of one row)
-// free of bank conflicts. The untwisted rows pass through the same shared
-// memory, where the kx-major writes (and reads) are gathered into runs of R
-// consecutive rows.
+// memory laid out row by row (Slots: padded per exchange, conflict-free), on
+// which only the row's own threads synchronise. The untwisted rows pass
+// through the same shared memory, where the kx-major writes (and reads) are
+// gathered into runs of R consecutive rows.
 #include <cmath>
 #include <vector>
 
@@ -42,11 +42,10 @@ struct Rows {
     static constexpr int T = H / 8;             // threads per row transform
     static constexpr int THREADS = 512;
     static constexpr int R = THREADS / T;       // rows per CTA
-    // a row's slots in shared memory: n/2 + 1 (the exchanges of the row
-    // transform are swizzled in place, see swz), which is 1 modulo 16, so that
-    // one column read across 16 rows (the kx-major runs) falls on 16
-    // different bank pairs
-    static constexpr int LP = H + 1;
+    // a row's slots in shared memory: those of its transform's exchanges
+    // (Slots) and n/2 + 1, rounded to 1 modulo 16, so that one column read
+    // across 16 rows (the kx-major runs) falls on 16 different bank pairs
+    static constexpr int LP = ((H >= 128 ? H + H / 8 : H) + 15) / 16 * 16 + 1;
     static constexpr int L = H;                 // length of a row transform
     // per-stage twiddle tables of the row transform (see stage_table_size)
     static constexpr int NS8 = (LOG2N - 1) / 3, REM = (LOG2N - 1) % 3;
@@ -58,25 +57,55 @@ struct Rows {
     static_assert(LP >= NXH, "a row's slots hold its half spectrum");
 };
 
-// Slot of position z of a row during the transform's exchanges: bits 0-3 of z
-// XORed with bits 3-6 (a bijection within each aligned run of 128, so the row
-// needs no padding). The writes of a stage (8 consecutive positions of a
-// thread, Ns apart) and the reads (t + i L/8, consecutive over t) then each
-// take the minimum of two wavefronts per warp for L = 128 .. 512.
-__device__ __forceinline__ int swz(int z) { return z ^ ((z >> 3) & 15); }
+// Slots of a row's positions z in the exchange after radix-8 stage s. A
+// warp-wide access of 8-byte values is served per half-warp, so a pattern is
+// conflict-free when the 16 threads of each half-warp reach 16 different
+// bank pairs. Rows of 128 and more pad each exchange for its own pattern:
+// after stage 0 (writes 8 t + q, reads t + i L/8) one slot per 16,
+// z + z/16; after stage 1 (writes 64 (t/8) + t mod 8 + 8 q) 8 slots per 64,
+// z + 8 (z/64); after stage 2 (writes and reads contiguous in t) none. Both
+// the writes and the reads of every exchange are then conflict-free and
+// reach their slots from one per-thread base at constant offsets
+// (at(s, base + q Ns) - at(s, base) = at(s, q Ns), and at(s, t + i L/8) -
+// at(s, t) = at(s, i L/8)). Rows of 64: bits 0-3 of z XORed with bits 3-6.
+template <int L>
+struct Slots {
+    static constexpr bool PAD = L >= 128;
+    static constexpr int SPAN = PAD ? L + L / 8 : L;  // slots a row takes
+    __device__ static __forceinline__ int at(int s, int z)
+    {
+        if constexpr (!PAD) return z ^ ((z >> 3) & 15);
+        return s == 0 ? z + (z >> 4) : (s == 1 ? z + 8 * (z >> 6) : z);
+    }
+};
+
+// Barrier over the T threads of one row r (its exchanges touch only its own
+// slots): the warp where rows fit in one, else a named barrier per row.
+template <int T>
+__device__ __forceinline__ void row_sync(int r)
+{
+    if constexpr (T <= 32)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + r), "n"(T) : "memory");
+}
 
 // In-register Stockham transform of length L = 2^LOG2L (L >= 64) and sign S;
-// row r's thread t holds positions t + i L/8 before and after. The threads of
+// row r's thread t holds positions t + i L/8 before and after. Only the row's
+// threads synchronise (row_sync; rows of 64 threads take named barriers
+// 1 .. 8): the caller orders the row's slots against other threads' use of
+// them. The threads of
 // a row are consecutive, so each stage reads its twiddles from a table laid
 // out in thread order (stw, from xpass_twiddles): radix-8 stage s (span
 // Ns = 8^s, s >= 1) at [q - 1][k], k = t mod Ns, holding w_L^(q k L/(8 Ns));
 // a last radix-2 stage at [m][t] (w_L^j, j = t + m L/8); a last radix-4
-// stage at [p - 1][j] (w_L^(p j)). Every thread of the block takes part.
+// stage at [p - 1][j] (w_L^(p j)).
 template <int LOG2L, int LP, int S>
 __device__ __forceinline__ void row_fft(float2 (&v)[8], const float2 *stw, float2 *buf, int t, int r)
 {
     constexpr int L = 1 << LOG2L, T = L / 8, NS8 = LOG2L / 3, REM = LOG2L % 3;
     static_assert(L >= 64, "at least two radix-8 stages");
+    static_assert(LP >= Slots<L>::SPAN, "a row's stride holds its exchange slots");
     float2 *row = buf + r * LP;
     int off = 0;
 #pragma unroll
@@ -90,13 +119,24 @@ __device__ __forceinline__ void row_fft(float2 (&v)[8], const float2 *stw, float
         }
         dft8<S>(v);
         if (s < NS8 - 1 || REM != 0) {
+            using Sl = Slots<L>;
             const int base = (t - k) * 8 + k;
-            __syncthreads();  // the previous exchange's (or the caller's) reads are done
+            row_sync<T>(r);  // the row's previous exchange (or the caller's reads of the row) is done
+            if constexpr (Sl::PAD) {
+                float2 *w = row + Sl::at(s, base);
 #pragma unroll
-            for (int q = 0; q < 8; q++) row[swz(base + q * Ns)] = v[q];
-            __syncthreads();
+                for (int q = 0; q < 8; q++) w[Sl::at(s, q * Ns)] = v[q];
+                row_sync<T>(r);
+                const float2 *rd = row + Sl::at(s, t);
 #pragma unroll
-            for (int i = 0; i < 8; i++) v[i] = row[swz(t + i * T)];
+                for (int i = 0; i < 8; i++) v[i] = rd[Sl::at(s, i * T)];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; q++) row[Sl::at(s, base + q * Ns)] = v[q];
+                row_sync<T>(r);
+#pragma unroll
+                for (int i = 0; i < 8; i++) v[i] = row[Sl::at(s, t + i * T)];
+            }
         }
     }
     if (REM == 1) {  // radix 2, span L/2: butterfly t + m L/8 on slots m, m + 4
@@ -126,18 +166,14 @@ __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.
 __device__ __forceinline__ float2 scale2(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }  // -i a
 
+// R rows y0 .. y0 + R - 1 of plane z: real-to-complex transform along x,
+// written kx-major (runs of R consecutive rows). tws: the row pass's table in
+// shared memory; buf: R LP slots.
 template <int LOG2N>
-__global__ void __launch_bounds__(Rows<LOG2N>::THREADS, 4)
-    xpass_r2c_kernel(const float *__restrict__ Y, int pitch, int ny, float2 *__restrict__ F,
-                     const float2 *__restrict__ tw)
+__device__ __forceinline__ void r2c_rows(const float *__restrict__ Y, int pitch, int ny, float2 *__restrict__ F,
+                                         const float2 *tws, float2 *buf, int z, int y0)
 {
     using P = Rows<LOG2N>;
-    extern __shared__ __align__(16) float2 xsm[];
-    float2 *const buf = xsm;
-    float2 *const tws = xsm + P::R * P::LP;
-    for (int i = threadIdx.x; i < P::TW; i += P::THREADS) tws[i] = tw[i];
-    __syncthreads();
-    const int z = blockIdx.y, y0 = blockIdx.x * P::R;
     const int t = threadIdx.x % P::T, r = threadIdx.x / P::T, y = y0 + r;
     const bool in = y < ny;
     const float2 *row = reinterpret_cast<const float2 *>(Y + ((long long)z * ny + (in ? y : 0)) * pitch);
@@ -147,13 +183,15 @@ __global__ void __launch_bounds__(Rows<LOG2N>::THREADS, 4)
     row_fft<LOG2N - 1, P::LP, -1>(v, tws + P::N, buf, t, r);
     float2 *u = buf + r * P::LP;
     if constexpr (P::T <= 32) {
-        // U[n/2 - k] of k = t + i T is held by thread T - t of the row at slot
-        // 7 - i (thread 0: its own slot 8 - i), within the row's lanes
+        // thread t untwists the pairs (k, n/2 - k), k = t + i T, i < 4: U[n/2 - k]
+        // is slot 7 - i of thread T - t of the row (for thread 0 its own slot
+        // 8 - i, and k = 0 gives X[0] and X[n/2]); thread 0 also takes
+        // k = n/4, which pairs with itself
         const int lane = threadIdx.x & 31;
         const int partner = (lane & ~(P::T - 1)) | ((P::T - t) & (P::T - 1));
-        __syncthreads();  // the transform's last exchange is read
+        row_sync<P::T>(r);  // the transform's last exchange is read
 #pragma unroll
-        for (int i = 0; i < 8; i++) {
+        for (int i = 0; i < 4; i++) {
             const float2 got = make_float2(__shfl_sync(0xffffffffu, v[7 - i].x, partner),
                                            __shfl_sync(0xffffffffu, v[7 - i].y, partner));
             const float2 uk = v[i];
@@ -165,14 +203,22 @@ __global__ void __launch_bounds__(Rows<LOG2N>::THREADS, 4)
                 const float2 um = conjf2(t == 0 ? v[(8 - i) & 7] : got);
                 const float2 e = scale2(cadd(uk, um), 0.5f);
                 const float2 o = scale2(mul_mi(csub(uk, um)), 0.5f);
-                u[k] = cadd(e, cmul(tws[k], o));
+                const float2 wo = cmul(tws[k], o);
+                u[k] = cadd(e, wo);
+                u[P::H - k] = conjf2(csub(e, wo));
             }
         }
+        if (t == 0) {
+            const float2 uk = v[4], um = conjf2(uk);
+            const float2 e = scale2(cadd(uk, um), 0.5f);
+            const float2 o = scale2(mul_mi(csub(uk, um)), 0.5f);
+            u[P::H / 2] = cadd(e, cmul(tws[P::H / 2], o));
+        }
     } else {
-        __syncthreads();  // the transform's last exchange is read
+        row_sync<P::T>(r);  // the transform's last exchange is read
 #pragma unroll
         for (int i = 0; i < 8; i++) u[t + i * P::T] = v[i];
-        __syncthreads();
+        row_sync<P::T>(r);
         for (int k = t; k <= P::H / 2; k += P::T) {
             const float2 uk = u[k];
             if (k == 0) {
@@ -189,39 +235,42 @@ __global__ void __launch_bounds__(Rows<LOG2N>::THREADS, 4)
         }
     }
     __syncthreads();
-    // kx-major: F[z][kx][y], runs of R consecutive rows
-    float2 *const Fz = F + (long long)z * P::NXH * ny;
-    for (int idx = threadIdx.x; idx < P::R * P::NXH; idx += P::THREADS) {
-        const int rr = idx % P::R, kx = idx / P::R, yy = y0 + rr;
-        if (yy < ny) Fz[(long long)kx * ny + yy] = buf[rr * P::LP + kx];
+    // kx-major: F[z][kx][y], runs of R consecutive rows; thread (rr, kx0)
+    // takes kx = kx0 + j KS of row rr
+    constexpr int KS = P::THREADS / P::R, NJ = (P::NXH + KS - 1) / KS;
+    const int rr = threadIdx.x % P::R, kx0 = threadIdx.x / P::R;
+    if (y0 + rr < ny) {
+        float2 *const dst = F + ((long long)z * P::NXH + kx0) * ny + y0 + rr;
+        const float2 *const src = buf + rr * P::LP + kx0;
+#pragma unroll
+        for (int j = 0; j < NJ; j++)
+            if (kx0 + j * KS < P::NXH) dst[(long long)j * KS * ny] = src[j * KS];
     }
 }
 
+// R rows y0 .. y0 + R - 1 of plane z from the kx-major half spectrum:
+// complex-to-real transform along x into Y (the gather streams through L2).
 template <int LOG2N>
-__global__ void __launch_bounds__(Rows<LOG2N>::THREADS, 4)
-    xpass_c2r_kernel(const float2 *__restrict__ F, int ny, float *__restrict__ Y, int pitch,
-                     const float2 *__restrict__ tw)
+__device__ __forceinline__ void c2r_rows(const float2 *__restrict__ F, int ny, float *__restrict__ Y, int pitch,
+                                         const float2 *tws, float2 *buf, int z, int y0)
 {
     using P = Rows<LOG2N>;
-    extern __shared__ __align__(16) float2 xsm[];
-    float2 *const buf = xsm;
-    float2 *const tws = xsm + P::R * P::LP;
-    for (int i = threadIdx.x; i < P::TW; i += P::THREADS) tws[i] = tw[i];
-    const int z = blockIdx.y, y0 = blockIdx.x * P::R;
     const float2 *const Fz = F + (long long)z * P::NXH * ny;
-    // kx-major runs of R rows; all of a thread's loads issued before its stores
-    constexpr int NG = (P::R * P::NXH + P::THREADS - 1) / P::THREADS;
-    float2 g[NG];
+    // kx-major runs of R rows, thread (rr, kx0) taking kx = kx0 + j KS of row
+    // rr; all of a thread's loads issued before its stores
+    constexpr int KS = P::THREADS / P::R, NG = (P::NXH + KS - 1) / KS;
+    {
+        const int rr = threadIdx.x % P::R, kx0 = threadIdx.x / P::R;
+        const bool in = y0 + rr < ny;
+        const float2 *const src = Fz + (long long)kx0 * ny + y0 + rr;
+        float2 g[NG];
 #pragma unroll
-    for (int j = 0; j < NG; j++) {
-        const int idx = threadIdx.x + j * P::THREADS;
-        const int rr = idx % P::R, kx = idx / P::R, yy = y0 + rr;
-        g[j] = (idx < P::R * P::NXH && yy < ny) ? Fz[(long long)kx * ny + yy] : make_float2(0.f, 0.f);
-    }
+        for (int j = 0; j < NG; j++)
+            g[j] = (in && kx0 + j * KS < P::NXH) ? __ldcg(src + (long long)j * KS * ny) : make_float2(0.f, 0.f);
+        float2 *const dst = buf + rr * P::LP + kx0;
 #pragma unroll
-    for (int j = 0; j < NG; j++) {
-        const int idx = threadIdx.x + j * P::THREADS;
-        if (idx < P::R * P::NXH) buf[(idx % P::R) * P::LP + idx / P::R] = g[j];
+        for (int j = 0; j < NG; j++)
+            if (kx0 + j * KS < P::NXH) dst[j * KS] = g[j];
     }
     __syncthreads();
     const int t = threadIdx.x % P::T, r = threadIdx.x / P::T, y = y0 + r;
@@ -243,6 +292,33 @@ __global__ void __launch_bounds__(Rows<LOG2N>::THREADS, 4)
 #pragma unroll
         for (int i = 0; i < 8; i++) row[t + i * P::T] = v[i];
     }
+}
+
+template <int LOG2N>
+__global__ void __launch_bounds__(Rows<LOG2N>::THREADS, 4)
+    xpass_r2c_kernel(const float *__restrict__ Y, int pitch, int ny, float2 *__restrict__ F,
+                     const float2 *__restrict__ tw)
+{
+    using P = Rows<LOG2N>;
+    extern __shared__ __align__(16) float2 xsm[];
+    float2 *const buf = xsm;
+    float2 *const tws = xsm + P::R * P::LP;
+    for (int i = threadIdx.x; i < P::TW; i += P::THREADS) tws[i] = tw[i];
+    __syncthreads();
+    r2c_rows<LOG2N>(Y, pitch, ny, F, tws, buf, blockIdx.y, blockIdx.x * P::R);
+}
+
+template <int LOG2N>
+__global__ void __launch_bounds__(Rows<LOG2N>::THREADS, 4)
+    xpass_c2r_kernel(const float2 *__restrict__ F, int ny, float *__restrict__ Y, int pitch,
+                     const float2 *__restrict__ tw)
+{
+    using P = Rows<LOG2N>;
+    extern __shared__ __align__(16) float2 xsm[];
+    float2 *const buf = xsm;
+    float2 *const tws = xsm + P::R * P::LP;
+    for (int i = threadIdx.x; i < P::TW; i += P::THREADS) tws[i] = tw[i];  // c2r_rows syncs before reading
+    c2r_rows<LOG2N>(F, ny, Y, pitch, tws, buf, blockIdx.y, blockIdx.x * P::R);
 }
 
 // out[z][c][r] = in[z][r][c] for planes of rows x cols elements.
@@ -299,6 +375,30 @@ cudaError_t transpose_planes(const T *in, T *out, int rows, int cols, int nz, cu
     return cudaGetLastError();
 }
 
+// Per-stage tables of a length-L row transform in the order row_fft reads
+// them, each entry w_L^e evaluated directly in double precision.
+void append_stage_tables(int L, std::vector<float2> *table)
+{
+    const double pi = 3.14159265358979323846;
+    auto w = [&](long long e) {
+        const double a = -2.0 * pi * (double)(e % L) / (double)L;
+        return make_float2((float)std::cos(a), (float)std::sin(a));
+    };
+    int log2l = 0;
+    while ((1 << log2l) < L) log2l++;
+    const int ns8 = log2l / 3, rem = log2l % 3;
+    for (int s = 1; s < ns8; s++) {
+        const int Ns = 1 << (3 * s), step = L / (8 * Ns);
+        for (int q = 1; q < 8; q++)
+            for (int k = 0; k < Ns; k++) table->push_back(w((long long)q * k * step));
+    }
+    if (rem == 1)
+        for (int j = 0; j < L / 2; j++) table->push_back(w(j));
+    else if (rem == 2)
+        for (int p = 1; p <= 3; p++)
+            for (int j = 0; j < L / 4; j++) table->push_back(w((long long)p * j));
+}
+
 }  // namespace
 
 bool xpass_supported(int nx, int nz) { return (nx == 128 || nx == 256 || nx == 512 || nx == 1024) && nz <= 65535; }
@@ -306,29 +406,14 @@ bool xpass_supported(int nx, int nz) { return (nx == 128 || nx == 256 || nx == 5
 void xpass_twiddles(int nx, std::vector<float2> *table)
 {
     // w_n^m for m < n (the untwist), then the row transform's stage tables
-    // (length L = n/2) in the order row_fft reads them, each entry w_L^e
-    // evaluated directly in double precision
+    // (length L = n/2)
     const double pi = 3.14159265358979323846;
-    auto w = [&](long long e, long long len) {
-        const double a = -2.0 * pi * (double)(e % len) / (double)len;
-        return make_float2((float)std::cos(a), (float)std::sin(a));
-    };
     table->clear();
-    for (int m = 0; m < nx; m++) table->push_back(w(m, nx));
-    const int L = nx / 2;
-    int log2l = 0;
-    while ((1 << log2l) < L) log2l++;
-    const int ns8 = log2l / 3, rem = log2l % 3;
-    for (int s = 1; s < ns8; s++) {
-        const int Ns = 1 << (3 * s), step = L / (8 * Ns);
-        for (int q = 1; q < 8; q++)
-            for (int k = 0; k < Ns; k++) table->push_back(w((long long)q * k * step, L));
+    for (int m = 0; m < nx; m++) {
+        const double a = -2.0 * pi * (double)m / (double)nx;
+        table->push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
     }
-    if (rem == 1)
-        for (int j = 0; j < L / 2; j++) table->push_back(w(j, L));
-    else if (rem == 2)
-        for (int p = 1; p <= 3; p++)
-            for (int j = 0; j < L / 4; j++) table->push_back(w((long long)p * j, L));
+    append_stage_tables(nx / 2, table);
 }
 
 cudaError_t launch_xpass_r2c(int nx, const float *Y, int pitch, int ny, int nz, float2 *F, const float2 *tw,
