@@ -97,37 +97,48 @@ __global__ void spec_max_kernel(const float *N, long long n, unsigned int *out)
 }
 
 // Half-spectrum sum of 1/2 |Y - sqrt(N) F scale|^2, coefficients 0 < h < nx/2
-// counted twice. A block walks whole rows (no index division per element);
-// sqrt(N) is the float estimate refined by one Newton step in double,
-// s <- s + r (N - s^2) / 2 with r = 1/sqrt(N) in float, which leaves a
-// relative error of the order of the float estimate's squared (the data
-// term's residual cancels Y against sqrt(N) F scale, so sqrt(N) needs more
-// than float precision, and a double square root per coefficient would
-// dominate the pass on this GPU's narrow FP64 pipe).
+// counted twice. A block walks whole rows (no index division per element).
+// The data term's residual cancels Y against sqrt(N) F scale, so m =
+// sqrt(N) scale is carried as a pair of floats (m_hi + m_lo, about 44
+// significant bits) and the product m F is split exactly by fused
+// multiply-adds (Dekker's two-product); the residual
+// r = (Y - m_hi F) - (m_lo F + the product's rounding) is then accurate to
+// float rounding of r itself, as a double evaluation would be, without the
+// double-precision pipe (narrow on this GPU). sqrt(N): s0 = N rsqrt(N) in
+// float and one Newton correction (N - s0^2) / (2 s0), its numerator formed
+// by one fused multiply-add. Per thread the squares are summed compensated
+// (Kahan) in float; blocks reduce in double.
 __global__ void spec_value_kernel(const float2 *F, const float2 *Y, const float *N, int nz, int ny, int nx,
                                   float scale, double *partials)
 {
     __shared__ double red[32];
     const int nxh = nx / 2 + 1;
     const long long rows = (long long)nz * ny;
-    double acc = 0.0;
+    float sum = 0.f, comp = 0.f;
     for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
         const long long o = r * nxh;
         for (int h = threadIdx.x; h < nxh; h += blockDim.x) {
             const float nf = N[o + h];
-            double sq = 0.0;
+            float mh = 0.f, ml = 0.f;
             if (nf > 0.f) {
                 const float rs = rsqrtf(nf);
-                const double nd = nf, s0 = (double)nf * rs;
-                sq = s0 + 0.5 * (double)rs * (nd - s0 * s0);
+                const float s0 = nf * rs;
+                const float sl = 0.5f * fmaf(-s0, s0, nf) * rs;  // sqrt(N) ~ s0 + sl
+                mh = s0 * scale;
+                ml = fmaf(s0, scale, -mh) + sl * scale;
             }
-            const double m = sq * scale;
             const float2 f = F[o + h], y = Y[o + h];
-            const double rx = (double)y.x - m * f.x, ry = (double)y.y - m * f.y;
-            const double wgt = (h == 0 || (nx % 2 == 0 && h == nx / 2)) ? 0.5 : 1.0;
-            acc += wgt * (rx * rx + ry * ry);
+            const float px = mh * f.x, py = mh * f.y;
+            const float rx = (y.x - px) - (fmaf(mh, f.x, -px) + ml * f.x);
+            const float ry = (y.y - py) - (fmaf(mh, f.y, -py) + ml * f.y);
+            const float wgt = (h == 0 || (nx % 2 == 0 && h == nx / 2)) ? 0.5f : 1.0f;
+            const float v = wgt * fmaf(rx, rx, ry * ry) - comp;
+            const float t = sum + v;
+            comp = (t - sum) - v;
+            sum = t;
         }
     }
+    double acc = (double)sum - (double)comp;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -203,13 +214,14 @@ __global__ void sum_scales_kernel(const double *partials, int nblocks, double *o
     }
 }
 
+// One warp, fixed order: lane l sums partials l, l + 32, ... (its loads in
+// flight together), then a fixed tree over the lanes.
 __global__ void sum_partials_kernel(const double *partials, int n, double *out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < n; i++) s += partials[i];
-        *out = s;
-    }
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) s += partials[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *out = s;
 }
 
 int grid_for(long long n)

@@ -347,6 +347,22 @@ cudaError_t xpass(bool forward, const float *Yin, float *Yout, int pitch, int ny
 {
     using P = Rows<LOG2N>;
     const dim3 grid((ny + P::R - 1) / P::R, nz);
+    if constexpr (P::SMEM > 48 * 1024) {
+        // above the default dynamic shared-memory limit: opt in once per device
+        static bool opted[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!opted[dev]) {
+            e = cudaFuncSetAttribute(xpass_r2c_kernel<LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(xpass_c2r_kernel<LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)P::SMEM);
+            if (e != cudaSuccess) return e;
+            opted[dev] = true;
+        }
+    }
     if (forward)
         xpass_r2c_kernel<LOG2N><<<grid, P::THREADS, P::SMEM, s>>>(Yin, pitch, ny, Fout, tw);
     else
