@@ -344,6 +344,14 @@ spg_status spg_step_bound(spg_ctx *ctx, int vol, double out[2]);
  * reports that L and tau. Errors: SPG_EINVAL, SPG_ENOTREADY. Synchronises. */
 spg_status spg_set_step_bound(spg_ctx *ctx, int vol, double max_w, double max_omtv);
 
+/* Replace volume `vol`'s weights lambda_l1 and lambda_tv of the l1 and TV
+ * terms (Sec. 2.1, Eq. 11), e.g. between solves that learn them. The step
+ * tau = 1/L depends on lambda_tv, so the context then needs spg_reweight
+ * before it iterates or differentiates again (SPG_ENOTREADY until then).
+ * Values as in spg_create: finite and >= 0, else SPG_EINVAL with nothing
+ * changed. Synchronises. */
+spg_status spg_set_lambdas(spg_ctx *ctx, int vol, float lambda_l1, float lambda_tv);
+
 /* Copy planes [z0, z0 + n) of volume `vol`'s current iterate x_k (into x) and
  * of its pair (into pair: the increment d_k with SPG_STORE_DELTA, x_{k-1}
  * with SPG_STORE_PREV) out of the context, or into it. x and pair (either may
@@ -377,13 +385,17 @@ spg_status spg_set_state(spg_ctx *ctx, const void *blob, size_t size);
  * g_scalars = {dLoss/dlambda_l1, dLoss/dlambda_tv}. Recomputes the forward
  * iterates from checkpoints of (x_k, x_{k-1}) taken every `ckpt_every`
  * iterations (0 = 10). The context's own iterate is left unchanged.
- * Synchronises. */
+ * Working memory (2 ceil(K / ckpt_every) checkpoint volumes, ckpt_every + 2
+ * segment volumes and 15 more) comes from a workspace the context owns: it
+ * is allocated on first use, grown when a call needs more and kept until
+ * spg_destroy, so repeated calls allocate nothing. Synchronises. */
 spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *gw,
                         double g_scalars[2], int ckpt_every);
 
 /* Run the forward part of spg_backward: K iterations from the current
  * iterate with fixed weights and tau, writing x_K to `xK` (float32 volume);
- * the context's iterate is left unchanged. Synchronises. */
+ * the context's iterate is left unchanged. Its three iterate buffers come
+ * from the same context-owned workspace as spg_backward's. Synchronises. */
 spg_status spg_unrolled(spg_ctx *ctx, int K, float *xK);
 
 /* Self-test of the bounded device-side wait used by the fused step: launches

@@ -139,6 +139,10 @@ struct spg_ctx {
     long long nhalf = 0;
 
     cudaGraphExec_t gexec = nullptr;
+    // workspace of spg_unrolled and spg_backward: one device buffer, grown
+    // when a call needs more and kept until spg_destroy
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
     long long launches = 0;
     std::string err = "no error";
 
@@ -199,6 +203,7 @@ void free_all(spg_ctx *c)
                   c->vol_out_d, c->maxw_d, c->rstats_d};
     for (void *p : ps)
         if (p) cudaFree(p);
+    if (c->ws) cudaFree(c->ws);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -723,6 +728,43 @@ struct Scratch {
     }
 };
 
+// The context's workspace, at least `bytes` long. Calls on a context are
+// ordered on its stream, so a call may reuse what an earlier one left there;
+// growing it frees the old buffer first (cudaFree waits for the device).
+cudaError_t workspace(spg_ctx *ctx, size_t bytes, char **p)
+{
+    if (ctx->ws_bytes < bytes) {
+        if (ctx->ws) {
+            cudaError_t e = cudaFree(ctx->ws);
+            ctx->ws = nullptr;
+            ctx->ws_bytes = 0;
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = dalloc(&ctx->ws, bytes);
+        if (e != cudaSuccess) {
+            ctx->ws = nullptr;
+            return e;
+        }
+        ctx->ws_bytes = bytes;
+    }
+    *p = static_cast<char *>(ctx->ws);
+    return cudaSuccess;
+}
+
+// Consecutive 256-byte aligned pieces of a workspace; with base null it only
+// counts the bytes (the first pass of a two-pass sizing).
+struct Carve {
+    char *base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t bytes)
+    {
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += (bytes + 255) / 256 * 256;
+        return p;
+    }
+};
+
 std::vector<float> beta_table_host(const spg_ctx *ctx, int K)
 {
     std::vector<float> b(std::max(K, 1));
@@ -749,7 +791,6 @@ struct Sweep {
     };
     spg_ctx *ctx;
     StepVariant v;
-    Scratch sc;
     DevState *st = nullptr;
     VolDesc *vol = nullptr;
     TmapSet *tm = nullptr;
@@ -759,13 +800,19 @@ struct Sweep {
 
     explicit Sweep(spg_ctx *c) : ctx(c), v(c->var) { v.xd = false; }
     void add(float *xk, float *xkm1, float *xout, int k) { plan.push_back({xk, xkm1, xout, k}); }
-    cudaError_t upload()
+    // device state, descriptor and tensor maps of n planned steps, from a workspace
+    static void carve(Carve &cv, size_t n, DevState **st, VolDesc **vol, TmapSet **tm)
+    {
+        *st = cv.take<DevState>(sizeof(DevState));
+        *vol = cv.take<VolDesc>(sizeof(VolDesc));
+        *tm = cv.take<TmapSet>(std::max<size_t>(1, n) * sizeof(TmapSet));
+    }
+    // cv: where the step state lives (carved after what cv already holds)
+    cudaError_t upload(Carve &cv)
     {
         int occ = 0;
         cudaError_t e = step_configure(v, &occ);
-        if (e == cudaSuccess) e = sc.get(&st, sizeof(DevState));
-        if (e == cudaSuccess) e = sc.get(&vol, sizeof(VolDesc));
-        if (e == cudaSuccess) e = sc.get(&tm, std::max<size_t>(1, plan.size()) * sizeof(TmapSet));
+        carve(cv, plan.size(), &st, &vol, &tm);
         if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(DevState), ctx->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(vol, ctx->vols_d, sizeof(VolDesc), cudaMemcpyDeviceToDevice, ctx->stream);
@@ -1465,6 +1512,30 @@ spg_status spg_step_bound(spg_ctx *ctx, int vol, double out[2])
     return SPG_OK;
 }
 
+spg_status spg_set_lambdas(spg_ctx *ctx, int vol, float lambda_l1, float lambda_tv)
+{
+    SPG_TRACE();
+    if (!ctx) return fail(nullptr, SPG_EINVAL, "null context");
+    if (vol < 0 || vol >= ctx->nvol || !std::isfinite(lambda_l1) || !std::isfinite(lambda_tv) ||
+        !(lambda_l1 >= 0.f) || !(lambda_tv >= 0.f))
+        return fail(ctx, SPG_EINVAL, "spg_set_lambdas: bad arguments");
+    // only these two fields of the device descriptor: tau and the
+    // extrapolation index there belong to the device
+    const float l[2] = {lambda_l1, lambda_tv};
+    static_assert(offsetof(VolDesc, lambda_tv) == offsetof(VolDesc, lambda_l1) + sizeof(float),
+                  "lambda_l1 and lambda_tv are adjacent");
+    CK(cudaMemcpyAsync(reinterpret_cast<char *>(ctx->vols_d + vol) + offsetof(VolDesc, lambda_l1), l, sizeof(l),
+                       cudaMemcpyHostToDevice, ctx->stream),
+       "write lambdas");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    ctx->vols_h[vol].lambda_l1 = lambda_l1;
+    ctx->vols_h[vol].lambda_tv = lambda_tv;
+    ctx->vp[vol].lambda_l1 = lambda_l1;
+    ctx->vp[vol].lambda_tv = lambda_tv;
+    ctx->reweighted = false;  // tau depends on lambda_tv
+    return SPG_OK;
+}
+
 spg_status spg_set_step_bound(spg_ctx *ctx, int vol, double max_w, double max_omtv)
 {
     SPG_TRACE();
@@ -1695,9 +1766,19 @@ spg_status spg_unrolled(spg_ctx *ctx, int K, float *xK)
     if (K > ctx->max_iters) return fail(ctx, SPG_EINVAL, "spg_unrolled: K above max_iters_per_round");
     const VolDesc &d = ctx->vols_h[0];
     const size_t vb = (size_t)ctx->total * 4;
-    Scratch sc;
+    // three rotating iterate buffers, then the steps' state
+    Carve cv;
+    {
+        Carve size;
+        for (int q = 0; q < 3; q++) size.take<float>(vb);
+        DevState *s0;
+        VolDesc *v0;
+        TmapSet *t0;
+        Sweep::carve(size, (size_t)K, &s0, &v0, &t0);
+        CK(workspace(ctx, size.off, &cv.base), "alloc workspace");
+    }
     float *buf[3];
-    for (int q = 0; q < 3; q++) CK(sc.get(&buf[q], vb), "alloc");
+    for (int q = 0; q < 3; q++) buf[q] = cv.take<float>(vb);
     CK(cudaMemcpyAsync(buf[0], ctx->X[ctx->cur()], vb, cudaMemcpyDeviceToDevice, ctx->stream), "copy x0");
     CK(cudaMemcpyAsync(buf[2], buf[0], vb, cudaMemcpyDeviceToDevice, ctx->stream), "copy x0");
     Sweep sw(ctx);
@@ -1706,7 +1787,7 @@ spg_status spg_unrolled(spg_ctx *ctx, int K, float *xK)
         sw.add(buf[c], buf[(c + 2) % 3], buf[(c + 1) % 3], k);
         c = (c + 1) % 3;
     }
-    CK(sw.upload(), "plan the unrolled steps");
+    CK(sw.upload(cv), "plan the unrolled steps");
     for (int k = 0; k < K; k++) CK(sw.launch(), "fused step");
     spg_status s = sw.status();
     if (s != SPG_OK) return fail(ctx, s, "spg_unrolled: a fused step failed");
@@ -1729,20 +1810,36 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
     const VolDesc &d = ctx->vols_h[0];
     const size_t vb = (size_t)ctx->total * 4;
     const int nck = (K + C - 1) / C;  // checkpoints at k = 0, C, 2C, ... (< K)
-    Scratch sc;
+    // one forward sweep plus, per segment, the recomputation of all but its last step
+    const size_t nsteps = (size_t)K + (size_t)(K - nck);
+    // workspace: checkpoints, segment, adjoint volumes, scalar partials, the steps' state
     float *ck = nullptr, *seg = nullptr, *ga[3], *m = nullptr, *accb = nullptr, *accw = nullptr;
+    float *fG = nullptr, *fP = nullptr, *fH = nullptr;  // 3-vector fields of the adjoint passes
     double *pp = nullptr;
-    CK(sc.get(&ck, vb * 2 * nck), "alloc checkpoints");
-    CK(sc.get(&seg, vb * (C + 2)), "alloc segment");
-    for (int q = 0; q < 3; q++) CK(sc.get(&ga[q], vb), "alloc adjoint");
-    CK(sc.get(&m, vb), "alloc");
-    CK(sc.get(&accb, vb), "alloc");
-    CK(sc.get(&accw, vb), "alloc");
-    CK(sc.get(&pp, (size_t)K * d.nz * AUX_SEG * 4 * sizeof(double)), "alloc scalar partials");
-    float *fG = nullptr, *fP = nullptr, *fH = nullptr;  // 3-vector scratch fields of the adjoint passes
-    CK(sc.get(&fG, vb * 3), "alloc");
-    CK(sc.get(&fP, vb * 3), "alloc");
-    CK(sc.get(&fH, vb * 3), "alloc");
+    Carve cv;
+    for (int pass = 0; pass < 2; pass++) {
+        Carve t;
+        t.base = cv.base;
+        ck = t.take<float>(vb * 2 * nck);
+        seg = t.take<float>(vb * (C + 2));
+        for (int q = 0; q < 3; q++) ga[q] = t.take<float>(vb);
+        m = t.take<float>(vb);
+        accb = t.take<float>(vb);
+        accw = t.take<float>(vb);
+        fG = t.take<float>(vb * 3);
+        fP = t.take<float>(vb * 3);
+        fH = t.take<float>(vb * 3);
+        pp = t.take<double>((size_t)K * d.nz * AUX_SEG * 4 * sizeof(double));
+        if (pass == 0) {
+            DevState *s0;
+            VolDesc *v0;
+            TmapSet *t0;
+            Sweep::carve(t, nsteps, &s0, &v0, &t0);
+            CK(workspace(ctx, t.off, &cv.base), "alloc workspace");
+        } else {
+            cv = t;  // the steps' state follows
+        }
+    }
     const auto beta = beta_table_host(ctx, K);
     auto vol_at = [&](float *base, int i) { return base + (size_t)i * ctx->total; };
 
@@ -1767,7 +1864,8 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
             }
         }
     }
-    CK(sw.upload(), "plan the forward steps");
+    if (sw.plan.size() != nsteps) return fail(ctx, SPG_EINVAL, "spg_backward: step plan size mismatch");
+    CK(sw.upload(cv), "plan the forward steps");
     // forward sweep, keeping (x_k, x_{k-1}) at every checkpoint
     {
         CK(cudaMemcpyAsync(b3[0], ctx->X[ctx->cur()], vb, cudaMemcpyDeviceToDevice, ctx->stream), "copy x0");

@@ -42,7 +42,7 @@ EXPORTS = ["spg_create", "spg_create_batch", "spg_set_data", "spg_set_x", "spg_g
            "spg_fsc", "spg_fsc_last_error", "spg_set_data_fourier", "spg_backproject",
            "spg_backproject_last_error", "spg_grid_create", "spg_grid_add", "spg_grid_finish", "spg_grid_reset",
            "spg_grid_count", "spg_grid_last_error", "spg_grid_destroy", "spg_set_halo", "spg_step_bound",
-           "spg_set_step_bound", "spg_get_planes", "spg_set_planes"]
+           "spg_set_step_bound", "spg_get_planes", "spg_set_planes", "spg_set_lambdas"]
 
 
 class SPGError(RuntimeError):
@@ -142,6 +142,7 @@ def load():
             "spg_set_step_bound": (I, [P, I, D, D]),
             "spg_get_planes": (I, [P, I, I, I, V, V]),
             "spg_set_planes": (I, [P, I, I, I, V, V]),
+            "spg_set_lambdas": (I, [P, I, ctypes.c_float, ctypes.c_float]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -398,6 +399,10 @@ def spg_set_step_bound(h, vol, max_w, max_omtv):
     _check(load().spg_set_step_bound(h, int(vol), float(max_w), float(max_omtv)), h)
 
 
+def spg_set_lambdas(h, vol, lambda_l1, lambda_tv):
+    _check(load().spg_set_lambdas(h, int(vol), float(lambda_l1), float(lambda_tv)), h)
+
+
 def _opt_ptr(a):
     return (None, None) if a is None else _ptr(a)
 
@@ -555,6 +560,9 @@ class SPG:
     def set_x(self, vol, x):
         spg_set_x(self.handle, vol, x)
 
+    def set_lambdas(self, vol, lambda_l1, lambda_tv):
+        spg_set_lambdas(self.handle, vol, lambda_l1, lambda_tv)
+
     def set_data_fourier(self, vol, y_half, N_half):
         spg_set_data_fourier(self.handle, vol, y_half, N_half)
 
@@ -651,13 +659,43 @@ class SPG:
         self.close()
 
 
+# Idle contexts of UnrolledSPG, by (shape, mu, eps, eps_tv, momentum, device,
+# stream). A forward takes one (or creates one) and re-sets its weights and
+# data; its backward hands it back. A loop of forward/backward calls thus
+# creates one context, whose workspace the later calls reuse. At most two
+# idle contexts are kept per key.
+_UNROLLED_POOL = {}
+_UNROLLED_LOCK = threading.Lock()
+
+
 def _unrolled_ctx(b, w, lambda_l1, lambda_tv, mu, eps, eps_tv, momentum):
-    p = dict(shape=tuple(b.shape), lambda_l1=float(lambda_l1), lambda_tv=float(lambda_tv), mu=mu, eps=eps,
-             eps_tv=eps_tv)
-    s = SPG(p, momentum=momentum, hist_every=1 << 30)
+    import torch
+    stream = torch.cuda.current_stream(b.device).cuda_stream
+    key = (tuple(b.shape), float(mu), float(eps), float(eps_tv), momentum, b.device.index, stream)
+    with _UNROLLED_LOCK:
+        idle = _UNROLLED_POOL.get(key)
+        s = idle.pop() if idle else None
+    if s is None:
+        p = dict(shape=tuple(b.shape), lambda_l1=float(lambda_l1), lambda_tv=float(lambda_tv), mu=mu, eps=eps,
+                 eps_tv=eps_tv)
+        s = SPG(p, momentum=momentum, hist_every=1 << 30, stream=stream)
+    else:
+        s.set_lambdas(0, lambda_l1, lambda_tv)
+    s.pool_key = key
+    # the context's own iterate stays x_0 = 0: spg_unrolled and spg_backward
+    # work on copies
     s.set_data(0, b.detach().contiguous(), w.detach().contiguous())
     s.reweight()  # from x_0 = 0: om1 = omtv = 1, tau = 1/L
     return s
+
+
+def _unrolled_release(s):
+    with _UNROLLED_LOCK:
+        idle = _UNROLLED_POOL.setdefault(s.pool_key, [])
+        if len(idle) < 2:
+            idle.append(s)
+            return
+    s.close()
 
 
 class UnrolledSPG:
@@ -682,10 +720,17 @@ class UnrolledSPG:
             @staticmethod
             def backward(fctx, gx):
                 s = fctx.solver
+                if s is None:
+                    raise RuntimeError("UnrolledSPG: one backward per forward")
+                fctx.solver = None
                 gb = torch.empty_like(gx)
                 gw = torch.empty_like(gx)
-                gs = spg_backward(s.handle, K, gx.contiguous(), gb, gw, ckpt_every)
-                s.close()
+                try:
+                    gs = spg_backward(s.handle, K, gx.contiguous(), gb, gw, ckpt_every)
+                except BaseException:
+                    s.close()
+                    raise
+                _unrolled_release(s)
                 l1_, tv_ = fctx.scalar_like
                 return (gb, gw, torch.tensor(gs[0], dtype=l1_.dtype, device=l1_.device),
                         torch.tensor(gs[1], dtype=tv_.dtype, device=tv_.device))

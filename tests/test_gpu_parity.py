@@ -474,6 +474,13 @@ def test_adjoint_matches_oracle(shape):
     gb = torch.empty_like(b)
     gw = torch.empty_like(b)
     gs = spg.spg_backward(s.handle, K, gx.contiguous(), gb, gw, ckpt_every=5)
+    # again on the same context, whose workspace is now carved for other
+    # checkpoint intervals: the recomputed iterates are the same, so are the
+    # gradients, bit for bit
+    for ck in (3, 12, 1):
+        gb2, gw2 = torch.empty_like(b), torch.empty_like(b)
+        gs2 = spg.spg_backward(s.handle, K, gx.contiguous(), gb2, gw2, ckpt_every=ck)
+        assert torch.equal(gb2, gb) and torch.equal(gw2, gw) and list(gs2) == list(gs)
     s.close()
     p = oparams(shape, hyper)
     x0 = np.zeros(shape)
@@ -549,6 +556,68 @@ def test_autograd_function(K, ckpt):
     x2 = spg.UnrolledSPG.apply(b2, w2, hyper["lambda_l1"], hyper["lambda_tv"], K, mu=hyper["mu"], ckpt_every=ckpt)
     (-3 * ((x2 - torch.from_numpy(vol.phantom).cuda()) ** 2).sum()).backward()
     assert rel_l2(b2.grad.cpu().numpy(), -3 * rb) <= 1e-4
+
+
+def test_unrolled_context_reuse_with_new_lambdas():
+    """UnrolledSPG hands its context back after the backward, and the next
+    forward of the same shape re-sets lambda_l1, lambda_tv and the data on
+    it (spg_set_lambdas, spg_set_data, spg_reweight). Three calls in a row
+    with other weights and other data each match the oracle: x_K to 1e-6 and
+    the four gradients to 1e-4."""
+    shape, K, ckpt = (9, 14, 20), 12, 5
+    for seed, l1v, tvv in [(81, 0.05, 0.1), (82, 0.09, 0.16), (83, 0.02, 0.05)]:
+        vol = synth.make_volume(shape, blobs=5, radius=3, seed=seed)
+        hyper = dict(HYPER, mu=0.02, lambda_l1=l1v, lambda_tv=tvv)
+        b = torch.from_numpy(vol.b).cuda().requires_grad_(True)
+        w = torch.from_numpy(vol.w).cuda().requires_grad_(True)
+        l1 = torch.tensor(l1v, dtype=torch.float64, requires_grad=True)
+        tv = torch.tensor(tvv, dtype=torch.float64, requires_grad=True)
+        x = spg.UnrolledSPG.apply(b, w, l1, tv, K, mu=hyper["mu"], ckpt_every=ckpt)
+        ((x - torch.from_numpy(vol.phantom).cuda()) ** 2).sum().backward()
+        p = oparams(shape, hyper)
+        tau = 1.0 / oracle.lipschitz(vol.w, 1.0, p)
+        x0 = np.zeros(shape)
+        ref_xK = oracle.unrolled(vol.b, vol.w, None, None, tau, K, x0, p)
+        assert rel_l2(x.detach().cpu().numpy(), ref_xK) <= 1e-6
+        rb, rw, rs = oracle.backward(vol.b, vol.w, None, None, tau, K, x0, 2 * (ref_xK - vol.phantom), p)
+        assert rel_l2(b.grad.cpu().numpy(), rb) <= 1e-4
+        assert rel_l2(w.grad.cpu().numpy(), rw) <= 1e-4
+        assert float(l1.grad) == pytest.approx(rs[0], rel=1e-4)
+        assert float(tv.grad) == pytest.approx(rs[1], rel=1e-4)
+
+
+def test_set_lambdas_matches_a_fresh_context():
+    """spg_set_lambdas: invalid weights are rejected with nothing changed;
+    valid ones leave the context not ready until spg_reweight; after it the
+    solve is bitwise that of a context created with those weights."""
+    shape = (12, 20, 36)
+    vol = synth.make_volume(shape, blobs=6, radius=4, seed=84)
+    bd = torch.from_numpy(vol.b).cuda()
+    wd = torch.from_numpy(vol.w).cuda()
+    s = make_solver(shape)
+    s.set_data(0, bd, wd)
+    s.reweight()
+    s.iterate(5)
+    for bad in [(-1.0, 0.1), (0.05, float("nan")), (float("inf"), 0.1)]:
+        with pytest.raises(spg.SPGError, match="SPG_EINVAL"):
+            s.set_lambdas(0, *bad)
+    with pytest.raises(spg.SPGError, match="SPG_EINVAL"):
+        s.set_lambdas(1, 0.05, 0.1)
+    s.iterate(1)  # still ready: nothing changed
+    new = dict(HYPER, lambda_l1=0.08, lambda_tv=0.2)
+    s.set_lambdas(0, new["lambda_l1"], new["lambda_tv"])
+    with pytest.raises(spg.SPGError, match="SPG_ENOTREADY"):
+        s.iterate(1)
+    s.set_x(0, torch.zeros_like(bd))
+    s.reweight()
+    s.iterate(20)
+    f = make_solver(shape, new)
+    f.set_data(0, bd, wd)
+    f.reweight()
+    f.iterate(20)
+    np.testing.assert_array_equal(s.get_x(0).cpu().numpy(), f.get_x(0).cpu().numpy())
+    np.testing.assert_array_equal(s.round_stats(0), f.round_stats(0))
+    np.testing.assert_array_equal(s.objective(0), f.objective(0))
 
 
 def test_autotune_keeps_the_solve():
