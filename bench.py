@@ -874,11 +874,12 @@ def measure_fourier(args):
     s.close()
     nvox = shape[0] * shape[1] * shape[2]
     peaks, kind = measured_peaks()
-    # minimal bytes per voxel (a half-spectrum coefficient is half a voxel):
-    # forward transform of y_k (4 + 4), residual spectrum N F / V - C
-    # (4 + 2 + 4 + 4), inverse transform (4 + 4), fused step without w that
-    # also writes the next y (28 + 4 B)
-    bpv = 8 + 14 + 8 + 32
+    # bytes per voxel (a half-spectrum coefficient is half a voxel): forward
+    # transform of y_k = x_k + beta d_k, formed from x_k and d_k as the row
+    # pass reads them (8 + 4), residual spectrum N F / V - C (4 + 2 + 4 + 4),
+    # inverse transform (4 + 4), fused step without w (x_k, d_k, the data
+    # gradient, om1, omtv read, x_{k+1} and d_{k+1} written: 28 B)
+    bpv = 12 + 14 + 8 + 28
     achieved = bpv * nvox * args.steps / (ms / 1e3) / 1e9
     return {"metric": "Gvoxel-iter/s, Fourier-domain data term (Eq. 31), %dx%dx%d" % shape,
             "value": nvox * args.steps / (ms / 1e3) / 1e9, "unit": UNIT, "steps": args.steps,

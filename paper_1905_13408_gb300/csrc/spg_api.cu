@@ -502,7 +502,9 @@ StepParams step_params(const spg_ctx *c)
     p.hist_every = c->hist_every;
     p.restart = c->opt.restart ? 1 : 0;
     p.fourier = c->fourier ? 1 : 0;
-    p.ybuf = c->fourier ? c->Ybuf : nullptr;
+    // the library's transforms read y_{k+1} from a buffer the step writes; the
+    // own row pass forms it from x_{k+1} and d_{k+1} as it reads them
+    p.ybuf = (c->fourier && !c->xown) ? c->Ybuf : nullptr;
     p.timeout_ns = kTimeoutNs;
     return p;
 }
@@ -599,7 +601,8 @@ cudaError_t issue_iteration(spg_ctx *ctx, const StepParams &p)
         const bool anc = ctx->gamma_f > 0.f;
         if (ctx->xown) {
             cufftComplex *Fc = reinterpret_cast<cufftComplex *>(ctx->Fh);
-            e = launch_xpass_r2c(d.nx, ctx->Ybuf, d.pitch, d.ny, d.nz, ctx->Fh, ctx->xtw, ctx->stream);
+            e = launch_xpass_r2c_extrap(d.nx, ctx->st_d, ctx->vols_d, ctx->beta_d, ctx->X, d.pitch, d.ny, d.nz,
+                                        ctx->Fh, ctx->xtw, ctx->stream);
             if (e != cudaSuccess) return e;
             if (cf.exec_c2c(ctx->pyc, Fc, Fc, CUFFT_FORWARD) != CUFFT_SUCCESS) return cudaErrorUnknown;
             if (ctx->zmapsx_ok[anc ? 1 : 0])
@@ -661,7 +664,7 @@ spg_status launch_steps(spg_ctx *ctx, int k)
     const StepParams p = step_params(ctx);
     // kernels of this library per iteration
     const long long per_iter = ctx->fourier ? (ctx->xown ? 4 : 2) : 1;
-    if (ctx->fourier && k > 0 && !ctx->y_fresh) {
+    if (ctx->fourier && !ctx->xown && k > 0 && !ctx->y_fresh) {
         // y_k of the first step; every fused step then writes the next one
         CK(launch_form_y(ctx->st_d, ctx->vols_d, ctx->beta_d, ctx->X, ctx->Ybuf, ctx->total, ctx->stream), "form y");
         ctx->launches += 1;

@@ -223,6 +223,12 @@ bool xpass_supported(int nx, int nz);
 void xpass_twiddles(int nx, std::vector<float2> *table);
 cudaError_t launch_xpass_r2c(int nx, const float *Y, int pitch, int ny, int nz, float2 *F, const float2 *tw,
                              cudaStream_t s);
+// The forward row pass of y_k = x_k + beta_k d_k formed from the increment-
+// storage buffers (xbuf[0..1]: x, xbuf[2..3]: d; the current pair and beta_k
+// read on the device, as the step that follows reads them).
+cudaError_t launch_xpass_r2c_extrap(int nx, const DevState *st, const VolDesc *vols, const float *beta,
+                                    float *const *xbuf, int pitch, int ny, int nz, float2 *F, const float2 *tw,
+                                    cudaStream_t s);
 cudaError_t launch_xpass_c2r(int nx, const float2 *F, int ny, int nz, float *Y, int pitch, const float2 *tw,
                              cudaStream_t s);
 cudaError_t launch_kx_major(const float *in, float *out, int ny, int nxh, int nz, cudaStream_t s);

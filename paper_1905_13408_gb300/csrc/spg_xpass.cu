@@ -68,6 +68,19 @@ struct Rows {
 // reach their slots from one per-thread base at constant offsets
 // (at(s, base + q Ns) - at(s, base) = at(s, q Ns), and at(s, t + i L/8) -
 // at(s, t) = at(s, i L/8)). Rows of 64: bits 0-3 of z XORed with bits 3-6.
+// Input rows of the forward row pass: a real volume y, or (y null) the
+// extrapolated point y_k = x_k + beta_k d_k of an increment-storage solve,
+// formed while the rows are read: x_k in xs[cur], d_k in ds[cur], with cur
+// and beta_k = beta[kmom] read from the device state and descriptor when the
+// launch runs.
+struct RowSrc {
+    const float *y;
+    const float *xs[2], *ds[2];
+    const DevState *st;
+    const VolDesc *vols;
+    const float *beta;
+};
+
 template <int L>
 struct Slots {
     static constexpr bool PAD = L >= 128;
@@ -169,17 +182,34 @@ __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.
 // R rows y0 .. y0 + R - 1 of plane z: real-to-complex transform along x,
 // written kx-major (runs of R consecutive rows). tws: the row pass's table in
 // shared memory; buf: R LP slots.
-template <int LOG2N>
-__device__ __forceinline__ void r2c_rows(const float *__restrict__ Y, int pitch, int ny, float2 *__restrict__ F,
-                                         const float2 *tws, float2 *buf, int z, int y0)
+// With EXT the rows are those of y = x + beta d, formed from Y (x) and D (d)
+// by one fused multiply-add per value, as the fused step forms y.
+template <int LOG2N, bool EXT>
+__device__ __forceinline__ void r2c_rows(const float *__restrict__ Y, const float *__restrict__ D, float beta,
+                                         int pitch, int ny, float2 *__restrict__ F, const float2 *tws, float2 *buf,
+                                         int z, int y0)
 {
     using P = Rows<LOG2N>;
     const int t = threadIdx.x % P::T, r = threadIdx.x / P::T, y = y0 + r;
     const bool in = y < ny;
-    const float2 *row = reinterpret_cast<const float2 *>(Y + ((long long)z * ny + (in ? y : 0)) * pitch);
+    const long long ro = ((long long)z * ny + (in ? y : 0)) * pitch;
+    const float2 *row = reinterpret_cast<const float2 *>(Y + ro);
     float2 v[8];
+    if constexpr (EXT) {
+        const float2 *drow = reinterpret_cast<const float2 *>(D + ro);
 #pragma unroll
-    for (int i = 0; i < 8; i++) v[i] = in ? __ldg(row + t + i * P::T) : make_float2(0.f, 0.f);
+        for (int i = 0; i < 8; i++) {
+            if (in) {
+                const float2 xv = __ldg(row + t + i * P::T), dv = __ldg(drow + t + i * P::T);
+                v[i] = make_float2(fmaf(beta, dv.x, xv.x), fmaf(beta, dv.y, xv.y));
+            } else {
+                v[i] = make_float2(0.f, 0.f);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; i++) v[i] = in ? __ldg(row + t + i * P::T) : make_float2(0.f, 0.f);
+    }
     row_fft<LOG2N - 1, P::LP, -1>(v, tws + P::N, buf, t, r);
     float2 *u = buf + r * P::LP;
     if constexpr (P::T <= 32) {
@@ -294,18 +324,27 @@ __device__ __forceinline__ void c2r_rows(const float2 *__restrict__ F, int ny, f
     }
 }
 
-template <int LOG2N>
+template <int LOG2N, bool EXT>
 __global__ void __launch_bounds__(Rows<LOG2N>::THREADS, 4)
-    xpass_r2c_kernel(const float *__restrict__ Y, int pitch, int ny, float2 *__restrict__ F,
-                     const float2 *__restrict__ tw)
+    xpass_r2c_kernel(const RowSrc src, int pitch, int ny, float2 *__restrict__ F, const float2 *__restrict__ tw)
 {
     using P = Rows<LOG2N>;
     extern __shared__ __align__(16) float2 xsm[];
     float2 *const buf = xsm;
     float2 *const tws = xsm + P::R * P::LP;
     for (int i = threadIdx.x; i < P::TW; i += P::THREADS) tws[i] = tw[i];
+    const float *Y = src.y, *D = nullptr;
+    float beta = 0.f;
+    if constexpr (EXT) {
+        // the solver's current pair and extrapolation weight, as the device
+        // state holds them when this launch runs
+        const int cur = src.st->cur;
+        Y = cur == 0 ? src.xs[0] : src.xs[1];
+        D = cur == 0 ? src.ds[0] : src.ds[1];
+        beta = src.beta[src.vols[0].kmom];
+    }
     __syncthreads();
-    r2c_rows<LOG2N>(Y, pitch, ny, F, tws, buf, blockIdx.y, blockIdx.x * P::R);
+    r2c_rows<LOG2N, EXT>(Y, D, beta, pitch, ny, F, tws, buf, blockIdx.y, blockIdx.x * P::R);
 }
 
 template <int LOG2N>
@@ -342,7 +381,7 @@ __global__ void plane_transpose_kernel(const T *__restrict__ in, T *__restrict__
 }
 
 template <int LOG2N>
-cudaError_t xpass(bool forward, const float *Yin, float *Yout, int pitch, int ny, int nz, const float2 *Fin,
+cudaError_t xpass(bool forward, const RowSrc &src, float *Yout, int pitch, int ny, int nz, const float2 *Fin,
                   float2 *Fout, const float2 *tw, cudaStream_t s)
 {
     using P = Rows<LOG2N>;
@@ -355,7 +394,11 @@ cudaError_t xpass(bool forward, const float *Yin, float *Yout, int pitch, int ny
         if (e != cudaSuccess) return e;
         if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
         if (!opted[dev]) {
-            e = cudaFuncSetAttribute(xpass_r2c_kernel<LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);
+            e = cudaFuncSetAttribute(xpass_r2c_kernel<LOG2N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)P::SMEM);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(xpass_r2c_kernel<LOG2N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)P::SMEM);
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(xpass_c2r_kernel<LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)P::SMEM);
@@ -363,21 +406,23 @@ cudaError_t xpass(bool forward, const float *Yin, float *Yout, int pitch, int ny
             opted[dev] = true;
         }
     }
-    if (forward)
-        xpass_r2c_kernel<LOG2N><<<grid, P::THREADS, P::SMEM, s>>>(Yin, pitch, ny, Fout, tw);
+    if (forward && src.y)
+        xpass_r2c_kernel<LOG2N, false><<<grid, P::THREADS, P::SMEM, s>>>(src, pitch, ny, Fout, tw);
+    else if (forward)
+        xpass_r2c_kernel<LOG2N, true><<<grid, P::THREADS, P::SMEM, s>>>(src, pitch, ny, Fout, tw);
     else
         xpass_c2r_kernel<LOG2N><<<grid, P::THREADS, P::SMEM, s>>>(Fin, ny, Yout, pitch, tw);
     return cudaGetLastError();
 }
 
-cudaError_t xpass_dispatch(int nx, bool forward, const float *Yin, float *Yout, int pitch, int ny, int nz,
+cudaError_t xpass_dispatch(int nx, bool forward, const RowSrc &src, float *Yout, int pitch, int ny, int nz,
                            const float2 *Fin, float2 *Fout, const float2 *tw, cudaStream_t s)
 {
     switch (nx) {
-    case 128: return xpass<7>(forward, Yin, Yout, pitch, ny, nz, Fin, Fout, tw, s);
-    case 256: return xpass<8>(forward, Yin, Yout, pitch, ny, nz, Fin, Fout, tw, s);
-    case 512: return xpass<9>(forward, Yin, Yout, pitch, ny, nz, Fin, Fout, tw, s);
-    case 1024: return xpass<10>(forward, Yin, Yout, pitch, ny, nz, Fin, Fout, tw, s);
+    case 128: return xpass<7>(forward, src, Yout, pitch, ny, nz, Fin, Fout, tw, s);
+    case 256: return xpass<8>(forward, src, Yout, pitch, ny, nz, Fin, Fout, tw, s);
+    case 512: return xpass<9>(forward, src, Yout, pitch, ny, nz, Fin, Fout, tw, s);
+    case 1024: return xpass<10>(forward, src, Yout, pitch, ny, nz, Fin, Fout, tw, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -435,13 +480,32 @@ void xpass_twiddles(int nx, std::vector<float2> *table)
 cudaError_t launch_xpass_r2c(int nx, const float *Y, int pitch, int ny, int nz, float2 *F, const float2 *tw,
                              cudaStream_t s)
 {
-    return xpass_dispatch(nx, true, Y, nullptr, pitch, ny, nz, nullptr, F, tw, s);
+    if (!Y) return cudaErrorInvalidValue;
+    RowSrc src{};
+    src.y = Y;
+    return xpass_dispatch(nx, true, src, nullptr, pitch, ny, nz, nullptr, F, tw, s);
+}
+
+cudaError_t launch_xpass_r2c_extrap(int nx, const DevState *st, const VolDesc *vols, const float *beta,
+                                    float *const *xbuf, int pitch, int ny, int nz, float2 *F, const float2 *tw,
+                                    cudaStream_t s)
+{
+    RowSrc src{};
+    src.xs[0] = xbuf[0];
+    src.xs[1] = xbuf[1];
+    src.ds[0] = xbuf[2];
+    src.ds[1] = xbuf[3];
+    src.st = st;
+    src.vols = vols;
+    src.beta = beta;
+    if (!src.xs[0] || !src.xs[1] || !src.ds[0] || !src.ds[1] || !st || !vols || !beta) return cudaErrorInvalidValue;
+    return xpass_dispatch(nx, true, src, nullptr, pitch, ny, nz, nullptr, F, tw, s);
 }
 
 cudaError_t launch_xpass_c2r(int nx, const float2 *F, int ny, int nz, float *Y, int pitch, const float2 *tw,
                              cudaStream_t s)
 {
-    return xpass_dispatch(nx, false, nullptr, Y, pitch, ny, nz, F, nullptr, tw, s);
+    return xpass_dispatch(nx, false, RowSrc{}, Y, pitch, ny, nz, F, nullptr, tw, s);
 }
 
 cudaError_t launch_kx_major(const float *in, float *out, int ny, int nxh, int nz, cudaStream_t s)

@@ -145,11 +145,12 @@ def test_fourier_anchor_matches_oracle(shape):
     np.testing.assert_allclose(obj[0], want, rtol=1e-5)
 
 
-def test_fourier_checkpoint_resume_bitwise():
+@pytest.mark.parametrize("shape", [(16, 18, 20), (16, 40, 128)])
+def test_fourier_checkpoint_resume_bitwise(shape):
     """State saved in the middle of a Fourier-domain round and restored gives
-    the same iterates bit for bit (the extrapolated point is re-formed from
-    the restored x_k and d_k exactly as the fused step writes it)."""
-    shape = (16, 18, 20)
+    the same iterates bit for bit: the extrapolated point is formed from the
+    restored x_k and d_k exactly as before (by a separate pass ahead of the
+    library's transforms, x = 20; inside the own row pass, x = 128)."""
     fv = synth.make_fourier_volume(shape, blobs=6, radius=4, seed=67)
     hyper = dict(HYPER, mu=0.02)
     s = spg.SPG(dict(shape=shape, **hyper))
