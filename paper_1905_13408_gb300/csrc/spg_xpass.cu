@@ -324,6 +324,14 @@ __device__ __forceinline__ void c2r_rows(const float2 *__restrict__ F, int ny, f
     }
 }
 
+// Both row passes take the planes from the last to the first (CTAs start
+// in about blockIdx order): their neighbours in an iteration walk the planes
+// upwards (the fused step's z march; the library's batched transforms along
+// y, line index z (nx/2+1) + kx), so the planes a pass reads first are the
+// ones its producer wrote last, still in L2, and the planes it writes last
+// are the ones its consumer reads first.
+__device__ __forceinline__ int plane_descending() { return (int)(gridDim.y - 1 - blockIdx.y); }
+
 template <int LOG2N, bool EXT>
 __global__ void __launch_bounds__(Rows<LOG2N>::THREADS, 4)
     xpass_r2c_kernel(const RowSrc src, int pitch, int ny, float2 *__restrict__ F, const float2 *__restrict__ tw)
@@ -344,7 +352,7 @@ __global__ void __launch_bounds__(Rows<LOG2N>::THREADS, 4)
         beta = src.beta[src.vols[0].kmom];
     }
     __syncthreads();
-    r2c_rows<LOG2N, EXT>(Y, D, beta, pitch, ny, F, tws, buf, blockIdx.y, blockIdx.x * P::R);
+    r2c_rows<LOG2N, EXT>(Y, D, beta, pitch, ny, F, tws, buf, plane_descending(), blockIdx.x * P::R);
 }
 
 template <int LOG2N>
@@ -357,7 +365,7 @@ __global__ void __launch_bounds__(Rows<LOG2N>::THREADS, 4)
     float2 *const buf = xsm;
     float2 *const tws = xsm + P::R * P::LP;
     for (int i = threadIdx.x; i < P::TW; i += P::THREADS) tws[i] = tw[i];  // c2r_rows syncs before reading
-    c2r_rows<LOG2N>(F, ny, Y, pitch, tws, buf, blockIdx.y, blockIdx.x * P::R);
+    c2r_rows<LOG2N>(F, ny, Y, pitch, tws, buf, plane_descending(), blockIdx.x * P::R);
 }
 
 // out[z][c][r] = in[z][r][c] for planes of rows x cols elements.
