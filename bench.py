@@ -598,7 +598,7 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=10, world=1):
     """Through the public API with host buffers. Each step uploads b and w from
     pinned host memory (with the device validation), re-weights, runs `iters`
     fused iterations, reads the objective and downloads x to pinned host
-    memory. Three contexts on three streams take the steps in rotation, so a
+    memory. Four contexts on four streams take the steps in rotation, so a
     step's upload and the previous step's objective and download overlap
     iterations (the serving pattern); the same steps run back to back on one
     context are reported beside it. With several ranks every rank runs its own volume;
@@ -610,7 +610,7 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=10, world=1):
     b_h = torch.from_numpy(vol.b).pin_memory()
     w_h = torch.from_numpy(vol.w).pin_memory()
     x_h = torch.empty(vol.b.shape, dtype=torch.float32).pin_memory()
-    streams = [stream, torch.cuda.Stream(), torch.cuda.Stream()]
+    streams = [stream, torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()]
     ctxs = [spg.SPG(dict(shape=vol.b.shape, **hyper), data_dtype=args.dtype, tile=args.tile, zchunk=args.zchunk,
                     stream=st.cuda_stream, storage=args.storage, hist_every=args.hist_every) for st in streams]
     for _ in range(2):
@@ -658,11 +658,12 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=10, world=1):
     t_seq = max_over_ranks(time.perf_counter() - t0, world)
     seq = world * nvox * iters * reps / t_seq / 1e9
 
-    # three contexts in rotation: steps i+1 and i+2 are uploaded and enqueued
+    # four contexts in rotation: steps i+1 .. i+3 are uploaded and enqueued
     # while step i iterates, and step i's objective and download overlap their
     # iterations; the fused launches of consecutive steps are ordered by an
-    # event, so they never share the GPU. Two steps of queued GPU work (about
-    # 0.12 s) ride out a stall of the host thread
+    # event, so they never share the GPU. Three steps of queued GPU work
+    # (about 0.19 s) ride out a stall of the host thread (stalls of up to
+    # 0.15 s were seen on the GPU machine; two queued steps left the GPU idle)
     steps = 2 * reps
     nq = len(ctxs)
     torch.cuda.synchronize()
@@ -701,7 +702,7 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=10, world=1):
             "h2d_bytes_per_step": int(world * (b_h.numel() * 4 + w_h.numel() * 4)),
             "d2h_bytes_per_step": int(world * (x_h.numel() * 4 + 4 * 8)),
             "step": f"upload b,w from pinned host (validated), re-weight, {iters} fused iterations, objective, "
-                    f"download x; three contexts on three streams take the steps in rotation, so a step's "
+                    f"download x; four contexts on four streams take the steps in rotation, so a step's "
                     f"upload and the previous step's objective and download overlap iterations",
             "host_ms_per_step": [round(v, 2) for v in step_ms],
             "back_to_back_one_context": {"value": seq, "ms_per_phase": {k: 1e3 * v / reps for k, v in phases.items()},
