@@ -663,7 +663,7 @@ def measure_e2e(vol, hyper, args, stream, iters=100, reps=10, world=1):
     # iterations; the fused launches of consecutive steps are ordered by an
     # event, so they never share the GPU. Three steps of queued GPU work
     # (about 0.19 s) ride out a stall of the host thread (stalls of up to
-    # 0.15 s were seen on the GPU machine; two queued steps left the GPU idle)
+    # 0.15 s were measured; two queued steps left the GPU idle through them)
     steps = 2 * reps
     nq = len(ctxs)
     torch.cuda.synchronize()
