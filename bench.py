@@ -811,17 +811,15 @@ def measure_adjoint(args):
         b.grad = None
         w.grad = None
     fwd, bwd = min(t[0] for t in times), min(t[1] for t in times)
-    # bytes the backward moves per voxel: the four adjoint passes per step
-    # (D y and p: x_k, x_{k-1}, omtv read, two 3-vector fields written, 36 B;
-    # mask: p and its forward neighbours, x_k, x_{k-1}, b, w, om1, gnext, gb,
-    # gw read, m, gb, gw written, 56 B; H D m: m, D y, omtv read, a 3-vector
-    # field written, 32 B; apply: that field, m, w, gcur, gprev read, gcur,
-    # gprev written, 36 B) and the fused forward steps it runs (a sweep of K
-    # and the recomputation of K - K/C, 28 B each with previous-iterate
-    # storage)
+    # bytes the backward moves per voxel: the two adjoint passes per step
+    # (mask: x_k, x_{k-1}, omtv, b, w, om1, gnext, gb, gw read, m, gb, gw
+    # written, 48 B; apply: x_k, x_{k-1}, m, omtv, w, gcur, gprev read, gcur,
+    # gprev written, 36 B; the neighbours' rows come from cache) and the fused
+    # forward steps it runs (a sweep of K and the recomputation of K - K/C,
+    # 28 B each with previous-iterate storage)
     C = 10
     nck = (K + C - 1) // C
-    per_voxel = 160 * K + 28 * (2 * K - nck)
+    per_voxel = 84 * K + 28 * (2 * K - nck)
     achieved = per_voxel * vol.b.size / bwd / 1e9
     peaks, kind = measured_peaks()
     peak = peaks["hbm_gbs"]

@@ -386,7 +386,7 @@ spg_status spg_set_state(spg_ctx *ctx, const void *blob, size_t size);
  * iterates from checkpoints of (x_k, x_{k-1}) taken every `ckpt_every`
  * iterations (0 = 10). The context's own iterate is left unchanged.
  * Working memory (2 ceil(K / ckpt_every) checkpoint volumes, ckpt_every + 2
- * segment volumes and 15 more) comes from a workspace the context owns: it
+ * segment volumes and 6 more) comes from a workspace the context owns: it
  * is allocated on first use, grown when a call needs more and kept until
  * spg_destroy, so repeated calls allocate nothing. Synchronises. */
 spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *gw,

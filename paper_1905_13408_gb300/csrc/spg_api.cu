@@ -1817,8 +1817,8 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
     const size_t nsteps = (size_t)K + (size_t)(K - nck);
     // workspace: checkpoints, segment, adjoint volumes, scalar partials, the steps' state
     float *ck = nullptr, *seg = nullptr, *ga[3], *m = nullptr, *accb = nullptr, *accw = nullptr;
-    float *fG = nullptr, *fP = nullptr, *fH = nullptr;  // 3-vector fields of the adjoint passes
     double *pp = nullptr;
+    const int nblk = adjoint_blocks(d.nx, d.ny, d.nz);  // CTAs of each adjoint pass, one scalar partial each
     Carve cv;
     for (int pass = 0; pass < 2; pass++) {
         Carve t;
@@ -1829,10 +1829,7 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
         m = t.take<float>(vb);
         accb = t.take<float>(vb);
         accw = t.take<float>(vb);
-        fG = t.take<float>(vb * 3);
-        fP = t.take<float>(vb * 3);
-        fH = t.take<float>(vb * 3);
-        pp = t.take<double>((size_t)K * d.nz * AUX_SEG * 4 * sizeof(double));
+        pp = t.take<double>((size_t)K * nblk * 4 * sizeof(double));
         if (pass == 0) {
             DevState *s0;
             VolDesc *v0;
@@ -1920,15 +1917,12 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
             a.gprev = k >= 1 ? ga[iprev] : ga[icur];
             a.gb = accb;
             a.gw = accw;
-            a.plane_part = pp + (size_t)k * d.nz * AUX_SEG * 4;
-            a.G = fG;
-            a.P = fP;
-            a.HQ = fH;
-            a.stride = ctx->total;
+            a.plane_part = pp + (size_t)k * nblk * 4;
+            a.nblocks = nblk;
             a.prev_fresh = k >= 1 ? 1 : 0;  // dL/dx_{k-1} gets its first contribution here
             CK(launch_adjoint_mask(a, ctx->stream), "adjoint mask");
             CK(launch_adjoint_apply(a, ctx->stream), "adjoint apply");
-            ctx->launches += 4;
+            ctx->launches += 2;
             // rotate: dL/dx_k is complete; the old dL/dx_{k+1} buffer becomes dL/dx_{k-2},
             // which the next step writes (no clearing needed)
             const int t = inext;
@@ -1939,7 +1933,7 @@ spg_status spg_backward(spg_ctx *ctx, int K, const float *gx, float *gb, float *
     }
     if ((s = copy_volume_out(ctx, gb, accb, 4, d)) != SPG_OK) return s;
     if ((s = copy_volume_out(ctx, gw, accw, 4, d)) != SPG_OK) return s;
-    const size_t segs = (size_t)d.nz * AUX_SEG;
+    const size_t segs = (size_t)nblk;
     std::vector<double> hp((size_t)K * segs * 4);
     CK(cudaMemcpyAsync(hp.data(), pp, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "read");
     CK(cudaStreamSynchronize(ctx->stream), "synchronise");

@@ -829,21 +829,23 @@ __global__ void generic_step_kernel(GenericParams g)
 }
 
 // ---------------- adjoint of one step ----------------
-// Four passes over row segments, each a stencil of radius one on fields the
-// previous pass stored (component c of a 3-vector field at c * stride):
-//   1. G = D y and P = omtv grad h_mu(G) at every voxel;
-//   2. tvg = D^T P, the step's z, the soft-threshold mask m = gnext [pass],
-//      the l1 / TV scalar partials, gb += tau w m, gw += -tau (y - b) m;
-//   3. HQ = omtv H_mu(G) D m, H_mu = I/mu inside the smoothing ball and
-//      (I - e e^T)/|G| outside (the Hessian of Eq. 14);
-//   4. ybar = m - tau (w m + lambda_tv D^T HQ); gcur += (1+beta) ybar,
+// Two passes, each a march over z (a CTA owns TY rows of a 128-voxel chunk
+// of x over ZC planes, warp r row y0 + r, one more warp the row below the
+// tile), 4 voxels per lane with 16-byte loads and x-neighbours by shuffle:
+//   1. mask: p = omtv grad h_mu(D y) (Eq. 12, 16), tvg = D^T p (Eq. 17),
+//      the step's z, the soft-threshold mask m = gnext [pass] (Eq. 21), the
+//      l1 / TV scalar partials, gb += tau w m, gw += -tau (y - b) m;
+//   2. apply: hq = omtv H_mu(D y) D m, H_mu = I/mu inside the smoothing ball
+//      and (I - e e^T)/|D y| outside (the Hessian of Eq. 14);
+//      ybar = m - tau (w m + lambda_tv D^T hq); gcur += (1+beta) ybar,
 //      gprev += -beta ybar (gprev is written, not accumulated, when it has
 //      no earlier contribution).
-// The values equal those of evaluating every quantity on the fly at each
-// neighbour. Each pass walks rows like the re-weighting: 4 voxels per lane
-// with 16-byte loads, x-neighbours by shuffle; padding columns of the pitch
-// get zeros in every stored field, so they read as the zero outside the
-// volume.
+// Each step of the march evaluates p (hq) on the next plane once per voxel
+// and keeps it in registers, where it is the forward z-neighbour now and the
+// voxel's own value one step later; the y-component of the row below comes
+// from the warp that owns that row through a 3-plane shared ring; the
+// x-neighbour from the next lane (a chunk's last lane evaluates it). Only m
+// is stored between the passes.
 struct Lane4 {
     int x0, y, z, lane;
     bool act;
@@ -889,122 +891,254 @@ __device__ __forceinline__ void right4(const VolDesc &V, const float *f, const L
         if (L.x0 + q + 1 >= V.nx) r[q] = 0.f;
 }
 
-#define ADJ_WALK_BEGIN                                                                  \
-    const VolDesc V = a.vols[0];                                                        \
-    const int zz_ = blockIdx.x / AUX_SEG;                                               \
-    int r0, r1;                                                                         \
-    seg_rows(V.ny, blockIdx.x % AUX_SEG, r0, r1);                                       \
-    const int lane_ = threadIdx.x & 31, warp_ = threadIdx.x >> 5, nw_ = blockDim.x >> 5; \
-    const int nchunk_ = (V.nx + 127) / 128;                                             \
-    const long long S = a.stride, PS = (long long)V.pitch * V.ny;                       \
-    for (int rc = warp_; rc < (r1 - r0) * nchunk_; rc += nw_) {                         \
-        Lane4 L;                                                                        \
-        L.y = r0 + rc / nchunk_;                                                        \
-        L.z = zz_;                                                                      \
-        L.x0 = (rc % nchunk_) * 128 + 4 * lane_;                                        \
-        L.lane = lane_;                                                                 \
-        L.act = L.x0 < V.nx;                                                            \
-        L.i = V.off + ((long long)L.z * V.ny + L.y) * V.pitch + L.x0;
-#define ADJ_WALK_END }
+namespace adj {
+constexpr int TY = 7;                  // output rows per CTA
+constexpr int THREADS = 32 * (TY + 1); // warp TY: the row below the tile
+constexpr int ZC = 8;                  // planes per CTA
+}  // namespace adj
 
-__global__ void adjoint_grad_kernel(AdjParams a)
+// f at the lane's voxels of the row whose voxel x0 is element i (zeros where
+// `ok` is false) and at x0-1: from the lane before, loaded by a chunk's first
+// lane, and the voxel's own value at the volume's first column (zero backward
+// difference along x). Every lane of the warp calls it.
+__device__ __forceinline__ void row4(const float *f, const Lane4 &L, long long i, bool ok, float (&c)[4], float &l)
 {
-    ADJ_WALK_BEGIN
-    float xc[4], mc[4], xu[4], mu_[4], xw[4], mw[4], xl[4], ml[4], ot[4];
-    unpack4(ldz4(a.xk + L.i, L.act), xc);
-    unpack4(ldz4(a.xkm1 + L.i, L.act), mc);
-    left4(a.xk, L, xc, xl);
-    left4(a.xkm1, L, mc, ml);
-    if (L.y >= 1) {
-        unpack4(ldz4(a.xk + L.i - V.pitch, L.act), xu);
-        unpack4(ldz4(a.xkm1 + L.i - V.pitch, L.act), mu_);
+    unpack4(ldz4(f + i, ok), c);
+    l = __shfl_up_sync(FULL, c[3], 1);
+    if (L.lane == 0) l = (ok && L.x0 >= 1) ? f[i - 1] : c[0];
+    if (L.x0 == 0) l = c[0];
+}
+
+// f on the row whose voxel x0 is element i when `have`, else a copy of c
+// (a missing backward neighbour: the voxel stands in for it).
+__device__ __forceinline__ void row4_or(const float *f, long long i, bool have, bool ok, const float (&c)[4],
+                                        float (&r)[4])
+{
+    if (have) {
+        unpack4(ldz4(f + i, ok), r);
     } else {
 #pragma unroll
-        for (int q = 0; q < 4; q++) xu[q] = xc[q], mu_[q] = mc[q];
+        for (int q = 0; q < 4; q++) r[q] = c[q];
     }
-    if (L.z >= 1) {
-        unpack4(ldz4(a.xk + L.i - PS, L.act), xw);
-        unpack4(ldz4(a.xkm1 + L.i - PS, L.act), mw);
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; q++) xw[q] = xc[q], mw[q] = mc[q];
-    }
-    unpack4(ldz4(a.omtv + L.i, L.act), ot);
-    float G[3][4], P[3][4];
+}
+
+// (D y)_a at the lane's 4 voxels (Eq. 12 on y = x_k + beta (x_k - x_{k-1})),
+// differences of x_k and of d = x_k - x_{k-1} taken separately: xc, mc on
+// the voxels' row (xl, ml at x0-1), xu, mu_ on the row below in y, xw, mw on
+// the plane below.
+__device__ __forceinline__ void dy4(const float (&xc)[4], const float (&mc)[4], float xl, float ml,
+                                    const float (&xu)[4], const float (&mu_)[4], const float (&xw)[4],
+                                    const float (&mw)[4], float beta, float (&g)[3][4])
+{
 #pragma unroll
     for (int q = 0; q < 4; q++) {
         const float dc = xc[q] - mc[q];
-        float g[3];
-        g[0] = (xc[q] - xl[q]) + a.beta * (dc - (xl[q] - ml[q]));
-        g[1] = (xc[q] - xu[q]) + a.beta * (dc - (xu[q] - mu_[q]));
-        g[2] = (xc[q] - xw[q]) + a.beta * (dc - (xw[q] - mw[q]));
-        const bool valid = L.act && L.x0 + q < V.nx;
-        const float s2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-        const float sc = ot[q] * fminf(1.0f / V.mu, rsqrtf(s2));
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            G[c][q] = valid ? g[c] : 0.f;
-            P[c][q] = valid ? g[c] * sc : 0.f;
-        }
+        const float lx = q ? xc[q - 1] : xl, lm = q ? mc[q - 1] : ml;
+        g[0][q] = (xc[q] - lx) + beta * (dc - (lx - lm));
+        g[1][q] = (xc[q] - xu[q]) + beta * (dc - (xu[q] - mu_[q]));
+        g[2][q] = (xc[q] - xw[q]) + beta * (dc - (xw[q] - mw[q]));
     }
-    if (L.act) {
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            st4(a.G + c * S + L.i, G[c]);
-            st4(a.P + c * S + L.i, P[c]);
-        }
-    }
-    ADJ_WALK_END
 }
 
-__global__ void adjoint_mask_kernel(AdjParams a)
+// The same at one voxel: (xa, ma) there, (xl, ml) at x-1, (xu, mu_) at y-1,
+// (xw, mw) at z-1.
+__device__ __forceinline__ void dy1(float xa, float ma, float xl, float ml, float xu, float mu_, float xw, float mw,
+                                    float beta, float (&g)[3])
 {
+    const float dc = xa - ma;
+    g[0] = (xa - xl) + beta * (dc - (xl - ml));
+    g[1] = (xa - xu) + beta * (dc - (xu - mu_));
+    g[2] = (xa - xw) + beta * (dc - (xw - mw));
+}
+
+// omtv / max(mu, |g|): the factor by which omtv grad h_mu(g) (Eq. 16) scales g.
+__device__ __forceinline__ float p_scale(float g0, float g1, float g2, float ot, float mu)
+{
+    const float s2 = g0 * g0 + g1 * g1 + g2 * g2;
+    return ot * fminf(1.0f / mu, rsqrtf(s2));
+}
+
+// omtv H_mu(g) q at one voxel, H_mu the Hessian of the smoothed norm (Eq. 14):
+// I/mu inside the ball |g| <= mu, (I - e e^T)/|g| with e = g/|g| outside.
+__device__ __forceinline__ void hq1(float g0, float g1, float g2, float q0, float q1, float q2, float ot, float mu,
+                                    float (&h)[3])
+{
+    const float s = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
+    if (s <= mu) {
+        const float c = ot / mu;
+        h[0] = q0 * c;
+        h[1] = q1 * c;
+        h[2] = q2 * c;
+    } else {
+        const float inv = 1.0f / s;
+        const float e0 = g0 * inv, e1 = g1 * inv, e2 = g2 * inv;
+        const float eq = e0 * q0 + e1 * q1 + e2 * q2;
+        const float c = ot * inv;
+        h[0] = (q0 - e0 * eq) * c;
+        h[1] = (q1 - e1 * eq) * c;
+        h[2] = (q2 - e2 * eq) * c;
+    }
+}
+
+// Where a thread of the two passes works: chunk of x, tile of rows, planes.
+struct AdjPlace {
+    Lane4 L;
+    int r, z0, z1;
+    bool row_in;   // the warp's row is inside the volume
+    long long PS;  // plane stride
+};
+
+__device__ __forceinline__ AdjPlace adj_place(const VolDesc &V)
+{
+    AdjPlace P;
+    const int nchunk = (V.nx + 127) / 128, ntile = (V.ny + adj::TY - 1) / adj::TY;
+    int b = blockIdx.x;
+    const int cx = b % nchunk;
+    b /= nchunk;
+    const int by = b % ntile, bz = b / ntile;
+    P.r = threadIdx.x >> 5;
+    P.L.lane = threadIdx.x & 31;
+    P.L.x0 = cx * 128 + 4 * P.L.lane;
+    P.L.y = by * adj::TY + P.r;
+    P.row_in = P.L.y < V.ny;
+    P.L.act = P.row_in && P.L.x0 < V.nx;
+    P.z0 = bz * adj::ZC;
+    P.z1 = min(V.nz, P.z0 + adj::ZC);
+    P.PS = (long long)V.pitch * V.ny;
+    return P;
+}
+
+// element index of voxel x0 of row (y, z); only formed for rows in the volume
+__device__ __forceinline__ long long adj_row(const VolDesc &V, int x0, int y, int z)
+{
+    return V.off + ((long long)z * V.ny + y) * V.pitch + x0;
+}
+
+__global__ void __launch_bounds__(adj::THREADS) adjoint_mask_kernel(AdjParams a)
+{
+    __shared__ __align__(16) float ring[3][adj::TY + 1][128];  // p_y of the tile's rows and the row below it
     __shared__ double scratch[32 * 4];
+    const VolDesc V = a.vols[0];
+    AdjPlace P = adj_place(V);
+    Lane4 &L = P.L;
+    const float beta = a.beta, mu = V.mu;
     KSum k1, k2;
-    ADJ_WALK_BEGIN
-    float p0[4], p1[4], p2[4], px[4], py[4], pz[4];
-    unpack4(ldz4(a.P + L.i, L.act), p0);
-    unpack4(ldz4(a.P + S + L.i, L.act), p1);
-    unpack4(ldz4(a.P + 2 * S + L.i, L.act), p2);
-    right4(V, a.P, L, p0, px);
-    unpack4(ldz4(a.P + S + L.i + V.pitch, L.act && L.y + 1 < V.ny), py);
-    unpack4(ldz4(a.P + 2 * S + L.i + PS, L.act && L.z + 1 < V.nz), pz);
-    float xk[4], xm[4], bv[4], wv[4], o1[4], gn[4], gb[4], gw[4], m[4];
-    unpack4(ldz4(a.xk + L.i, L.act), xk);
-    unpack4(ldz4(a.xkm1 + L.i, L.act), xm);
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    unpack4(L.act ? ld4_data(a.b, a.bf16, L.i) : zero, bv);
-    unpack4(L.act ? ld4_data(a.w, a.bf16, L.i) : zero, wv);
-    unpack4(ldz4(a.om1 + L.i, L.act), o1);
-    unpack4(ldz4(a.gnext + L.i, L.act), gn);
-    unpack4(ldz4(a.gb + L.i, L.act), gb);
-    unpack4(ldz4(a.gw + L.i, L.act), gw);
-    float s1 = 0.f, s2 = 0.f;
+    // x_k, x_{k-1} on the warp's row of the current plane, and p there
+    float xc[4], mc[4], xl, ml, pc[3][4];
+    {
+        const int z = P.z0;
+        L.z = z;
+        L.i = P.row_in ? adj_row(V, L.x0, L.y, z) : 0;
+        float xu[4], mu_[4], xw[4], mw[4], ot[4], g[3][4];
+        row4(a.xk, L, L.i, L.act, xc, xl);
+        row4(a.xkm1, L, L.i, L.act, mc, ml);
+        row4_or(a.xk, L.i - V.pitch, L.y >= 1, L.act, xc, xu);
+        row4_or(a.xkm1, L.i - V.pitch, L.y >= 1, L.act, mc, mu_);
+        row4_or(a.xk, L.i - P.PS, z >= 1, L.act, xc, xw);
+        row4_or(a.xkm1, L.i - P.PS, z >= 1, L.act, mc, mw);
+        unpack4(ldz4(a.omtv + L.i, L.act), ot);
+        dy4(xc, mc, xl, ml, xu, mu_, xw, mw, beta, g);
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const bool valid = L.act && L.x0 + q < V.nx;
-        const float d = xk[q] - xm[q];
-        const float tvg = (p0[q] - px[q]) + (p1[q] - py[q]) + (p2[q] - pz[q]);
-        const float g = wv[q] * ((xk[q] - bv[q]) + a.beta * d) + V.lambda_tv * tvg;
-        const float delta = a.beta * d - V.tau * g;
-        const float zz = xk[q] + delta;
-        const float th = V.tau * V.lambda_l1 * o1[q];
-        const bool pass = fabsf(zz) > th || th <= 0.f;
-        m[q] = (valid && pass) ? gn[q] : 0.f;
-        const float sg = zz > 0.f ? 1.f : (zz < 0.f ? -1.f : 0.f);
-        s1 += -V.tau * o1[q] * sg * m[q];
-        s2 += -V.tau * tvg * m[q];
-        gb[q] += V.tau * wv[q] * m[q];
-        gw[q] += -V.tau * ((xk[q] - bv[q]) + a.beta * d) * m[q];
+        for (int q = 0; q < 4; q++) {
+            const bool valid = L.act && L.x0 + q < V.nx;
+            const float sc = p_scale(g[0][q], g[1][q], g[2][q], ot[q], mu);
+#pragma unroll
+            for (int c = 0; c < 3; c++) pc[c][q] = valid ? g[c][q] * sc : 0.f;
+        }
+        *reinterpret_cast<float4 *>(&ring[z % 3][P.r][4 * L.lane]) = make_float4(pc[1][0], pc[1][1], pc[1][2], pc[1][3]);
     }
-    if (L.act) {
-        st4(a.m + L.i, m);
-        st4(a.gb + L.i, gb);
-        st4(a.gw + L.i, gw);
+    for (int z = P.z0; z < P.z1; z++) {
+        // p on the next plane (zero beyond the volume)
+        const bool zn = z + 1 < V.nz;
+        const bool okn = L.act && zn;
+        const long long in_ = L.i + P.PS;
+        float xn[4], mn[4], xnl, mnl, pn[3][4];
+        {
+            float xu[4], mu_[4], ot[4], g[3][4];
+            row4(a.xk, L, in_, okn, xn, xnl);
+            row4(a.xkm1, L, in_, okn, mn, mnl);
+            row4_or(a.xk, in_ - V.pitch, L.y >= 1, okn, xn, xu);
+            row4_or(a.xkm1, in_ - V.pitch, L.y >= 1, okn, mn, mu_);
+            unpack4(ldz4(a.omtv + in_, okn), ot);
+            dy4(xn, mn, xnl, mnl, xu, mu_, xc, mc, beta, g);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const bool valid = okn && L.x0 + q < V.nx;
+                const float sc = p_scale(g[0][q], g[1][q], g[2][q], ot[q], mu);
+#pragma unroll
+                for (int c = 0; c < 3; c++) pn[c][q] = valid ? g[c][q] * sc : 0.f;
+            }
+            *reinterpret_cast<float4 *>(&ring[(z + 1) % 3][P.r][4 * L.lane]) =
+                make_float4(pn[1][0], pn[1][1], pn[1][2], pn[1][3]);
+        }
+        __syncthreads();  // p_y of plane z of every row of the tile is in the ring
+        // p_x at x+1: the next lane's first voxel; a chunk's last lane evaluates it
+        float pxn = __shfl_down_sync(FULL, pc[0][0], 1);
+        if (L.lane == 31) {
+            pxn = 0.f;
+            if (L.act && L.x0 + 4 < V.nx) {
+                const long long j = L.i + 4;
+                const float xa = a.xk[j], ma = a.xkm1[j];
+                const float xau = L.y >= 1 ? a.xk[j - V.pitch] : xa, mau = L.y >= 1 ? a.xkm1[j - V.pitch] : ma;
+                const float xaw = z >= 1 ? a.xk[j - P.PS] : xa, maw = z >= 1 ? a.xkm1[j - P.PS] : ma;
+                float ga[3];
+                dy1(xa, ma, xc[3], mc[3], xau, mau, xaw, maw, beta, ga);
+                pxn = ga[0] * p_scale(ga[0], ga[1], ga[2], a.omtv[j], mu);
+            }
+        }
+        if (P.r < adj::TY && P.row_in) {
+            float px[4] = {pc[0][1], pc[0][2], pc[0][3], pxn};
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (L.x0 + q + 1 >= V.nx) px[q] = 0.f;
+            const float4 pyv = *reinterpret_cast<const float4 *>(&ring[z % 3][P.r + 1][4 * L.lane]);
+            const float py[4] = {pyv.x, pyv.y, pyv.z, pyv.w};  // zero when row y + 1 is outside
+            float bv[4], wv[4], o1[4], gn[4], gb[4], gw[4], m[4];
+            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            unpack4(L.act ? ld4_data(a.b, a.bf16, L.i) : zero, bv);
+            unpack4(L.act ? ld4_data(a.w, a.bf16, L.i) : zero, wv);
+            unpack4(ldz4(a.om1 + L.i, L.act), o1);
+            unpack4(ldz4(a.gnext + L.i, L.act), gn);
+            unpack4(ldz4(a.gb + L.i, L.act), gb);
+            unpack4(ldz4(a.gw + L.i, L.act), gw);
+            float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const bool valid = L.act && L.x0 + q < V.nx;
+                const float d = xc[q] - mc[q];
+                const float tvg = (pc[0][q] - px[q]) + (pc[1][q] - py[q]) + (pc[2][q] - pn[2][q]);
+                const float g = wv[q] * ((xc[q] - bv[q]) + beta * d) + V.lambda_tv * tvg;
+                const float delta = beta * d - V.tau * g;
+                const float zz = xc[q] + delta;
+                const float th = V.tau * V.lambda_l1 * o1[q];
+                const bool pass = fabsf(zz) > th || th <= 0.f;
+                m[q] = (valid && pass) ? gn[q] : 0.f;
+                const float sg = zz > 0.f ? 1.f : (zz < 0.f ? -1.f : 0.f);
+                s1 += -V.tau * o1[q] * sg * m[q];
+                s2 += -V.tau * tvg * m[q];
+                gb[q] += V.tau * wv[q] * m[q];
+                gw[q] += -V.tau * ((xc[q] - bv[q]) + beta * d) * m[q];
+            }
+            if (L.act) {
+                st4(a.m + L.i, m);
+                st4(a.gb + L.i, gb);
+                st4(a.gw + L.i, gw);
+            }
+            k1.add(s1);
+            k2.add(s2);
+        }
+        // the next plane becomes the current one
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            xc[q] = xn[q];
+            mc[q] = mn[q];
+#pragma unroll
+            for (int c = 0; c < 3; c++) pc[c][q] = pn[c][q];
+        }
+        xl = xnl;
+        ml = mnl;
+        L.i = in_;
     }
-    k1.add(s1);
-    k2.add(s2);
-    ADJ_WALK_END
     double sm[2] = {k1.value(), k2.value()};
     block_sum<2>(sm, scratch);
     if (threadIdx.x == 0) {
@@ -1013,86 +1147,132 @@ __global__ void adjoint_mask_kernel(AdjParams a)
     }
 }
 
-__global__ void adjoint_hq_kernel(AdjParams a)
+// hq at the lane's 4 voxels from D y and D m there (zero where !ok or beyond nx)
+__device__ __forceinline__ void hq4(const float (&g)[3][4], const float (&qc)[4], float ql, const float (&qu)[4],
+                                    const float (&qw)[4], const float (&ot)[4], float mu, bool ok, int x0, int nx,
+                                    float (&h)[3][4])
 {
-    ADJ_WALK_BEGIN
-    float mc[4], ml[4], mu_[4], mw[4], g0[4], g1[4], g2[4], ot[4];
-    unpack4(ldz4(a.m + L.i, L.act), mc);
-    left4(a.m, L, mc, ml);
-    if (L.y >= 1) unpack4(ldz4(a.m + L.i - V.pitch, L.act), mu_);
-    else
-        for (int q = 0; q < 4; q++) mu_[q] = mc[q];
-    if (L.z >= 1) unpack4(ldz4(a.m + L.i - PS, L.act), mw);
-    else
-        for (int q = 0; q < 4; q++) mw[q] = mc[q];
-    unpack4(ldz4(a.G + L.i, L.act), g0);
-    unpack4(ldz4(a.G + S + L.i, L.act), g1);
-    unpack4(ldz4(a.G + 2 * S + L.i, L.act), g2);
-    unpack4(ldz4(a.omtv + L.i, L.act), ot);
-    float H[3][4];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-        const bool valid = L.act && L.x0 + q < V.nx;
-        const float qx = mc[q] - ml[q], qy = mc[q] - mu_[q], qz = mc[q] - mw[q];
-        const float s = sqrtf(g0[q] * g0[q] + g1[q] * g1[q] + g2[q] * g2[q]);
-        float h0, h1, h2;
-        if (s <= V.mu) {
-            const float c = ot[q] / V.mu;
-            h0 = qx * c;
-            h1 = qy * c;
-            h2 = qz * c;
-        } else {
-            const float inv = 1.0f / s;
-            const float e0 = g0[q] * inv, e1 = g1[q] * inv, e2 = g2[q] * inv;
-            const float eq = e0 * qx + e1 * qy + e2 * qz;
-            const float c = ot[q] * inv;
-            h0 = (qx - e0 * eq) * c;
-            h1 = (qy - e1 * eq) * c;
-            h2 = (qz - e2 * eq) * c;
-        }
-        H[0][q] = valid ? h0 : 0.f;
-        H[1][q] = valid ? h1 : 0.f;
-        H[2][q] = valid ? h2 : 0.f;
-    }
-    if (L.act) {
+        float t[3];
+        hq1(g[0][q], g[1][q], g[2][q], qc[q] - (q ? qc[q - 1] : ql), qc[q] - qu[q], qc[q] - qw[q], ot[q], mu, t);
+        const bool valid = ok && x0 + q < nx;
 #pragma unroll
-        for (int c = 0; c < 3; c++) st4(a.HQ + c * S + L.i, H[c]);
+        for (int c = 0; c < 3; c++) h[c][q] = valid ? t[c] : 0.f;
     }
-    ADJ_WALK_END
 }
 
-__global__ void adjoint_apply_kernel(AdjParams a)
+__global__ void __launch_bounds__(adj::THREADS) adjoint_apply_kernel(AdjParams a)
 {
-    ADJ_WALK_BEGIN
-    float h0[4], h1[4], h2[4], hx[4], hy[4], hz[4], m[4], wv[4], gc[4], gp[4] = {0.f, 0.f, 0.f, 0.f};
-    unpack4(ldz4(a.HQ + L.i, L.act), h0);
-    unpack4(ldz4(a.HQ + S + L.i, L.act), h1);
-    unpack4(ldz4(a.HQ + 2 * S + L.i, L.act), h2);
-    right4(V, a.HQ, L, h0, hx);
-    unpack4(ldz4(a.HQ + S + L.i + V.pitch, L.act && L.y + 1 < V.ny), hy);
-    unpack4(ldz4(a.HQ + 2 * S + L.i + PS, L.act && L.z + 1 < V.nz), hz);
-    unpack4(ldz4(a.m + L.i, L.act), m);
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    unpack4(L.act ? ld4_data(a.w, a.bf16, L.i) : zero, wv);
-    unpack4(ldz4(a.gcur + L.i, L.act), gc);
-    const bool alias = a.gprev == a.gcur;  // k = 0: x_{-1} = x_0
-    if (!alias && !a.prev_fresh) unpack4(ldz4(a.gprev + L.i, L.act), gp);
+    __shared__ __align__(16) float ring[3][adj::TY + 1][128];  // hq_y of the tile's rows and the row below it
+    const VolDesc V = a.vols[0];
+    AdjPlace P = adj_place(V);
+    Lane4 &L = P.L;
+    const float beta = a.beta, mu = V.mu;
+    // x_k, x_{k-1} and m on the warp's row of the current plane, and hq there
+    float xc[4], mc[4], qc[4], xl, ml, ql, hc[3][4];
+    {
+        const int z = P.z0;
+        L.z = z;
+        L.i = P.row_in ? adj_row(V, L.x0, L.y, z) : 0;
+        float xu[4], mu_[4], qu[4], xw[4], mw[4], qw[4], ot[4], g[3][4];
+        row4(a.xk, L, L.i, L.act, xc, xl);
+        row4(a.xkm1, L, L.i, L.act, mc, ml);
+        row4(a.m, L, L.i, L.act, qc, ql);
+        row4_or(a.xk, L.i - V.pitch, L.y >= 1, L.act, xc, xu);
+        row4_or(a.xkm1, L.i - V.pitch, L.y >= 1, L.act, mc, mu_);
+        row4_or(a.m, L.i - V.pitch, L.y >= 1, L.act, qc, qu);
+        row4_or(a.xk, L.i - P.PS, z >= 1, L.act, xc, xw);
+        row4_or(a.xkm1, L.i - P.PS, z >= 1, L.act, mc, mw);
+        row4_or(a.m, L.i - P.PS, z >= 1, L.act, qc, qw);
+        unpack4(ldz4(a.omtv + L.i, L.act), ot);
+        dy4(xc, mc, xl, ml, xu, mu_, xw, mw, beta, g);
+        hq4(g, qc, ql, qu, qw, ot, mu, L.act, L.x0, V.nx, hc);
+        *reinterpret_cast<float4 *>(&ring[z % 3][P.r][4 * L.lane]) = make_float4(hc[1][0], hc[1][1], hc[1][2], hc[1][3]);
+    }
+    for (int z = P.z0; z < P.z1; z++) {
+        const bool zn = z + 1 < V.nz;
+        const bool okn = L.act && zn;
+        const long long in_ = L.i + P.PS;
+        float xn[4], mn[4], qn[4], xnl, mnl, qnl, hn[3][4];
+        {
+            float xu[4], mu_[4], qu[4], ot[4], g[3][4];
+            row4(a.xk, L, in_, okn, xn, xnl);
+            row4(a.xkm1, L, in_, okn, mn, mnl);
+            row4(a.m, L, in_, okn, qn, qnl);
+            row4_or(a.xk, in_ - V.pitch, L.y >= 1, okn, xn, xu);
+            row4_or(a.xkm1, in_ - V.pitch, L.y >= 1, okn, mn, mu_);
+            row4_or(a.m, in_ - V.pitch, L.y >= 1, okn, qn, qu);
+            unpack4(ldz4(a.omtv + in_, okn), ot);
+            dy4(xn, mn, xnl, mnl, xu, mu_, xc, mc, beta, g);
+            hq4(g, qn, qnl, qu, qc, ot, mu, okn, L.x0, V.nx, hn);
+            *reinterpret_cast<float4 *>(&ring[(z + 1) % 3][P.r][4 * L.lane]) =
+                make_float4(hn[1][0], hn[1][1], hn[1][2], hn[1][3]);
+        }
+        __syncthreads();  // hq_y of plane z of every row of the tile is in the ring
+        // hq_x at x+1: the next lane's first voxel; a chunk's last lane evaluates it
+        float hxn = __shfl_down_sync(FULL, hc[0][0], 1);
+        if (L.lane == 31) {
+            hxn = 0.f;
+            if (L.act && L.x0 + 4 < V.nx) {
+                const long long j = L.i + 4;
+                const float xa = a.xk[j], ma = a.xkm1[j], qa = a.m[j];
+                const bool u = L.y >= 1, w = z >= 1;
+                const float xau = u ? a.xk[j - V.pitch] : xa, mau = u ? a.xkm1[j - V.pitch] : ma;
+                const float qau = u ? a.m[j - V.pitch] : qa;
+                const float xaw = w ? a.xk[j - P.PS] : xa, maw = w ? a.xkm1[j - P.PS] : ma;
+                const float qaw = w ? a.m[j - P.PS] : qa;
+                float ga[3], h[3];
+                dy1(xa, ma, xc[3], mc[3], xau, mau, xaw, maw, beta, ga);
+                hq1(ga[0], ga[1], ga[2], qa - qc[3], qa - qau, qa - qaw, a.omtv[j], mu, h);
+                hxn = h[0];
+            }
+        }
+        if (P.r < adj::TY && P.row_in) {
+            float hx[4] = {hc[0][1], hc[0][2], hc[0][3], hxn};
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const bool valid = L.act && L.x0 + q < V.nx;
-        const float dtv = (h0[q] - hx[q]) + (h1[q] - hy[q]) + (h2[q] - hz[q]);
-        const float ybar = valid ? m[q] - V.tau * (wv[q] * m[q] + V.lambda_tv * dtv) : 0.f;
-        gc[q] += (1.f + a.beta) * ybar;
-        if (alias) gc[q] += -a.beta * ybar;
-        else if (a.prev_fresh) gp[q] = -a.beta * ybar;
-        else gp[q] += -a.beta * ybar;
+            for (int q = 0; q < 4; q++)
+                if (L.x0 + q + 1 >= V.nx) hx[q] = 0.f;
+            const float4 hyv = *reinterpret_cast<const float4 *>(&ring[z % 3][P.r + 1][4 * L.lane]);
+            const float hy[4] = {hyv.x, hyv.y, hyv.z, hyv.w};
+            float wv[4], gc[4], gp[4] = {0.f, 0.f, 0.f, 0.f};
+            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            unpack4(L.act ? ld4_data(a.w, a.bf16, L.i) : zero, wv);
+            unpack4(ldz4(a.gcur + L.i, L.act), gc);
+            const bool alias = a.gprev == a.gcur;  // k = 0: x_{-1} = x_0
+            if (!alias && !a.prev_fresh) unpack4(ldz4(a.gprev + L.i, L.act), gp);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const bool valid = L.act && L.x0 + q < V.nx;
+                const float dtv = (hc[0][q] - hx[q]) + (hc[1][q] - hy[q]) + (hc[2][q] - hn[2][q]);
+                const float ybar = valid ? qc[q] - V.tau * (wv[q] * qc[q] + V.lambda_tv * dtv) : 0.f;
+                gc[q] += (1.f + beta) * ybar;
+                if (alias) gc[q] += -beta * ybar;
+                else if (a.prev_fresh) gp[q] = -beta * ybar;
+                else gp[q] += -beta * ybar;
+            }
+            if (L.act) {
+                st4(a.gcur + L.i, gc);
+                if (!alias) st4(a.gprev + L.i, gp);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            xc[q] = xn[q];
+            mc[q] = mn[q];
+            qc[q] = qn[q];
+#pragma unroll
+            for (int c = 0; c < 3; c++) hc[c][q] = hn[c][q];
+        }
+        xl = xnl;
+        ml = mnl;
+        ql = qnl;
+        L.i = in_;
     }
-    if (L.act) {
-        st4(a.gcur + L.i, gc);
-        if (!alias) st4(a.gprev + L.i, gp);
-    }
-    ADJ_WALK_END
 }
+
+// closes the row walks of the certificate passes below
+#define ADJ_WALK_END }
 
 // ---------------- certificate, two row-vector passes ----------------
 // Q = P(x+) - P(y) with P = omtv grad h_mu(D .), stored as 3 fields; then
@@ -1342,16 +1522,19 @@ cudaError_t launch_generic_step(const GenericParams &g, cudaStream_t s)
 
 cudaError_t launch_adjoint_mask(const AdjParams &a, cudaStream_t s)
 {
-    adjoint_grad_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a);
-    adjoint_mask_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a);
+    adjoint_mask_kernel<<<a.nblocks, adj::THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_apply(const AdjParams &a, cudaStream_t s)
 {
-    adjoint_hq_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a);
-    adjoint_apply_kernel<<<a.nplanes * AUX_SEG, AUX_THREADS, 0, s>>>(a);
+    adjoint_apply_kernel<<<a.nblocks, adj::THREADS, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+int adjoint_blocks(int nx, int ny, int nz)
+{
+    return ((nx + 127) / 128) * ((ny + adj::TY - 1) / adj::TY) * ((nz + adj::ZC - 1) / adj::ZC);
 }
 
 }  // namespace spg

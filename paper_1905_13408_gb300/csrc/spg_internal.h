@@ -138,14 +138,15 @@ struct AdjParams {
     const float *gnext;
     float *m;                // scratch volume: masked cotangent of z
     float *gcur, *gprev, *gb, *gw;
-    double *plane_part;      // [nplanes * AUX_SEG][4]
-    float *G, *P, *HQ;       // scratch 3-vector fields, component c at c * stride
-    long long stride;        // a multiple of 4 elements (16-byte aligned components)
+    double *plane_part;      // [nblocks][4]: the mask pass's scalar partials, one per CTA
+    int nblocks;             // CTAs of each pass: adjoint_blocks(nx, ny, nz)
     int prev_fresh;          // gprev has no earlier contribution: write it instead of adding
 };
-// Pass 1 and 2 of the adjoint (D y and p; mask, scalars, gb, gw): two kernels.
+// The adjoint of one step in two passes marching over z: the mask (p, the
+// mask m, the scalar partials, gb, gw), then the update of the cotangents
+// (H_mu D m and ybar). Each is one kernel of adjoint_blocks(...) CTAs.
+int adjoint_blocks(int nx, int ny, int nz);
 cudaError_t launch_adjoint_mask(const AdjParams &a, cudaStream_t s);
-// Pass 3 and 4 (H D m; ybar and the cotangent update): two kernels.
 cudaError_t launch_adjoint_apply(const AdjParams &a, cudaStream_t s);
 cudaError_t launch_timeout_probe(DevState *st, long long timeout_ns, cudaStream_t s);
 // One iteration under alternative readings (VolDesc.readings != 0): the fused
