@@ -785,6 +785,28 @@ def run_adjoint(args):
     return 0
 
 
+def adjoint_bytes_per_voxel(K, C):
+    """Bytes per voxel one backward call over K unrolled iterations moves:
+    two adjoint passes per iteration (mask: x_k, x_{k-1}, omtv, b, w, om1,
+    gnext, gb, gw read, m, gb, gw written, 48 B; apply: x_k, x_{k-1}, m,
+    omtv, w, gcur, gprev read, gcur, gprev written, 36 B; the neighbours'
+    rows come from cache) and the fused forward steps it runs (a sweep of K
+    and the recomputation of all but the last step of each of the
+    ceil(K / C) segments, 28 B each with previous-iterate storage)."""
+    nck = (K + C - 1) // C
+    return 84 * K + 28 * (2 * K - nck)
+
+
+def fourier_bytes_per_voxel():
+    """Bytes per voxel of one iteration with the Fourier-domain data term (a
+    half-spectrum coefficient is half a voxel): forward transform of
+    y_k = x_k + beta d_k, formed from x_k and d_k as the row pass reads them
+    (8 + 4), residual spectrum N F / V - C (4 + 2 + 4 + 4), inverse transform
+    (4 + 4), fused step without w (x_k, d_k, the data gradient, om1, omtv
+    read, x_{k+1} and d_{k+1} written: 28 B)."""
+    return (8 + 4) + (4 + 2 + 4 + 4) + (4 + 4) + 28
+
+
 def measure_adjoint(args):
     """128^3 volume, 50 unrolled iterations (weights 1, tau fixed), forward
     and hand-written adjoint with checkpoints every 10 iterations."""
@@ -811,15 +833,7 @@ def measure_adjoint(args):
         b.grad = None
         w.grad = None
     fwd, bwd = min(t[0] for t in times), min(t[1] for t in times)
-    # bytes the backward moves per voxel: the two adjoint passes per step
-    # (mask: x_k, x_{k-1}, omtv, b, w, om1, gnext, gb, gw read, m, gb, gw
-    # written, 48 B; apply: x_k, x_{k-1}, m, omtv, w, gcur, gprev read, gcur,
-    # gprev written, 36 B; the neighbours' rows come from cache) and the fused
-    # forward steps it runs (a sweep of K and the recomputation of K - K/C,
-    # 28 B each with previous-iterate storage)
-    C = 10
-    nck = (K + C - 1) // C
-    per_voxel = 84 * K + 28 * (2 * K - nck)
+    per_voxel = adjoint_bytes_per_voxel(K, 10)
     achieved = per_voxel * vol.b.size / bwd / 1e9
     peaks, kind = measured_peaks()
     peak = peaks["hbm_gbs"]
@@ -873,12 +887,7 @@ def measure_fourier(args):
     s.close()
     nvox = shape[0] * shape[1] * shape[2]
     peaks, kind = measured_peaks()
-    # bytes per voxel (a half-spectrum coefficient is half a voxel): forward
-    # transform of y_k = x_k + beta d_k, formed from x_k and d_k as the row
-    # pass reads them (8 + 4), residual spectrum N F / V - C (4 + 2 + 4 + 4),
-    # inverse transform (4 + 4), fused step without w (x_k, d_k, the data
-    # gradient, om1, omtv read, x_{k+1} and d_{k+1} written: 28 B)
-    bpv = 12 + 14 + 8 + 28
+    bpv = fourier_bytes_per_voxel()
     achieved = bpv * nvox * args.steps / (ms / 1e3) / 1e9
     return {"metric": "Gvoxel-iter/s, Fourier-domain data term (Eq. 31), %dx%dx%d" % shape,
             "value": nvox * args.steps / (ms / 1e3) / 1e9, "unit": UNIT, "steps": args.steps,

@@ -66,3 +66,15 @@ def test_roofline_counts_the_method_bytes():
     r = bench.roofline_block("bf16", "prev", nvox, 1e-3, 6791.0, "measured")
     assert r["algorithmic_bytes_per_launch"] == r["moved_bytes_per_launch"] == 24 * nvox
     assert r["storage_overhead_bytes_per_launch"] == 0 and r["traffic"] is None
+
+
+def test_secondary_byte_models():
+    """Bytes per voxel behind the adjoint and Fourier-domain lines."""
+    sys.path.insert(0, ROOT)
+    import bench
+    # 50 iterations, checkpoints every 10: 50 adjoint steps of 84 B, a sweep of
+    # 50 fused steps and 5 segments recomputed up to their last step (45), 28 B each
+    assert bench.adjoint_bytes_per_voxel(50, 10) == 84 * 50 + 28 * (50 + 45)
+    assert bench.adjoint_bytes_per_voxel(1, 10) == 84 + 28
+    assert bench.adjoint_bytes_per_voxel(12, 5) == 84 * 12 + 28 * (12 + 9)
+    assert bench.fourier_bytes_per_voxel() == 62
