@@ -3,11 +3,13 @@
 // the strong-convexity certificate, the passes of the adjoint of one step,
 // and the plain step used under alternative readings of the paper.
 //
-// None of them is on the fused hot path, so they use plain global loads;
-// each runs AUX_SEG CTAs per z-plane (one per row segment), every reduction
-// keeps one partial per segment, and the last CTA to finish sums the
-// partials of each volume in segment order, so the results are
-// deterministic. No kernel here waits on another CTA.
+// None of them is on the fused hot path, so they use plain global loads.
+// All but the two adjoint passes run AUX_SEG CTAs per z-plane (one per row
+// segment), every reduction keeps one partial per segment, and the last CTA
+// to finish sums the partials of each volume in segment order, so the
+// results are deterministic; the adjoint passes march over z (a CTA per
+// tile of rows and run of planes) and keep one scalar partial per CTA,
+// which the host sums in a fixed order. No kernel here waits on another CTA.
 #include <cuda_bf16.h>
 
 #include <algorithm>
